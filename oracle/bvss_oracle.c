@@ -1,0 +1,456 @@
+/*
+ * bvss_oracle.c -- plain, slow CPU oracle for the BioVSS++ query path
+ * (arXiv 2412.03301, "Approximate Vector Set Search Inspired by Fly
+ * Olfactory Neural System").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header, table or constant
+ * with the CUDA implementation; it includes only the C standard library.
+ *
+ * Every function follows one definition or algorithm of the paper, step by
+ * step, with no blocking or reordering beyond what that definition states:
+ *
+ *   orc_encode          Def. 7 (FlyHash, h = WTA(W v)) and Alg. 1
+ *   orc_build_filters   count Bloom filter (Def. 8, Alg. 3) and binary
+ *                       Bloom filter / set sketch (Def. 10, Alg. 5)
+ *   orc_query_filters   Alg. 6 lines 1-4 (C_Q, S_Q, P = top-A of C_Q)
+ *   orc_inv_*           inverted index on count Bloom filters (Def. 9,
+ *                       Alg. 4) and the list walk of Alg. 6 lines 5-9
+ *   orc_gate_dense      the same first-layer predicate written directly
+ *   orc_hamming         Alg. 6 line 12 (Hamming distance of sketches)
+ *   orc_heap_select     Alg. 6 lines 10-18 (bounded max-heap of T entries)
+ *   orc_haus*           Def. 4 (Hausdorff distance), in FP64
+ *   orc_refine_topk     Alg. 6 lines 19-23 (exact re-rank, top-k)
+ *
+ * Readings where the paper is silent (the same readings the GPU path uses):
+ *   - activations a_j are FP32 sums taken in the order of W's row, starting
+ *     from +0.0 (a sparse binary W row lists its F input dims ascending);
+ *   - WTA keeps the L largest a_j under the strict order (a desc, j asc):
+ *     values compare as numbers, so -0.0 ties with +0.0; lower index wins;
+ *   - P takes positions by (C_Q desc, position asc);
+ *   - counts saturate at 255 (uint8 storage);
+ *   - the heap orders entries by the pair (d, i) and the sets of F1 are
+ *     visited in ascending id, so it keeps the T smallest pairs (d, i);
+ *   - top-k orders by (distance, id) and pads with (-1, +inf).
+ * Non-finite inputs are outside the method's domain; results are undefined.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+
+/* ------------------------------------------------------------------ */
+/* FlyHash: a = W x with a sparse binary W (row j lists F input dims), */
+/* then winner-take-all keeps the L largest activations (Def. 7).      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    float a;
+    int32_t j;
+} orc_act;
+
+/* strict total order: larger activation first, then lower index first */
+static int orc_act_cmp(const void *pa, const void *pb) {
+    const orc_act *x = (const orc_act *)pa;
+    const orc_act *y = (const orc_act *)pb;
+    if (x->a > y->a) return -1;
+    if (x->a < y->a) return 1;
+    if (x->j < y->j) return -1;
+    if (x->j > y->j) return 1;
+    return 0;
+}
+
+static int orc_u16_cmp(const void *pa, const void *pb) {
+    uint16_t x = *(const uint16_t *)pa, y = *(const uint16_t *)pb;
+    return (x > y) - (x < y);
+}
+
+/* x: n x d row-major; proj: m x F (row j = the input dims summed by output j)
+ * pos: n x L winner positions, ascending; mask: n x ceil(m/32) words or NULL;
+ * act: n x m activations or NULL. */
+int orc_encode(const float *x, int64_t n, int32_t d, const uint16_t *proj,
+               int32_t m, int32_t F, int32_t L, uint16_t *pos, uint32_t *mask,
+               float *act) {
+    if (n < 0 || d < 1 || m < 1 || F < 1 || L < 1 || L > m) return ORC_EINVAL;
+    orc_act *buf = (orc_act *)malloc(sizeof(orc_act) * (size_t)m);
+    if (!buf) return ORC_ENOMEM;
+    const int32_t words = (m + 31) / 32;
+    for (int64_t v = 0; v < n; ++v) {
+        const float *xv = x + v * (int64_t)d;
+        for (int32_t j = 0; j < m; ++j) {
+            float a = 0.0f;
+            for (int32_t t = 0; t < F; ++t) {
+                uint16_t dim = proj[(int64_t)j * F + t];
+                a = a + xv[dim];
+            }
+            buf[j].a = a;
+            buf[j].j = j;
+            if (act) act[v * (int64_t)m + j] = a;
+        }
+        qsort(buf, (size_t)m, sizeof(orc_act), orc_act_cmp);
+        uint16_t *pv = pos + v * (int64_t)L;
+        for (int32_t r = 0; r < L; ++r) pv[r] = (uint16_t)buf[r].j;
+        qsort(pv, (size_t)L, sizeof(uint16_t), orc_u16_cmp);
+        if (mask) {
+            uint32_t *mv = mask + v * (int64_t)words;
+            memset(mv, 0, sizeof(uint32_t) * (size_t)words);
+            for (int32_t r = 0; r < L; ++r)
+                mv[pv[r] >> 5] |= 1u << (pv[r] & 31);
+        }
+    }
+    free(buf);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Filters of every database set (Alg. 3 and Alg. 5):                  */
+/*   sketch S_i = OR of the member codes, count C_i[p] = sum of codes.  */
+/* pos: V_total x L code positions; set_off: n_sets+1 CSR offsets.      */
+/* sketch: n_sets x ceil(m/32) words; count_pm: m x n_sets (position-major) */
+/* ------------------------------------------------------------------ */
+int orc_build_filters(const uint16_t *pos, int32_t L, const int64_t *set_off,
+                      int64_t n_sets, int32_t m, uint32_t *sketch,
+                      uint8_t *count_pm) {
+    if (L < 1 || m < 1 || n_sets < 0) return ORC_EINVAL;
+    const int32_t words = (m + 31) / 32;
+    int32_t *c = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    if (!c) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n_sets; ++i) {
+        memset(c, 0, sizeof(int32_t) * (size_t)m);
+        for (int64_t v = set_off[i]; v < set_off[i + 1]; ++v)
+            for (int32_t r = 0; r < L; ++r) c[pos[v * L + r]] += 1;
+        uint32_t *s = sketch + i * (int64_t)words;
+        memset(s, 0, sizeof(uint32_t) * (size_t)words);
+        for (int32_t p = 0; p < m; ++p) {
+            if (c[p] > 0) s[p >> 5] |= 1u << (p & 31);
+            count_pm[(int64_t)p * n_sets + i] = (uint8_t)(c[p] > 255 ? 255 : c[p]);
+        }
+    }
+    free(c);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Query filters (Alg. 6 lines 1-4).                                   */
+/* qpos: m_q x L codes of the query set.  cq: m counts (not saturated); */
+/* sq: ceil(m/32) words; plist: the first A positions of C_Q sorted by  */
+/* (count desc, position asc).                                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t c;
+    int32_t p;
+} orc_cpos;
+
+static int orc_cpos_cmp(const void *pa, const void *pb) {
+    const orc_cpos *x = (const orc_cpos *)pa, *y = (const orc_cpos *)pb;
+    if (x->c > y->c) return -1;
+    if (x->c < y->c) return 1;
+    return (x->p > y->p) - (x->p < y->p);
+}
+
+int orc_query_filters(const uint16_t *qpos, int64_t m_q, int32_t L, int32_t m,
+                      int32_t A, int32_t *cq, uint32_t *sq, uint16_t *plist) {
+    if (m_q < 1 || L < 1 || m < 1 || A < 0 || A > m) return ORC_EINVAL;
+    memset(cq, 0, sizeof(int32_t) * (size_t)m);
+    for (int64_t v = 0; v < m_q; ++v)
+        for (int32_t r = 0; r < L; ++r) cq[qpos[v * L + r]] += 1;
+    memset(sq, 0, sizeof(uint32_t) * (size_t)((m + 31) / 32));
+    for (int32_t p = 0; p < m; ++p)
+        if (cq[p] > 0) sq[p >> 5] |= 1u << (p & 31);
+    orc_cpos *o = (orc_cpos *)malloc(sizeof(orc_cpos) * (size_t)m);
+    if (!o) return ORC_ENOMEM;
+    for (int32_t p = 0; p < m; ++p) {
+        o[p].c = cq[p];
+        o[p].p = p;
+    }
+    qsort(o, (size_t)m, sizeof(orc_cpos), orc_cpos_cmp);
+    for (int32_t a = 0; a < A; ++a) plist[a] = (uint16_t)o[a].p;
+    free(o);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Inverted index on count Bloom filters (Def. 9, Alg. 4).             */
+/* List p holds (i, C_i[p]) sorted by count descending.  Entries with   */
+/* count 0 are kept implicitly: they sit at the tail of every list in   */
+/* ascending id, and a walk with threshold M <= 0 reaches all of them.  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t m;
+    int64_t n_sets;
+    int64_t *off;   /* m+1 */
+    int32_t *ids;   /* nonzero entries, list-major */
+    uint8_t *cnt;
+} orc_inv;
+
+typedef struct {
+    uint8_t c;
+    int32_t i;
+} orc_entry;
+
+static int orc_entry_cmp(const void *pa, const void *pb) {
+    const orc_entry *x = (const orc_entry *)pa, *y = (const orc_entry *)pb;
+    if (x->c > y->c) return -1;
+    if (x->c < y->c) return 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+void orc_inv_free(orc_inv *ix) {
+    if (!ix) return;
+    free(ix->off);
+    free(ix->ids);
+    free(ix->cnt);
+    free(ix);
+}
+
+orc_inv *orc_inv_build(const uint8_t *count_pm, int32_t m, int64_t n_sets) {
+    orc_inv *ix = (orc_inv *)calloc(1, sizeof(orc_inv));
+    if (!ix) return NULL;
+    ix->m = m;
+    ix->n_sets = n_sets;
+    ix->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    if (!ix->off) { orc_inv_free(ix); return NULL; }
+    int64_t total = 0;
+    for (int32_t p = 0; p < m; ++p) {
+        ix->off[p] = total;
+        for (int64_t i = 0; i < n_sets; ++i)
+            if (count_pm[(int64_t)p * n_sets + i] > 0) ++total;
+    }
+    ix->off[m] = total;
+    ix->ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
+    ix->cnt = (uint8_t *)malloc((size_t)(total > 0 ? total : 1));
+    orc_entry *tmp = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(n_sets > 0 ? n_sets : 1));
+    if (!ix->ids || !ix->cnt || !tmp) { free(tmp); orc_inv_free(ix); return NULL; }
+    for (int32_t p = 0; p < m; ++p) {
+        int64_t k = 0;
+        for (int64_t i = 0; i < n_sets; ++i) {
+            uint8_t c = count_pm[(int64_t)p * n_sets + i];
+            if (c > 0) { tmp[k].c = c; tmp[k].i = (int32_t)i; ++k; }
+        }
+        qsort(tmp, (size_t)k, sizeof(orc_entry), orc_entry_cmp);
+        for (int64_t e = 0; e < k; ++e) {
+            ix->ids[ix->off[p] + e] = tmp[e].i;
+            ix->cnt[ix->off[p] + e] = tmp[e].c;
+        }
+    }
+    free(tmp);
+    return ix;
+}
+
+/* number of stored (nonzero) entries of list p, and a copy of them */
+int64_t orc_inv_list(const orc_inv *ix, int32_t p, int32_t *ids, uint8_t *cnt) {
+    int64_t n = ix->off[p + 1] - ix->off[p];
+    if (ids) memcpy(ids, ix->ids + ix->off[p], sizeof(int32_t) * (size_t)n);
+    if (cnt) memcpy(cnt, ix->cnt + ix->off[p], (size_t)n);
+    return n;
+}
+
+/* Alg. 6 lines 5-9: F1 = union over p in P of {i : (i, c) in I[p], c >= M}.
+ * gate: n_sets bytes, 1 = in F1. */
+int orc_inv_gate(const orc_inv *ix, const uint16_t *plist, int32_t A,
+                 int32_t M, uint8_t *gate) {
+    memset(gate, 0, (size_t)ix->n_sets);
+    for (int32_t a = 0; a < A; ++a) {
+        int32_t p = plist[a];
+        for (int64_t e = ix->off[p]; e < ix->off[p + 1]; ++e)
+            if ((int32_t)ix->cnt[e] >= M) gate[ix->ids[e]] = 1;
+        /* implicit zero-count entries: (i, 0) for every set not listed */
+        if (M <= 0)
+            for (int64_t i = 0; i < ix->n_sets; ++i) gate[i] = 1;
+    }
+    return ORC_OK;
+}
+
+/* the same predicate read straight off the counts: exists p in P with C_i[p] >= M */
+int orc_gate_dense(const uint8_t *count_pm, int32_t m, int64_t n_sets,
+                   const uint16_t *plist, int32_t A, int32_t M, uint8_t *gate) {
+    (void)m;
+    for (int64_t i = 0; i < n_sets; ++i) {
+        uint8_t g = 0;
+        for (int32_t a = 0; a < A; ++a)
+            if ((int32_t)count_pm[(int64_t)plist[a] * n_sets + i] >= M) g = 1;
+        gate[i] = g;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 6 line 12: Hamming distance between S_Q and every sketch,      */
+/* counted bit by bit.  h[i] = -1 where gate[i] == 0 (gate may be NULL) */
+/* ------------------------------------------------------------------ */
+int orc_hamming(const uint32_t *sq, const uint32_t *sketch, int64_t n_sets,
+                int32_t m, const uint8_t *gate, int32_t *h) {
+    const int32_t words = (m + 31) / 32;
+    for (int64_t i = 0; i < n_sets; ++i) {
+        if (gate && !gate[i]) { h[i] = -1; continue; }
+        const uint32_t *s = sketch + i * (int64_t)words;
+        int32_t d = 0;
+        for (int32_t p = 0; p < m; ++p) {
+            uint32_t bq = (sq[p >> 5] >> (p & 31)) & 1u;
+            uint32_t bi = (s[p >> 5] >> (p & 31)) & 1u;
+            if (bq != bi) ++d;
+        }
+        h[i] = d;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 6 lines 10-18: a max-heap of capacity T over pairs (d, i),      */
+/* filled by visiting F1 in ascending id.  out_ids receives the ids of */
+/* the heap in ascending id order; *n_out their number.                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t d;
+    int32_t i;
+} orc_hent;
+
+static int orc_hent_gt(orc_hent x, orc_hent y) { /* (d, i) lexicographic > */
+    return x.d > y.d || (x.d == y.d && x.i > y.i);
+}
+
+static void orc_heap_sift_up(orc_hent *hp, int64_t k) {
+    while (k > 0) {
+        int64_t par = (k - 1) / 2;
+        if (!orc_hent_gt(hp[k], hp[par])) break;
+        orc_hent t = hp[k]; hp[k] = hp[par]; hp[par] = t;
+        k = par;
+    }
+}
+
+static void orc_heap_sift_down(orc_hent *hp, int64_t n, int64_t k) {
+    for (;;) {
+        int64_t l = 2 * k + 1, r = l + 1, b = k;
+        if (l < n && orc_hent_gt(hp[l], hp[b])) b = l;
+        if (r < n && orc_hent_gt(hp[r], hp[b])) b = r;
+        if (b == k) break;
+        orc_hent t = hp[k]; hp[k] = hp[b]; hp[b] = t;
+        k = b;
+    }
+}
+
+static int orc_i32_cmp(const void *pa, const void *pb) {
+    int32_t x = *(const int32_t *)pa, y = *(const int32_t *)pb;
+    return (x > y) - (x < y);
+}
+
+int orc_heap_select(const int32_t *h, const uint8_t *gate, int64_t n_sets,
+                    int32_t T, int32_t *out_ids, int32_t *n_out) {
+    if (T < 0) return ORC_EINVAL;
+    orc_hent *hp = (orc_hent *)malloc(sizeof(orc_hent) * (size_t)(T > 0 ? T : 1));
+    if (!hp) return ORC_ENOMEM;
+    int64_t size = 0;
+    for (int64_t i = 0; i < n_sets; ++i) {
+        if (gate && !gate[i]) continue;
+        orc_hent e = {h[i], (int32_t)i};
+        if (size < T) {                 /* |G| < T: push */
+            hp[size] = e;
+            orc_heap_sift_up(hp, size);
+            ++size;
+        } else if (T > 0 && e.d < hp[0].d) { /* d < top: pop, push */
+            hp[0] = e;
+            orc_heap_sift_down(hp, size, 0);
+        }
+    }
+    for (int64_t k = 0; k < size; ++k) out_ids[k] = hp[k].i;
+    qsort(out_ids, (size_t)size, sizeof(int32_t), orc_i32_cmp);
+    *n_out = (int32_t)size;
+    free(hp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Def. 4: Hausdorff distance with dist = Euclidean norm, in FP64.     */
+/* ------------------------------------------------------------------ */
+static double orc_dist(const float *a, const float *b, int32_t d) {
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)a[k] - (double)b[k];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+/* max over q in Q of min over v in V of dist(q, v) */
+double orc_haus_directed(const float *Q, int64_t mq, const float *V, int64_t mv,
+                         int32_t d) {
+    double worst = 0.0;
+    for (int64_t a = 0; a < mq; ++a) {
+        double best = INFINITY;
+        for (int64_t b = 0; b < mv; ++b) {
+            double t = orc_dist(Q + a * d, V + b * d, d);
+            if (t < best) best = t;
+        }
+        if (best > worst) worst = best;
+    }
+    return worst;
+}
+
+double orc_haus(const float *Q, int64_t mq, const float *V, int64_t mv, int32_t d) {
+    double x = orc_haus_directed(Q, mq, V, mv, d);
+    double y = orc_haus_directed(V, mv, Q, mq, d);
+    return x > y ? x : y;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 6 lines 19-23: exact Hausdorff of every candidate, then the k  */
+/* smallest by (distance, id); padded with (-1, +inf).                  */
+/* cand_dist (optional) receives the distance of every candidate.       */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double dist;
+    int64_t id;
+} orc_res;
+
+static int orc_res_cmp(const void *pa, const void *pb) {
+    const orc_res *x = (const orc_res *)pa, *y = (const orc_res *)pb;
+    if (x->dist < y->dist) return -1;
+    if (x->dist > y->dist) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+int orc_refine_topk(const float *Q, int64_t mq, const float *vectors,
+                    const int64_t *set_off, int32_t d, const int32_t *cand,
+                    int64_t n_cand, int32_t k, int64_t *out_ids,
+                    double *out_dist, double *cand_dist) {
+    if (k < 1 || n_cand < 0) return ORC_EINVAL;
+    orc_res *r = (orc_res *)malloc(sizeof(orc_res) * (size_t)(n_cand > 0 ? n_cand : 1));
+    if (!r) return ORC_ENOMEM;
+    for (int64_t c = 0; c < n_cand; ++c) {
+        int64_t i = cand[c];
+        const float *V = vectors + set_off[i] * (int64_t)d;
+        r[c].dist = orc_haus(Q, mq, V, set_off[i + 1] - set_off[i], d);
+        r[c].id = i;
+        if (cand_dist) cand_dist[c] = r[c].dist;
+    }
+    qsort(r, (size_t)n_cand, sizeof(orc_res), orc_res_cmp);
+    for (int32_t t = 0; t < k; ++t) {
+        if (t < n_cand) {
+            out_ids[t] = r[t].id;
+            out_dist[t] = r[t].dist;
+        } else {
+            out_ids[t] = -1;
+            out_dist[t] = INFINITY;
+        }
+    }
+    free(r);
+    return ORC_OK;
+}
+
+/* exact top-k over all sets (Def. 5 with delta = 0): the ground truth */
+int orc_bruteforce_topk(const float *Q, int64_t mq, const float *vectors,
+                        const int64_t *set_off, int64_t n_sets, int32_t d,
+                        int32_t k, int64_t *out_ids, double *out_dist) {
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_sets > 0 ? n_sets : 1));
+    if (!all) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n_sets; ++i) all[i] = (int32_t)i;
+    int rc = orc_refine_topk(Q, mq, vectors, set_off, d, all, n_sets, k, out_ids,
+                             out_dist, NULL);
+    free(all);
+    return rc;
+}
