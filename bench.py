@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""Throughput of the BioVSS++ query path (arXiv 2412.03301) on GB300.
+
+One step = one bvss_query call over a batch of 1000 query sets against an
+index of 1,000,000 synthetic vector sets (d = 384, FlyHash m = 4096, F = 8,
+L = 64, C = 2000, k = 10, A = 3, M = 1): FlyHash of the queries, both filter
+layers over every set, the candidate select, the exact FP32 Hausdorff
+re-rank and the top-k -- all in the library's CUDA kernels.
+
+Prints one JSON line (rank 0).  Under torchrun every rank holds its own copy
+of the index and answers its own query batch (query sets are independent),
+so the work per GPU is fixed ("weak" scaling) and no collective touches the
+data path; ranks only meet at the barriers around the timed region.
+
+--impl reference times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "query sets/s at recall@10≥0.95 (1M sets); fast vs plain form, same GB300"
+UNIT = "query sets/s"
+LAUNCHES_PER_BATCH = 10   # encode, prep, scan, hist, thresh, count, offsets, write, refine, topk
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+POPC_PER_CLK_PER_SM = 16   # 32-bit population count throughput per SM per clock
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["large", "small"], default="large")
+    ap.add_argument("--recall-queries", type=int, default=200)
+    ap.add_argument("--cpu-sample-sets", type=int, default=2000)
+    ap.add_argument("--cpu-sample-queries", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload_cfg(name):
+    from paper_2412_03301_gb300 import datagen
+    c = dict(datagen.LARGE if name == "large" else datagen.SMALL)
+    c["A"], c["M"] = 3, 1
+    return c
+
+
+def workload_name(c):
+    return ("vector-set search, N=%d sets of %d-%d vectors, d=%d FP32 (grid 2^-8), "
+            "%d-component mixture; FlyHash m=%d F=%d L=%d; %d query sets of %d-%d; "
+            "A=%d M=%d C=%d k=%d" % (c["n_sets"], c["size_lo"], c["size_hi"], c["d"],
+                                     c["n_components"], c["m"], c["fanin"], c["L"],
+                                     c["n_queries"], c["q_lo"], c["q_hi"], c["A"], c["M"],
+                                     c["C"], c["k"]))
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.proc = None
+        self.uuid = None
+        try:
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and f[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# exact ground truth (recall measurement only; plain torch GEMM + reductions)
+# --------------------------------------------------------------------------
+def exact_topk(vec, vnorm, set_of_row, n_sets, qvec, qoff, qids, k, chunk=1 << 21):
+    """Exact Hausdorff top-k over every set for the listed query sets.
+
+    Squared distances |q|^2 + |v|^2 - 2 q.v in FP32 (exact for values on the
+    2^-8 grid).  Returns (ids (len(qids), k), sorted squared distances, all
+    squared distances of the k-th place)."""
+    V = vec.shape[0]
+    out_ids, out_d2 = [], []
+    for q in qids:
+        Q = qvec[qoff[q]:qoff[q + 1]]
+        mq = Q.shape[0]
+        qn = (Q * Q).sum(1)
+        rowpart = torch.full((mq, n_sets), float("inf"), device=vec.device)
+        colpart = torch.zeros(n_sets, device=vec.device)
+        for r0 in range(0, V, chunk):
+            r1 = min(V, r0 + chunk)
+            D = torch.addmm(qn[:, None] + vnorm[None, r0:r1], Q, vec[r0:r1].T, beta=1, alpha=-2)
+            D.clamp_(min=0)
+            sid = set_of_row[r0:r1]
+            rowpart.scatter_reduce_(1, sid.expand(mq, -1), D, "amin")
+            colpart.scatter_reduce_(0, sid, D.min(0).values, "amax")
+        h2 = torch.maximum(rowpart.max(0).values, colpart)
+        srt, idx = torch.sort(h2, stable=True)
+        out_ids.append(idx[:k])
+        out_d2.append(srt[:k])
+    return torch.stack(out_ids), torch.stack(out_d2)
+
+
+def recall_at_k(got_ids, gt_ids, gt_d2, got_true_d2, k):
+    """(strict, tie-aware) recall@k averaged over queries (Sec. 7.1.3 metric)."""
+    strict, ties = [], []
+    for q in range(gt_ids.shape[0]):
+        g = set(gt_ids[q].tolist())
+        r = [i for i in got_ids[q].tolist() if i >= 0]
+        strict.append(len(g.intersection(r)) / len(g))
+        kth = gt_d2[q, k - 1]
+        ties.append(min(k, int((got_true_d2[q] <= kth).sum())) / k)
+    return float(np.mean(strict)), float(np.mean(ties))
+
+
+def true_d2_of(vec, vnorm, qvec, qoff, offsets, qids, ids):
+    """Squared Hausdorff (same FP32 GEMM form as exact_topk) of given (query, set) pairs."""
+    out = np.full(ids.shape, np.inf)
+    for j, q in enumerate(qids):
+        Q = qvec[qoff[q]:qoff[q + 1]]
+        qn = (Q * Q).sum(1)
+        for c, i in enumerate(ids[j].tolist()):
+            if i < 0:
+                continue
+            r0, r1 = int(offsets[i]), int(offsets[i + 1])
+            D = qn[:, None] + vnorm[None, r0:r1] - 2 * Q @ vec[r0:r1].T
+            D.clamp_(min=0)
+            out[j, c] = float(torch.maximum(D.min(1).values.max(), D.min(0).values.max()))
+    return out
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# --------------------------------------------------------------------------
+def oracle_sample_index(vec_host, offsets, proj, c, n_sets_s):
+    from oracle import oracle
+    off_s = offsets[:n_sets_s + 1].copy()
+    return oracle.Index(vec_host[:off_s[-1]], off_s, proj, c["L"])
+
+
+def oracle_query_estimate(ix, Q, c, n_sets_s):
+    """Seconds the oracle's Alg. 6 would take for one query set at full size.
+
+    Measured on the sample index: the fixed part (query FlyHash and filters),
+    the per-set part (gate walk, Hamming scan, heap) scaled by N / n_sets_s,
+    and the refine time per candidate scaled to C candidates."""
+    from oracle import oracle
+    C_s = min(n_sets_s, 10 * max(c["k"], int(round(c["C"] * n_sets_s / c["n_sets"]))))
+    t0 = time.perf_counter()
+    qpos, _ = oracle.encode(Q, ix.proj, ix.L)
+    cq, sq, plist = oracle.query_filters(qpos, ix.m, c["A"])
+    t1 = time.perf_counter()
+    gate = ix.inv.gate(plist, c["M"])
+    h = oracle.hamming(sq, ix.sketch, gate, m=ix.m)
+    cand = oracle.heap_select(h, gate, C_s)
+    t2 = time.perf_counter()
+    oracle.refine_topk(Q, ix.vectors, ix.set_off, cand, c["k"])
+    t3 = time.perf_counter()
+    parts = ((t1 - t0), (t2 - t1) * c["n_sets"] / n_sets_s,
+             (t3 - t2) / max(1, len(cand)) * c["C"])
+    return sum(parts), parts
+
+
+def oracle_description(c, n_sets_s, n_q):
+    return ("oracle Alg. 6 (literal inverted lists, bit-loop Hamming, heap, FP64 refine), "
+            "1 thread, index of the first %d of %d sets, %d query sets; per query set: "
+            "query FlyHash+filters + (gate walk, Hamming, heap) x %d/%d + refine time per "
+            "candidate x C=%d" % (n_sets_s, c["n_sets"], n_q, c["n_sets"], n_sets_s, c["C"]))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2412_03301_gb300 import datagen
+    from oracle import oracle
+    oracle.build()
+    c = workload_cfg(args.workload)
+    n_s = min(args.cpu_sample_sets, c["n_sets"])
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
+                         d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],
+                         q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
+                         seed=args.seed, device=gen_dev)
+    off, qoff = w["offsets"], w["q_offsets"]
+    vec_host = w["vectors"][:int(off[n_s])].cpu().numpy()
+    qvec_host = w["q_vectors"].cpu().numpy()
+    del w["vectors"]
+    ix = oracle_sample_index(vec_host, off, w["proj"], c, n_s)
+    times = []
+    for s in range(args.warmup + args.steps):
+        q = s % c["n_queries"]
+        est, _ = oracle_query_estimate(ix, qvec_host[qoff[q]:qoff[q + 1]], c, n_s)
+        if s >= args.warmup:
+            times.append(est)
+    value = 1.0 / float(np.mean(times))
+    desc = oracle_description(c, n_s, args.steps) + "; one query set per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(c)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    from paper_2412_03301_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2412_03301_gb300 import bvss, datagen
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    c = workload_cfg(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
+                         d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],
+                         q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
+                         seed=args.seed + 0 * rank, device=dev)
+    if rank > 0:   # each rank answers its own query sets against the same database
+        qs = datagen.set_sizes(c["n_queries"], c["q_lo"], c["q_hi"], 1000 * (args.seed + rank) + 12)
+        mix = datagen.Mixture(c["d"], c["n_components"], args.seed, device=dev)
+        w["q_vectors"] = mix.draw_sets(qs, 1000 * (args.seed + rank) + 22)
+        w["q_offsets"] = datagen.offsets_from_sizes(qs)
+    off = w["offsets"]
+    t0 = time.perf_counter()
+    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"])
+    torch.cuda.synchronize(dev)
+    build_s = time.perf_counter() - t0
+    qv, qoff = w["q_vectors"], w["q_offsets"]
+    nq = qoff.shape[0] - 1
+    kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"])
+
+    # one traced pass (outside the timed region): |F1| per query for the roofline
+    tr = bvss.bvss_query_trace(ix, qv, qoff, **kw)
+    torch.cuda.synchronize(dev)
+    h = tr["h"]
+    gated_pairs = int((h != -1).sum().item())        # 0xFFFF as int16 is -1
+    n_cand = tr["n_cand"].to(torch.int64)
+    sum_cand = int(n_cand.sum().item())
+    cand = tr["cand"]
+    sizes = torch.from_numpy(np.diff(off)).to(dev)
+    cand_rows = int(sizes[cand.clamp(min=0).to(torch.int64)].masked_fill(cand < 0, 0).sum().item())
+    qsz = torch.from_numpy(np.diff(qoff)).to(dev)
+    pair_elems = int((sizes[cand.clamp(min=0).to(torch.int64)].masked_fill(cand < 0, 0)
+                      * qsz[:, None]).sum().item())
+    ids_ref = tr["ids"].clone()
+    del tr, h, cand
+
+    # recall@10 against exact brute force (rank 0, subset of the query sets)
+    rec = None
+    if rank == 0 and args.recall_queries > 0:
+        vec = w["vectors"]
+        vnorm = (vec * vec).sum(1)
+        set_of_row = torch.repeat_interleave(torch.arange(c["n_sets"], device=dev),
+                                             torch.from_numpy(np.diff(off)).to(dev))
+        qids = list(range(min(args.recall_queries, nq)))
+        gt_ids, gt_d2 = exact_topk(vec, vnorm, set_of_row, c["n_sets"], qv, qoff, qids, c["k"])
+        got = ids_ref[qids].cpu().numpy()
+        got_d2 = true_d2_of(vec, vnorm, qv, qoff, off, qids, got)
+        rs, rt = recall_at_k(got, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(), got_d2, c["k"])
+        rec = {"recall_at_10": rs, "recall_at_10_ties": rt, "queries": len(qids)}
+        del vnorm, set_of_row
+
+    # CPU baseline sample (rank 0): copy the sample before freeing the database
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_s = min(args.cpu_sample_sets, c["n_sets"])
+        vec_host = w["vectors"][:int(off[n_s])].cpu().numpy()
+        qvec_host = qv.cpu().numpy()
+    del w["vectors"]
+    torch.cuda.empty_cache()
+
+    # device-resident inputs: the timed region
+    out_ids = torch.empty((nq, c["k"]), dtype=torch.int64, device=dev)
+    out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw)
+    torch.cuda.synchronize(dev)
+    assert torch.equal(out_ids, ids_ref)
+    bvss.bvss_profile_enable(ix, True)
+    bvss.bvss_profile_read(ix, reset=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stage_ms, nbatch = bvss.bvss_profile_read(ix, reset=True)
+    bvss.bvss_profile_enable(ix, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nq / (ms / 1e3)
+
+    # end to end through the same API: pinned host query vectors in, host results out
+    hq = qv.cpu().pin_memory()
+    hi = torch.empty((nq, c["k"]), dtype=torch.int64).pin_memory()
+    hd = torch.empty((nq, c["k"]), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert torch.equal(hi, ids_ref.cpu())
+    h2d = hq.numel() * 4 + (nq + 1) * 8
+    d2h = hi.numel() * 8 + hd.numel() * 4
+
+    if rank != 0:
+        return 0
+    if not args.no_cpu:
+        oix = oracle_sample_index(vec_host, off, w["proj"], c, n_s)
+        nqs = min(args.cpu_sample_queries, nq)
+        ests = [oracle_query_estimate(oix, qvec_host[qoff[q]:qoff[q + 1]], c, n_s)
+                for q in range(nqs)]
+        per_q = float(np.mean([e[0] for e in ests]))
+        parts = np.mean([e[1] for e in ests], axis=0)
+        cpu = {"value": 1.0 / per_q, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": oracle_description(c, n_s, nqs),
+               "parts_s": {"query_filters": float(parts[0]), "scan_scaled": float(parts[1]),
+                           "refine_scaled": float(parts[2])}}
+
+    # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
+    per_launch = {k: v / max(1, nbatch) for k, v in stage_ms.items()}
+    dominant = max(("scan", "refine"), key=lambda s: per_launch[s])
+    clock_hz = SM_MAX_MHZ * 1e6
+    if dominant == "scan":
+        popc = gated_pairs * (c["m"] // 32)             # one 32-bit popcount per sketch word
+        achieved = popc / (per_launch["scan"] / 1e3) / 1e12
+        peak = SM_COUNT * POPC_PER_CLK_PER_SM * clock_hz / 1e12
+        roof = {"kernel": "k_scan", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
+                "units_per_launch": "%d (query, gated set) pairs x %d words" % (gated_pairs,
+                                                                              c["m"] // 32),
+                "peak_basis": "152 SMs x 16 popc/clk x 2070 MHz (nominal unit count)"}
+    else:
+        flops = 2.0 * pair_elems * c["d"]
+        achieved = flops / (per_launch["refine"] / 1e3) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_hz / 1e12
+        roof = {"kernel": "k_refine", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "units_per_launch": "%d vector pairs x d=%d" % (pair_elems, c["d"]),
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FP32 FMA)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(c), "form": "plain (FP32 refine, random FlyHash)",
+                   "query_sets_per_step_per_gpu": nq,
+                   "l2": "inputs larger than L2 (sketch matrix %.0f MB, vectors %.1f GB)"
+                         % (c["n_sets"] * c["m"] / 8 / 1e6, off[-1] * c["d"] * 4 / 1e9),
+                   "parallelism": "replicated index, query sets split over ranks"},
+        "recall": rec,
+        "roofline": roof,
+        "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": LAUNCHES_PER_BATCH * nbatch,
+        "clocks": clk,
+        "build_s": build_s,
+        "work": {"gated_pairs_per_step": gated_pairs, "candidates_per_step": sum_cand,
+                 "candidate_rows_per_step": cand_rows},
+    }
+    print(json.dumps(line), flush=True)
+    ix.close()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

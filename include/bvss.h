@@ -1,0 +1,201 @@
+/*
+ * bvss.h -- C ABI of the GB300 BioVSS++ query path.
+ *
+ * Method: arXiv 2412.03301 ("Approximate Vector Set Search Inspired by Fly
+ * Olfactory Neural System").  A database of vector sets is encoded with
+ * FlyHash (Def. 7, Alg. 1) into sparse binary codes, summarised per set by a
+ * count Bloom filter (Def. 8, Alg. 3) and a binary Bloom filter / sketch
+ * (Def. 10, Alg. 5).  A query set is answered by Alg. 6: its own count
+ * filter and sketch, a first-layer gate over the A most frequent code
+ * positions (the inverted index of Def. 9 / Alg. 4, held here in dense
+ * position-major form), a second layer keeping the C sets of smallest
+ * sketch Hamming distance, then an exact Hausdorff re-rank (Def. 4) of those
+ * C candidates and a top-k (Def. 5).
+ *
+ * Conventions for every call:
+ *  - Return value: BVSS_OK (0) or a negative status; bvss_last_error()
+ *    gives a message for the calling thread.  No C++ exception crosses the
+ *    ABI.  A CUDA error inside a call returns BVSS_ECUDA.
+ *  - "device" pointers are CUDA device (or managed) memory of the device
+ *    that was current when the index was built; "host" pointers are host
+ *    memory.  Where a parameter says "host or device", the library looks the
+ *    pointer up (cudaPointerGetAttributes) and copies host data itself.
+ *  - stream: a cudaStream_t cast to void*, or NULL for the legacy default
+ *    stream.  Work is enqueued on it.  Calls that take only device pointers
+ *    return without waiting; their outputs are valid once the stream has
+ *    synchronised.  Calls given host outputs synchronise the stream before
+ *    returning.
+ *  - The caller owns every buffer it passes.  The index owns its copies.
+ *  - One index must not be queried from two host threads at once (queries
+ *    share index-owned scratch memory).
+ *  - Inputs are assumed finite; bvss_build rejects non-finite database
+ *    values, and non-finite query values give unspecified results.
+ *
+ * Readings of points the paper leaves open (see the oracle for the same):
+ * activations are FP32 sums in the order W's row lists its dims; WTA ties
+ * and P ties break by lower index; counts saturate at 255; the candidate
+ * stage keeps the min(C, |F1|) smallest (Hamming, id) pairs; top-k orders
+ * by (distance, id) and pads with (-1, +inf).
+ */
+#ifndef BVSS_H
+#define BVSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BVSS_OK 0
+#define BVSS_EINVAL (-1)   /* an argument is out of range or inconsistent */
+#define BVSS_ENOMEM (-2)   /* a device or host allocation failed */
+#define BVSS_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+
+/* limits of this implementation */
+#define BVSS_MAX_D 4096        /* vector dimension */
+#define BVSS_MAX_M 32768       /* code length b (FlyHash outputs) */
+#define BVSS_MAX_FANIN 32      /* nonzeros per row of the sparse projection */
+#define BVSS_MAX_L 1024        /* WTA winners per code */
+#define BVSS_MAX_A 64          /* inverted lists read per query */
+#define BVSS_MAX_C 16384       /* candidate budget per query set */
+#define BVSS_MAX_QSET 128      /* vectors per query set */
+
+/* Build parameters (Def. 7 and Alg. 6's Theta minus the search knobs). */
+typedef struct bvss_params {
+    int32_t d;       /* vector dimension, 4..BVSS_MAX_D, multiple of 4 */
+    int32_t m;       /* code length b = Bloom filter length; multiple of 128, <= BVSS_MAX_M */
+    int32_t fanin;   /* F: input dims summed by each output of W, 1..min(d, BVSS_MAX_FANIN) */
+    int32_t wta_l;   /* L_wta: winners kept by WTA, 1..min(m, BVSS_MAX_L) */
+    int32_t flags;   /* must be 0 */
+    int32_t reserved[3];
+} bvss_params;
+
+/* Search parameters of Alg. 6 (Theta's A, M, c = T) and Def. 5's k. */
+typedef struct bvss_search {
+    int32_t k;   /* results per query set, >= 1 */
+    int32_t C;   /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
+    int32_t A;   /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
+    int32_t M;   /* minimum count; 0 lets every set through the first layer */
+} bvss_search;
+
+typedef struct bvss_index bvss_index;   /* opaque; owns its device memory */
+
+/* Optional intermediates of Alg. 6 for parity checks.  Every pointer is
+ * device memory or NULL (skipped).  n_q = queries of the call, N = sets,
+ * W = m/32, Vq = query vectors of the call. */
+typedef struct bvss_trace {
+    uint16_t *qpos;      /* Vq x L   FlyHash positions of the query vectors, ascending */
+    int32_t *cq;         /* n_q x m  query count filter C_Q (Alg. 6 line 1) */
+    uint32_t *sq;        /* n_q x W  query sketch S_Q (line 2), bit p of word p/32 */
+    uint16_t *plist;     /* n_q x A  top-A positions of C_Q (lines 3-4) */
+    uint16_t *h;         /* n_q x N  Hamming(S_Q, S_i) (line 12); 0xFFFF = not in F1 */
+    int32_t *cand;       /* n_q x C  candidate ids (F2), ascending; -1 padded */
+    int32_t *n_cand;     /* n_q      number of candidates, min(C, |F1|) */
+    float *cand_dist;    /* n_q x C  Hausdorff distance of cand[j]; +inf padded */
+} bvss_trace;
+
+/*
+ * bvss_build -- encode every database vector (Def. 7, Alg. 1) and build the
+ * per-set sketches (Def. 10, Alg. 5) and count filters (Def. 8, Alg. 3),
+ * held position-major as the dense form of the inverted index (Def. 9).
+ *   vectors      host or device, V x d FP32 row-major, sets stored one after
+ *                another; V = set_offsets[n_sets]
+ *   set_offsets  host, n_sets + 1 int64, set_offsets[0] = 0, strictly
+ *                increasing (every set holds at least one vector, Def. 2)
+ *   n_sets       1 .. 2^31 - 1
+ *   proj         host, m x fanin uint16: row j lists the input dims whose sum
+ *                is output j of the sparse binary projection W, strictly
+ *                ascending, each < d
+ *   params       build parameters; flags = 0
+ *   stream       see conventions; bvss_build synchronises it before returning
+ *   out          receives the new index (NULL on error)
+ * Errors: EINVAL for any bad size, order or non-finite vector value; ENOMEM;
+ * ECUDA.  The caller may free every input once the call returns.
+ */
+int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+               const uint16_t *proj, const bvss_params *params, void *stream,
+               bvss_index **out);
+
+/*
+ * bvss_query -- Alg. 6 for a batch of query sets: FlyHash the query vectors,
+ * C_Q / S_Q / P, first-layer gate (count >= M at one of the A positions),
+ * the min(C, |F1|) smallest (Hamming, id) pairs, exact Hausdorff (Def. 4) of
+ * those candidates in FP32, then the k smallest (distance, id).
+ *   q_vectors   host or device, Vq x d FP32, query sets stored one after
+ *               another; Vq = q_offsets[n_queries]
+ *   q_offsets   host, n_queries + 1 int64, q_offsets[0] = 0, strictly
+ *               increasing, each set at most BVSS_MAX_QSET vectors
+ *   n_queries   >= 0
+ *   s           search parameters
+ *   out_ids     host or device, n_queries x k int64: set ids, -1 padded
+ *   out_dist    host or device, n_queries x k FP32: distances, +inf padded
+ * The first call (and any call with a larger batch) allocates index-owned
+ * scratch memory.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int bvss_query(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+               int64_t n_queries, const bvss_search *s, int64_t *out_ids,
+               float *out_dist, void *stream);
+
+/* bvss_query plus the intermediates named by tr (device pointers, may be NULL). */
+int bvss_query_trace(const bvss_index *ix, const float *q_vectors,
+                     const int64_t *q_offsets, int64_t n_queries,
+                     const bvss_search *s, int64_t *out_ids, float *out_dist,
+                     const bvss_trace *tr, void *stream);
+
+/*
+ * bvss_encode -- FlyHash (Def. 7) of n vectors with the index's projection.
+ *   x     device, n x d FP32
+ *   pos   device, n x L uint16 winner positions, ascending (may be NULL)
+ *   mask  device, n x (m/32) uint32 code bits (may be NULL)
+ */
+int bvss_encode(const bvss_index *ix, const float *x, int64_t n, uint16_t *pos,
+                uint32_t *mask, void *stream);
+
+/* Sizes of an index. Any output pointer may be NULL. */
+int bvss_index_info(const bvss_index *ix, bvss_params *params, int64_t *n_sets,
+                    int64_t *n_vectors);
+
+/* Copy database codes (Alg. 1) of vectors [first, first + n) to pos (device, n x L). */
+int bvss_get_codes(const bvss_index *ix, int64_t first, int64_t n, uint16_t *pos,
+                   void *stream);
+
+/* Gather the sketches (Def. 10) of the sets listed in ids (device, n int64)
+ * into out (device, n x m/32 uint32).  Ids must lie in [0, n_sets). */
+int bvss_get_sketches(const bvss_index *ix, const int64_t *ids, int64_t n,
+                      uint32_t *out, void *stream);
+
+/* Gather the count filters (Def. 8, saturated at 255) of the sets listed in
+ * ids (device, n int64) into out (device, n x m uint8, set-major). */
+int bvss_get_counts(const bvss_index *ix, const int64_t *ids, int64_t n,
+                    uint8_t *out, void *stream);
+
+/* Stages of bvss_query timed by the profiler (CUDA events on the query
+ * stream, recorded between the kernels of every batch). */
+#define BVSS_STAGE_ENCODE 0   /* FlyHash of the query vectors + C_Q, S_Q, P */
+#define BVSS_STAGE_SCAN 1     /* first-layer gate + sketch Hamming over all sets */
+#define BVSS_STAGE_SELECT 2   /* the C smallest (Hamming, id) */
+#define BVSS_STAGE_REFINE 3   /* exact Hausdorff of the candidates */
+#define BVSS_STAGE_TOPK 4     /* k smallest (distance, id) and result copies */
+#define BVSS_N_STAGES 5
+
+/* Turn per-stage timing of later bvss_query calls on (on != 0) or off. */
+int bvss_profile_enable(bvss_index *ix, int on);
+
+/* Sum of the stage times (ms, host array of BVSS_N_STAGES) and the number of
+ * timed query batches since the last reset.  Waits for the recorded events;
+ * reset != 0 clears the sums afterwards. */
+int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int reset);
+
+/* Release an index and all its device memory (NULL is a no-op).  Work that
+ * uses the index must have finished. */
+void bvss_free(bvss_index *ix);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bvss_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BVSS_H */

@@ -1,0 +1,276 @@
+"""Thin Python binding of the C ABI in include/bvss.h (same names).
+
+Argument marshalling only: torch tensors supply device memory and streams,
+numpy arrays supply host offsets and the projection table, and every step of
+the search runs in the CUDA kernels of ``libbvss.so``.  There is no CPU
+fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbvss.so")
+
+BVSS_OK, BVSS_EINVAL, BVSS_ENOMEM, BVSS_ECUDA = 0, -1, -2, -3
+GATED_OUT = 0xFFFF
+
+_c_i32, _c_i64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+
+class bvss_params(ctypes.Structure):
+    _fields_ = [("d", _c_i32), ("m", _c_i32), ("fanin", _c_i32), ("wta_l", _c_i32),
+                ("flags", _c_i32), ("reserved", _c_i32 * 3)]
+
+
+class bvss_search(ctypes.Structure):
+    _fields_ = [("k", _c_i32), ("C", _c_i32), ("A", _c_i32), ("M", _c_i32)]
+
+
+class bvss_trace(ctypes.Structure):
+    _fields_ = [("qpos", _vp), ("cq", _vp), ("sq", _vp), ("plist", _vp), ("h", _vp),
+                ("cand", _vp), ("n_cand", _vp), ("cand_dist", _vp)]
+
+
+class BvssError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bvss status %d: %s" % (code, msg))
+        self.code = code
+
+
+SYMBOLS = {
+    "bvss_build": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, ctypes.POINTER(bvss_params), _vp,
+                                  ctypes.POINTER(_vp)]),
+    "bvss_query": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, ctypes.POINTER(bvss_search), _vp,
+                                  _vp, _vp]),
+    "bvss_query_trace": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, ctypes.POINTER(bvss_search),
+                                        _vp, _vp, ctypes.POINTER(bvss_trace), _vp]),
+    "bvss_encode": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp, _vp]),
+    "bvss_index_info": (ctypes.c_int, [_vp, ctypes.POINTER(bvss_params),
+                                       ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64)]),
+    "bvss_get_codes": (ctypes.c_int, [_vp, _c_i64, _c_i64, _vp, _vp]),
+    "bvss_get_sketches": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "bvss_get_counts": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "bvss_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bvss_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(_c_i64), ctypes.c_int]),
+    "bvss_free": (None, [_vp]),
+    "bvss_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbvss.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libbvss.so not found at %s: build it with "
+                           "`python -m paper_2412_03301_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def bvss_last_error() -> str:
+    return load().bvss_last_error().decode()
+
+
+def _check(rc):
+    if rc != BVSS_OK:
+        raise BvssError(rc, bvss_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _host_i64(a):
+    a = np.ascontiguousarray(np.asarray(a), dtype=np.int64)
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+class Index:
+    """Owns a bvss_index handle; freed with bvss_free."""
+
+    def __init__(self, handle, params: bvss_params, n_sets: int, n_vectors: int, device):
+        self.handle = handle
+        self.params = params
+        self.n_sets = n_sets
+        self.n_vectors = n_vectors
+        self.device = device
+
+    @property
+    def d(self):
+        return self.params.d
+
+    @property
+    def m(self):
+        return self.params.m
+
+    @property
+    def L(self):
+        return self.params.wta_l
+
+    def close(self):
+        if self.handle:
+            torch.cuda.synchronize(self.device)
+            load().bvss_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: int,
+               stream=None) -> Index:
+    """Build an index (Alg. 1, 3, 4, 5). vectors: (V, d) float32, host or CUDA."""
+    lib = load()
+    assert vectors.dtype == torch.float32 and vectors.is_contiguous()
+    off, off_p = _host_i64(set_offsets)
+    proj = np.ascontiguousarray(proj, dtype=np.uint16)
+    p = bvss_params(d=vectors.shape[1], m=proj.shape[0],
+                    fanin=proj.shape[1] if fanin is None else fanin, wta_l=wta_l, flags=0)
+    h = ctypes.c_void_p()
+    dev = vectors.device if vectors.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _check(lib.bvss_build(_dptr(vectors), off_p, off.shape[0] - 1,
+                              ctypes.c_void_p(proj.ctypes.data), ctypes.byref(p),
+                              _stream(stream), ctypes.byref(h)))
+    return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
+
+
+def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
+               M: int = 1, out_ids=None, out_dist=None, stream=None):
+    """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
+
+    q_vectors and the outputs may live on the host or on the index's GPU."""
+    lib = load()
+    off, off_p = _host_i64(q_offsets)
+    nq = off.shape[0] - 1
+    dev = ix.device
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    s = bvss_search(k=k, C=C, A=A, M=M)
+    _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
+                          _dptr(out_ids), _dptr(out_dist), _stream(stream)))
+    return out_ids, out_dist
+
+
+def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
+                     A: int = 3, M: int = 1, stream=None):
+    """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
+
+    Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
+    holding the same bits (view them as uint16 / uint32 in numpy)."""
+    lib = load()
+    off, off_p = _host_i64(q_offsets)
+    nq = off.shape[0] - 1
+    dev = ix.device
+    vq = int(off[-1])
+    t = dict(
+        qpos=torch.empty((vq, ix.L), dtype=torch.int16, device=dev),
+        cq=torch.empty((nq, ix.m), dtype=torch.int32, device=dev),
+        sq=torch.empty((nq, ix.m // 32), dtype=torch.int32, device=dev),
+        plist=torch.empty((nq, A), dtype=torch.int16, device=dev),
+        h=torch.empty((nq, ix.n_sets), dtype=torch.int16, device=dev),
+        cand=torch.empty((nq, C), dtype=torch.int32, device=dev),
+        n_cand=torch.empty((nq,), dtype=torch.int32, device=dev),
+        cand_dist=torch.empty((nq, C), dtype=torch.float32, device=dev),
+    )
+    tr = bvss_trace(**{name: t[name].data_ptr() for name in t})
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    s = bvss_search(k=k, C=C, A=A, M=M)
+    _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
+                                _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
+    t["ids"] = ids
+    t["dist"] = dist
+    return t
+
+
+def bvss_encode(ix: Index, x: torch.Tensor, stream=None):
+    """FlyHash codes (Def. 7) of x (n, d) on the GPU -> (pos (n, L), mask (n, m/32)).
+
+    pos holds uint16 bits in an int16 tensor, mask uint32 bits in an int32 tensor."""
+    lib = load()
+    n = x.shape[0]
+    pos = torch.empty((n, ix.L), dtype=torch.int16, device=x.device)
+    mask = torch.empty((n, ix.m // 32), dtype=torch.int32, device=x.device)
+    _check(lib.bvss_encode(ix.handle, _dptr(x), n, _dptr(pos), _dptr(mask), _stream(stream)))
+    return pos, mask
+
+
+def bvss_index_info(ix: Index):
+    lib = load()
+    p = bvss_params()
+    n_sets, n_vec = _c_i64(), _c_i64()
+    _check(lib.bvss_index_info(ix.handle, ctypes.byref(p), ctypes.byref(n_sets),
+                               ctypes.byref(n_vec)))
+    return dict(d=p.d, m=p.m, fanin=p.fanin, wta_l=p.wta_l, n_sets=n_sets.value,
+                n_vectors=n_vec.value)
+
+
+def bvss_get_codes(ix: Index, first: int, n: int, stream=None):
+    lib = load()
+    out = torch.empty((n, ix.L), dtype=torch.int16, device=ix.device)   # uint16 bits
+    _check(lib.bvss_get_codes(ix.handle, first, n, _dptr(out), _stream(stream)))
+    return out
+
+
+def bvss_get_sketches(ix: Index, ids: torch.Tensor, stream=None):
+    lib = load()
+    ids = ids.to(device=ix.device, dtype=torch.int64).contiguous()
+    out = torch.empty((ids.shape[0], ix.m // 32), dtype=torch.int32, device=ix.device)  # uint32 bits
+    _check(lib.bvss_get_sketches(ix.handle, _dptr(ids), ids.shape[0], _dptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def bvss_get_counts(ix: Index, ids: torch.Tensor, stream=None):
+    lib = load()
+    ids = ids.to(device=ix.device, dtype=torch.int64).contiguous()
+    out = torch.empty((ids.shape[0], ix.m), dtype=torch.uint8, device=ix.device)
+    _check(lib.bvss_get_counts(ix.handle, _dptr(ids), ids.shape[0], _dptr(out),
+                               _stream(stream)))
+    return out
+
+
+STAGES = ("encode", "scan", "select", "refine", "topk")
+
+
+def bvss_profile_enable(ix: Index, on: bool = True):
+    _check(load().bvss_profile_enable(ix.handle, 1 if on else 0))
+
+
+def bvss_profile_read(ix: Index, reset: bool = True):
+    """({stage: summed ms}, number of timed batches) since the last reset."""
+    ms = (ctypes.c_double * len(STAGES))()
+    nb = _c_i64()
+    _check(load().bvss_profile_read(ix.handle, ms, ctypes.byref(nb), 1 if reset else 0))
+    return dict(zip(STAGES, list(ms))), nb.value
+
+
+def bvss_free(ix: Index):
+    ix.close()

@@ -1,0 +1,559 @@
+// api.cu -- the C ABI of include/bvss.h: argument checks, index memory,
+// and the order of kernels for bvss_build (Alg. 1, 3, 5 and the dense form of
+// Alg. 4) and bvss_query (Alg. 6) of arXiv 2412.03301.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "bvss_internal.cuh"
+
+using namespace bvss;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define BVSS_CU(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? BVSS_ENOMEM : BVSS_ECUDA,     \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),         \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+// device (or managed) memory, as opposed to host memory of any kind
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T));
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// h rows are padded to 64 entries so every row starts 128-byte aligned
+int64_t h_stride(const bvss_index *ix) { return round_up(ix->n_sets, 64); }
+
+// largest query batch whose score matrix stays within 2 GiB
+int64_t batch_cap(const bvss_index *ix) {
+    int64_t qb = ((int64_t)1 << 30) / h_stride(ix);
+    if (qb > 1024) qb = 1024;
+    if (qb < 1) qb = 1;
+    return qb;
+}
+
+void free_workspace(Workspace &w) {
+    dfree(w.qvec);
+    dfree(w.qoff);
+    dfree(w.qpos);
+    dfree(w.sq);
+    dfree(w.plist);
+    dfree(w.h);
+    dfree(w.hist);
+    dfree(w.thr);
+    dfree(w.chunk);
+    dfree(w.cand);
+    dfree(w.cand_dist);
+    dfree(w.out_ids);
+    dfree(w.out_dist);
+    w = Workspace();
+}
+
+void free_index(bvss_index *ix) {
+    if (!ix) return;
+    dfree(ix->vec);
+    dfree(ix->vnorm);
+    dfree(ix->set_off);
+    dfree(ix->proj);
+    dfree(ix->codes);
+    dfree(ix->sketch);
+    dfree(ix->count);
+    dfree(ix->flag);
+    for (int i = 0; i < ix->n_planes; ++i) dfree(ix->planes[i].words);
+    free_workspace(ix->ws);
+    for (int i = 0; i < kOffRing; ++i) {
+        if (ix->off_host[i]) cudaFreeHost(ix->off_host[i]);
+        if (ix->off_event[i]) cudaEventDestroy(ix->off_event[i]);
+    }
+    for (int64_t i = 0; i < ix->prof_cap; ++i) cudaEventDestroy(ix->prof_ev[i]);
+    delete[] ix->prof_ev;
+    delete ix;
+}
+
+int check_params(const bvss_params *p) {
+    if (!p) return fail(BVSS_EINVAL, "params is NULL");
+    if (p->d < 4 || p->d > BVSS_MAX_D || p->d % 4 != 0)
+        return fail(BVSS_EINVAL, "d = %d: need 4 <= d <= %d and d %% 4 == 0", p->d, BVSS_MAX_D);
+    if (p->m < 128 || p->m > BVSS_MAX_M || p->m % 128 != 0)
+        return fail(BVSS_EINVAL, "m = %d: need 128 <= m <= %d and m %% 128 == 0", p->m,
+                    BVSS_MAX_M);
+    if (p->fanin < 1 || p->fanin > BVSS_MAX_FANIN || p->fanin > p->d)
+        return fail(BVSS_EINVAL, "fanin = %d: need 1 <= fanin <= min(d, %d)", p->fanin,
+                    BVSS_MAX_FANIN);
+    if (p->wta_l < 1 || p->wta_l > BVSS_MAX_L || p->wta_l > p->m)
+        return fail(BVSS_EINVAL, "wta_l = %d: need 1 <= L <= min(m, %d)", p->wta_l, BVSS_MAX_L);
+    if (p->flags != 0) return fail(BVSS_EINVAL, "flags must be 0");
+    return BVSS_OK;
+}
+
+int check_offsets(const int64_t *off, int64_t n, int64_t max_size, const char *what) {
+    if (!off) return fail(BVSS_EINVAL, "%s offsets are NULL", what);
+    if (off[0] != 0) return fail(BVSS_EINVAL, "%s offsets must start at 0", what);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t s = off[i + 1] - off[i];
+        if (s < 1) return fail(BVSS_EINVAL, "%s set %lld is empty or offsets decrease", what,
+                               (long long)i);
+        if (max_size > 0 && s > max_size)
+            return fail(BVSS_EINVAL, "%s set %lld holds %lld vectors (limit %lld)", what,
+                        (long long)i, (long long)s, (long long)max_size);
+    }
+    return BVSS_OK;
+}
+
+int check_device(const bvss_index *ix) {
+    int dev = -1;
+    BVSS_CU(cudaGetDevice(&dev));
+    if (dev != ix->device)
+        return fail(BVSS_EINVAL, "index lives on device %d but device %d is current", ix->device,
+                    dev);
+    return BVSS_OK;
+}
+
+// first-layer gate plane for minimum count M (1 <= M <= 255), built on demand
+int get_plane(bvss_index *ix, int M, cudaStream_t st, const uint32_t **out) {
+    for (int i = 0; i < ix->n_planes; ++i)
+        if (ix->planes[i].M == M) {
+            *out = ix->planes[i].words;
+            return BVSS_OK;
+        }
+    int slot = ix->n_planes;
+    if (slot == kMaxPlanes) {
+        slot = kMaxPlanes - 1;   // replace the most recent extra plane
+        BVSS_CU(cudaStreamSynchronize(st));
+        dfree(ix->planes[slot].words);
+    } else {
+        ++ix->n_planes;
+    }
+    GatePlane &pl = ix->planes[slot];
+    pl.M = -1;
+    BVSS_CU(dalloc(&pl.words, (size_t)ix->p.m * ix->NW));
+    BVSS_CU(launch_gate_plane(ix->count, ix->p.m, ix->n_sets, ix->NW, M, pl.words, st));
+    pl.M = M;
+    *out = pl.words;
+    return BVSS_OK;
+}
+
+int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int k,
+                     bool need_qvec, bool need_out) {
+    Workspace &w = ix->ws;
+    const int m = ix->p.m, W = ix->W, L = ix->p.wta_l, d = ix->p.d;
+    const int64_t hs = h_stride(ix);
+    const int n_chunks = (int)((ix->n_sets + kSelChunk - 1) / kSelChunk);
+    if (nq > w.cap_q || nvq > w.cap_vq || C > w.cap_C || A > w.cap_A || k > w.cap_k ||
+        (need_qvec && !w.qvec) || (need_out && !w.out_ids)) {
+        const int64_t cq = nq > w.cap_q ? nq : w.cap_q;
+        const int64_t cvq = nvq > w.cap_vq ? nvq : w.cap_vq;
+        const int cC = C > w.cap_C ? C : w.cap_C;
+        const int cA = A > w.cap_A ? A : w.cap_A;
+        const int ck = k > w.cap_k ? k : w.cap_k;
+        const bool had_qvec = w.qvec != nullptr, had_out = w.out_ids != nullptr;
+        BVSS_CU(cudaDeviceSynchronize());
+        free_workspace(w);
+        BVSS_CU(dalloc(&w.qoff, cq + 1));
+        BVSS_CU(dalloc(&w.qpos, (size_t)cvq * L));
+        BVSS_CU(dalloc(&w.sq, (size_t)cq * W));
+        BVSS_CU(dalloc(&w.plist, (size_t)cq * cA));
+        BVSS_CU(dalloc(&w.h, (size_t)cq * hs));
+        BVSS_CU(dalloc(&w.hist, (size_t)cq * (m + 1)));
+        BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
+        BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * 4));
+        BVSS_CU(dalloc(&w.cand, (size_t)cq * cC));
+        BVSS_CU(dalloc(&w.cand_dist, (size_t)cq * cC));
+        if (need_qvec || had_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)cvq * d));
+        if (need_out || had_out) {
+            BVSS_CU(dalloc(&w.out_ids, (size_t)cq * ck));
+            BVSS_CU(dalloc(&w.out_dist, (size_t)cq * ck));
+        }
+        w.cap_q = cq;
+        w.cap_vq = cvq;
+        w.cap_C = cC;
+        w.cap_A = cA;
+        w.cap_k = ck;
+    }
+    // pinned staging ring for the per-batch query offsets
+    for (int i = 0; i < kOffRing; ++i) {
+        if (ix->off_cap < w.cap_q + 1 || !ix->off_host[i]) {
+            if (ix->off_event[i]) BVSS_CU(cudaEventSynchronize(ix->off_event[i]));
+            if (ix->off_host[i]) cudaFreeHost(ix->off_host[i]);
+            ix->off_host[i] = nullptr;
+            BVSS_CU(cudaMallocHost(reinterpret_cast<void **>(&ix->off_host[i]),
+                                   sizeof(int64_t) * (size_t)(w.cap_q + 1)));
+            if (!ix->off_event[i])
+                BVSS_CU(cudaEventCreateWithFlags(&ix->off_event[i], cudaEventDisableTiming));
+        }
+    }
+    ix->off_cap = w.cap_q + 1;
+    return BVSS_OK;
+}
+
+// reserve kProfEvents timing events for one batch; returns their base or null
+cudaEvent_t *prof_reserve(bvss_index *ix) {
+    if (ix->prof_used + kProfEvents > ix->prof_cap) {
+        const int64_t cap = ix->prof_cap ? 2 * ix->prof_cap : 64 * kProfEvents;
+        cudaEvent_t *ev = new (std::nothrow) cudaEvent_t[cap];
+        if (!ev) return nullptr;
+        for (int64_t i = 0; i < ix->prof_cap; ++i) ev[i] = ix->prof_ev[i];
+        for (int64_t i = ix->prof_cap; i < cap; ++i)
+            if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+                for (int64_t j = ix->prof_cap; j < i; ++j) cudaEventDestroy(ev[j]);
+                delete[] ev;
+                return nullptr;
+            }
+        delete[] ix->prof_ev;
+        ix->prof_ev = ev;
+        ix->prof_cap = cap;
+    }
+    cudaEvent_t *base = ix->prof_ev + ix->prof_used;
+    ix->prof_used += kProfEvents;
+    return base;
+}
+
+int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+               int64_t n_queries, const bvss_search *s, int64_t *out_ids, float *out_dist,
+               const bvss_trace *tr, void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (!s) return fail(BVSS_EINVAL, "search parameters are NULL");
+    const int L = ix->p.wta_l, m = ix->p.m, d = ix->p.d, W = ix->W;
+    if (s->k < 1) return fail(BVSS_EINVAL, "k = %d: need k >= 1", s->k);
+    if (s->C < s->k || s->C > BVSS_MAX_C)
+        return fail(BVSS_EINVAL, "C = %d: need k <= C <= %d", s->C, BVSS_MAX_C);
+    if (s->A < 1 || s->A > L || s->A > BVSS_MAX_A)
+        return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
+    if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
+    if (n_queries < 0) return fail(BVSS_EINVAL, "n_queries < 0");
+    if (n_queries == 0) return BVSS_OK;
+    if (!q_vectors || !out_ids || !out_dist)
+        return fail(BVSS_EINVAL, "query vectors or outputs are NULL");
+    int rc = check_offsets(q_offsets, n_queries, BVSS_MAX_QSET, "query");
+    if (rc) return rc;
+    rc = check_device(ix);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool qv_dev = is_device_ptr(q_vectors);
+    const bool ids_dev = is_device_ptr(out_ids), dist_dev = is_device_ptr(out_dist);
+    if (tr) {
+        const void *ptrs[] = {tr->qpos, tr->cq, tr->sq, tr->plist, tr->h, tr->cand, tr->n_cand,
+                              tr->cand_dist};
+        for (const void *p : ptrs)
+            if (p && !is_device_ptr(p)) return fail(BVSS_EINVAL, "trace pointers must be device memory");
+    }
+    const int k = s->k, C = s->C, A = s->A, M = s->M;
+    const int64_t QB = batch_cap(ix);
+    int64_t max_vq = 0;
+    for (int64_t b0 = 0; b0 < n_queries; b0 += QB) {
+        const int64_t b1 = b0 + QB < n_queries ? b0 + QB : n_queries;
+        const int64_t nv = q_offsets[b1] - q_offsets[b0];
+        if (nv > max_vq) max_vq = nv;
+    }
+    const int64_t nq_cap = n_queries < QB ? n_queries : QB;
+    rc = ensure_workspace(ix, nq_cap, max_vq, C, A, k, !qv_dev, !(ids_dev && dist_dev));
+    if (rc) return rc;
+    Workspace &w = ix->ws;
+
+    const int gate_mode = M == 0 ? 0 : (M > 255 ? 2 : 1);
+    const uint32_t *plane = nullptr;
+    if (gate_mode == 1) {
+        rc = get_plane(ix, M, st, &plane);
+        if (rc) return rc;
+    }
+    const int64_t hs = h_stride(ix);
+
+    for (int64_t b0 = 0; b0 < n_queries; b0 += QB) {
+        const int64_t b1 = b0 + QB < n_queries ? b0 + QB : n_queries;
+        const int nb = (int)(b1 - b0);
+        const int64_t v0 = q_offsets[b0], v1 = q_offsets[b1], nv = v1 - v0;
+        int max_mq = 0;
+        // batch-relative offsets through a pinned ring slot
+        const int slot = ix->off_next;
+        ix->off_next = (ix->off_next + 1) % kOffRing;
+        BVSS_CU(cudaEventSynchronize(ix->off_event[slot]));
+        int64_t *oh = ix->off_host[slot];
+        for (int j = 0; j <= nb; ++j) {
+            oh[j] = q_offsets[b0 + j] - v0;
+            if (j > 0 && oh[j] - oh[j - 1] > max_mq) max_mq = (int)(oh[j] - oh[j - 1]);
+        }
+        BVSS_CU(cudaMemcpyAsync(w.qoff, oh, sizeof(int64_t) * (size_t)(nb + 1),
+                                cudaMemcpyHostToDevice, st));
+        BVSS_CU(cudaEventRecord(ix->off_event[slot], st));
+        cudaEvent_t *ev = ix->prof_on ? prof_reserve(ix) : nullptr;
+        if (ev) BVSS_CU(cudaEventRecord(ev[0], st));
+        const float *qv = q_vectors + v0 * d;
+        if (!qv_dev) {
+            BVSS_CU(cudaMemcpyAsync(w.qvec, qv, sizeof(float) * (size_t)nv * d,
+                                    cudaMemcpyHostToDevice, st));
+            qv = w.qvec;
+        }
+        // Alg. 6 lines 1-4
+        BVSS_CU(launch_encode(qv, nv, d, ix->proj, m, ix->p.fanin, L, w.qpos, nullptr, st));
+        BVSS_CU(launch_query_prep(w.qpos, w.qoff, nb, m, L, A, w.sq, w.plist,
+                                  tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
+        // lines 5-12
+        BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, plane, ix->NW, gate_mode, w.sq, w.plist,
+                            A, nb, w.h, hs, st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
+        // lines 10-18
+        BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
+        // lines 19-23
+        BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d, w.cand,
+                              w.thr, C, w.cand_dist, st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
+        int64_t *ids = ids_dev ? out_ids + b0 * k : w.out_ids;
+        float *dist = dist_dev ? out_dist + b0 * k : w.out_dist;
+        BVSS_CU(launch_topk(w.cand, w.cand_dist, w.thr, nb, C, k, ids, dist, st));
+        if (!ids_dev)
+            BVSS_CU(cudaMemcpyAsync(out_ids + b0 * k, ids, sizeof(int64_t) * (size_t)nb * k,
+                                    cudaMemcpyDeviceToHost, st));
+        if (!dist_dev)
+            BVSS_CU(cudaMemcpyAsync(out_dist + b0 * k, dist, sizeof(float) * (size_t)nb * k,
+                                    cudaMemcpyDeviceToHost, st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
+        if (tr) {
+            const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+            if (tr->qpos)
+                BVSS_CU(cudaMemcpyAsync(tr->qpos + v0 * L, w.qpos, sizeof(uint16_t) * nv * L, dd, st));
+            if (tr->sq)
+                BVSS_CU(cudaMemcpyAsync(tr->sq + b0 * W, w.sq, sizeof(uint32_t) * nb * W, dd, st));
+            if (tr->plist)
+                BVSS_CU(cudaMemcpyAsync(tr->plist + b0 * A, w.plist, sizeof(uint16_t) * nb * A, dd, st));
+            if (tr->h)
+                BVSS_CU(cudaMemcpy2DAsync(tr->h + b0 * ix->n_sets, sizeof(uint16_t) * ix->n_sets,
+                                          w.h, sizeof(uint16_t) * hs,
+                                          sizeof(uint16_t) * ix->n_sets, nb, dd, st));
+            if (tr->cand)
+                BVSS_CU(cudaMemcpyAsync(tr->cand + b0 * C, w.cand, sizeof(int32_t) * nb * C, dd, st));
+            if (tr->n_cand)
+                BVSS_CU(cudaMemcpy2DAsync(tr->n_cand + b0, sizeof(int32_t), w.thr + 3,
+                                          4 * sizeof(int32_t), sizeof(int32_t), nb, dd, st));
+            if (tr->cand_dist)
+                BVSS_CU(cudaMemcpyAsync(tr->cand_dist + b0 * C, w.cand_dist,
+                                        sizeof(float) * nb * C, dd, st));
+        }
+    }
+    if (!ids_dev || !dist_dev) BVSS_CU(cudaStreamSynchronize(st));
+    return BVSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+               const uint16_t *proj, const bvss_params *params, void *stream,
+               bvss_index **out) {
+    if (!out) return fail(BVSS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n_sets < 1 || n_sets > 0x7fffffffLL)
+        return fail(BVSS_EINVAL, "n_sets = %lld: need 1 <= n_sets < 2^31", (long long)n_sets);
+    if (!vectors || !proj) return fail(BVSS_EINVAL, "vectors or proj is NULL");
+    rc = check_offsets(set_offsets, n_sets, 0, "database");
+    if (rc) return rc;
+    const bvss_params p = *params;
+    for (int j = 0; j < p.m; ++j) {
+        const uint16_t *row = proj + (int64_t)j * p.fanin;
+        for (int t = 0; t < p.fanin; ++t) {
+            if (row[t] >= p.d) return fail(BVSS_EINVAL, "proj[%d][%d] = %d >= d", j, t, row[t]);
+            if (t > 0 && row[t] <= row[t - 1])
+                return fail(BVSS_EINVAL, "proj row %d is not strictly ascending", j);
+        }
+    }
+    bvss_index *ix = new (std::nothrow) bvss_index();
+    if (!ix) return fail(BVSS_ENOMEM, "host allocation failed");
+    rc = [&]() -> int {
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        BVSS_CU(cudaGetDevice(&ix->device));
+        ix->p = p;
+        ix->n_sets = n_sets;
+        ix->n_vec = set_offsets[n_sets];
+        ix->W = p.m / 32;
+        ix->NW = (n_sets + 31) / 32;
+        const int64_t nv = ix->n_vec;
+        BVSS_CU(dalloc(&ix->vec, (size_t)nv * p.d));
+        BVSS_CU(dalloc(&ix->vnorm, (size_t)nv));
+        BVSS_CU(dalloc(&ix->set_off, (size_t)n_sets + 1));
+        BVSS_CU(dalloc(&ix->proj, (size_t)p.m * p.fanin));
+        BVSS_CU(dalloc(&ix->codes, (size_t)nv * p.wta_l));
+        BVSS_CU(dalloc(&ix->sketch, (size_t)n_sets * ix->W));
+        BVSS_CU(dalloc(&ix->count, (size_t)n_sets * p.m));
+        BVSS_CU(dalloc(&ix->flag, 1));
+        const cudaMemcpyKind kind =
+            is_device_ptr(vectors) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        BVSS_CU(cudaMemcpyAsync(ix->vec, vectors, sizeof(float) * (size_t)nv * p.d, kind, st));
+        BVSS_CU(cudaMemcpyAsync(ix->set_off, set_offsets, sizeof(int64_t) * (size_t)(n_sets + 1),
+                                cudaMemcpyHostToDevice, st));
+        BVSS_CU(cudaMemcpyAsync(ix->proj, proj, sizeof(uint16_t) * (size_t)p.m * p.fanin,
+                                cudaMemcpyHostToDevice, st));
+        BVSS_CU(cudaMemsetAsync(ix->flag, 0, sizeof(int), st));
+        BVSS_CU(launch_check_finite(ix->vec, nv * p.d, ix->flag, st));
+        int bad = 0;
+        BVSS_CU(cudaMemcpyAsync(&bad, ix->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BVSS_CU(cudaStreamSynchronize(st));
+        if (bad) return fail(BVSS_EINVAL, "database vectors hold non-finite values");
+        // Alg. 1 over the database, then Alg. 3 / Alg. 5 from the same codes
+        BVSS_CU(launch_norms(ix->vec, nv, p.d, ix->vnorm, st));
+        BVSS_CU(launch_encode(ix->vec, nv, p.d, ix->proj, p.m, p.fanin, p.wta_l, ix->codes,
+                              nullptr, st));
+        BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,
+                                     ix->count, st));
+        const uint32_t *pl = nullptr;
+        int r = get_plane(ix, 1, st, &pl);
+        if (r) return r;
+        BVSS_CU(cudaStreamSynchronize(st));
+        return BVSS_OK;
+    }();
+    if (rc) {
+        cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+        free_index(ix);
+        return rc;
+    }
+    *out = ix;
+    return BVSS_OK;
+}
+
+int bvss_query(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+               int64_t n_queries, const bvss_search *s, int64_t *out_ids, float *out_dist,
+               void *stream) {
+    return query_impl(const_cast<bvss_index *>(ix), q_vectors, q_offsets, n_queries, s, out_ids,
+                      out_dist, nullptr, stream);
+}
+
+int bvss_query_trace(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+                     int64_t n_queries, const bvss_search *s, int64_t *out_ids, float *out_dist,
+                     const bvss_trace *tr, void *stream) {
+    return query_impl(const_cast<bvss_index *>(ix), q_vectors, q_offsets, n_queries, s, out_ids,
+                      out_dist, tr, stream);
+}
+
+int bvss_encode(const bvss_index *ix, const float *x, int64_t n, uint16_t *pos, uint32_t *mask,
+                void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (n < 0) return fail(BVSS_EINVAL, "n < 0");
+    if (n == 0) return BVSS_OK;
+    if (!x || !is_device_ptr(x)) return fail(BVSS_EINVAL, "x must be device memory");
+    if ((pos && !is_device_ptr(pos)) || (mask && !is_device_ptr(mask)))
+        return fail(BVSS_EINVAL, "pos / mask must be device memory");
+    int rc = check_device(ix);
+    if (rc) return rc;
+    BVSS_CU(launch_encode(x, n, ix->p.d, ix->proj, ix->p.m, ix->p.fanin, ix->p.wta_l, pos, mask,
+                          reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_index_info(const bvss_index *ix, bvss_params *params, int64_t *n_sets,
+                    int64_t *n_vectors) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (params) *params = ix->p;
+    if (n_sets) *n_sets = ix->n_sets;
+    if (n_vectors) *n_vectors = ix->n_vec;
+    return BVSS_OK;
+}
+
+int bvss_get_codes(const bvss_index *ix, int64_t first, int64_t n, uint16_t *pos, void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (first < 0 || n < 0 || first + n > ix->n_vec)
+        return fail(BVSS_EINVAL, "vector range out of bounds");
+    if (n == 0) return BVSS_OK;
+    if (!pos || !is_device_ptr(pos)) return fail(BVSS_EINVAL, "pos must be device memory");
+    BVSS_CU(cudaMemcpyAsync(pos, ix->codes + first * ix->p.wta_l,
+                            sizeof(uint16_t) * (size_t)n * ix->p.wta_l, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_get_sketches(const bvss_index *ix, const int64_t *ids, int64_t n, uint32_t *out,
+                      void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (n < 0) return fail(BVSS_EINVAL, "n < 0");
+    if (n == 0) return BVSS_OK;
+    if (!ids || !out || !is_device_ptr(ids) || !is_device_ptr(out))
+        return fail(BVSS_EINVAL, "ids and out must be device memory");
+    BVSS_CU(launch_gather_sketches(ix->sketch, ix->W, ix->n_sets, ids, n, out,
+                                   reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_get_counts(const bvss_index *ix, const int64_t *ids, int64_t n, uint8_t *out,
+                    void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (n < 0) return fail(BVSS_EINVAL, "n < 0");
+    if (n == 0) return BVSS_OK;
+    if (!ids || !out || !is_device_ptr(ids) || !is_device_ptr(out))
+        return fail(BVSS_EINVAL, "ids and out must be device memory");
+    BVSS_CU(launch_gather_counts(ix->count, ix->p.m, ix->n_sets, ids, n, out,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_profile_enable(bvss_index *ix, int on) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    ix->prof_on = on != 0;
+    return BVSS_OK;
+}
+
+int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int reset) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    for (int64_t b = 0; b + kProfEvents <= ix->prof_used; b += kProfEvents) {
+        BVSS_CU(cudaEventSynchronize(ix->prof_ev[b + kProfEvents - 1]));
+        for (int sidx = 0; sidx < BVSS_N_STAGES; ++sidx) {
+            float ms = 0.0f;
+            BVSS_CU(cudaEventElapsedTime(&ms, ix->prof_ev[b + sidx], ix->prof_ev[b + sidx + 1]));
+            ix->prof_ms[sidx] += ms;
+        }
+        ix->prof_batches += 1;
+    }
+    ix->prof_used = 0;
+    if (stage_ms)
+        for (int sidx = 0; sidx < BVSS_N_STAGES; ++sidx) stage_ms[sidx] = ix->prof_ms[sidx];
+    if (n_batches) *n_batches = ix->prof_batches;
+    if (reset) {
+        for (int sidx = 0; sidx < BVSS_N_STAGES; ++sidx) ix->prof_ms[sidx] = 0.0;
+        ix->prof_batches = 0;
+    }
+    return BVSS_OK;
+}
+
+void bvss_free(bvss_index *ix) { free_index(ix); }
+
+const char *bvss_last_error(void) { return g_err; }
+
+}  // extern "C"

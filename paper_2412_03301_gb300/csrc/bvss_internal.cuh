@@ -1,0 +1,134 @@
+// bvss_internal.cuh -- index layout and kernel entry points shared by the
+// CUDA translation units of the BioVSS++ query path (arXiv 2412.03301).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bvss.h"
+
+namespace bvss {
+
+constexpr int kMaxPlanes = 8;          // cached first-layer gate planes (one per M)
+constexpr uint16_t kGatedOut = 0xFFFF; // h of a set outside F1
+constexpr int kSelChunk = 16384;       // sets per CTA in the candidate select
+constexpr int kOffRing = 4;            // pinned staging slots for query offsets
+constexpr int kProfEvents = BVSS_N_STAGES + 1;  // events per profiled batch
+
+// A bit plane of the first-layer gate for one minimum count M:
+// word w of row p holds bit b = (C_{32w+b}[p] >= M), for every set (Def. 9 in
+// dense form: the union of Alg. 6 lines 5-9 is an OR of A rows).
+struct GatePlane {
+    int M = -1;
+    uint32_t *words = nullptr;   // m x NW
+};
+
+// Scratch memory of one query batch (owned by the index, grown on demand).
+struct Workspace {
+    int64_t cap_q = 0, cap_vq = 0;
+    int cap_C = 0, cap_A = 0;
+    float *qvec = nullptr;        // staged query vectors (host input)   cap_vq x d
+    int64_t *qoff = nullptr;      // query offsets, batch-relative       cap_q + 1
+    uint16_t *qpos = nullptr;     // query codes                         cap_vq x L
+    uint32_t *sq = nullptr;       // query sketches                      cap_q x W
+    uint16_t *plist = nullptr;    // top-A positions                     cap_q x cap_A
+    uint16_t *h = nullptr;        // Hamming scores                      cap_q x N
+    uint32_t *hist = nullptr;     // histogram of h                      cap_q x (m + 1)
+    int32_t *thr = nullptr;       // per query: H*, n_lt, take_eq, n_sel cap_q x 4
+    int32_t *chunk = nullptr;     // per (query, chunk): lt, eq, eq_before, out_off
+    int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
+    float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
+    int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
+    float *out_dist = nullptr;
+    int cap_k = 0;
+};
+
+}  // namespace bvss
+
+struct bvss_index {
+    bvss_params p;
+    int device = 0;
+    int64_t n_sets = 0, n_vec = 0;
+    int W = 0;                   // m / 32 words per code or sketch
+    int64_t NW = 0;              // ceil(n_sets / 32) words per gate-plane row
+    float *vec = nullptr;        // n_vec x d FP32 (set-contiguous)
+    float *vnorm = nullptr;      // n_vec squared norms (FP32)
+    int64_t *set_off = nullptr;  // n_sets + 1
+    uint16_t *proj = nullptr;    // m x F
+    uint16_t *codes = nullptr;   // n_vec x L, ascending positions
+    uint32_t *sketch = nullptr;  // n_sets x W
+    uint8_t *count = nullptr;    // m x n_sets, position-major, saturated at 255
+    int *flag = nullptr;         // device status word (build-time checks)
+    bvss::GatePlane planes[bvss::kMaxPlanes];
+    int n_planes = 0;
+    bvss::Workspace ws;
+    int64_t *off_host[bvss::kOffRing] = {};     // pinned, batch-relative offsets
+    cudaEvent_t off_event[bvss::kOffRing] = {}; // last copy out of each slot
+    int off_next = 0;
+    int64_t off_cap = 0;
+    // per-stage profiling: kProfEvents events per batch, summed on read
+    bool prof_on = false;
+    cudaEvent_t *prof_ev = nullptr;
+    int64_t prof_cap = 0, prof_used = 0;
+    double prof_ms[BVSS_N_STAGES] = {};
+    int64_t prof_batches = 0;
+};
+
+namespace bvss {
+
+// ---- encode.cu --------------------------------------------------------------
+// FlyHash (Def. 7): pos[v] = ascending L winners, mask[v] = code bits.
+cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj,
+                          int m, int F, int L, uint16_t *pos, uint32_t *mask,
+                          cudaStream_t st);
+// Alg. 6 lines 1-4 for n_q query sets (codes qpos, offsets qoff relative to qpos).
+cudaError_t launch_query_prep(const uint16_t *qpos, const int64_t *qoff, int n_q,
+                              int m, int L, int A, uint32_t *sq, uint16_t *plist,
+                              int32_t *cq_trace, cudaStream_t st);
+
+// ---- filters.cu -------------------------------------------------------------
+cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream_t st);
+cudaError_t launch_norms(const float *x, int64_t n, int d, float *norm, cudaStream_t st);
+cudaError_t launch_build_filters(const uint16_t *codes, const int64_t *set_off,
+                                 int64_t n_sets, int m, int L, uint32_t *sketch,
+                                 uint8_t *count, cudaStream_t st);
+cudaError_t launch_gate_plane(const uint8_t *count, int m, int64_t n_sets, int64_t NW,
+                              int M, uint32_t *plane, cudaStream_t st);
+// gathers write zeros for ids outside [0, n_sets)
+cudaError_t launch_gather_sketches(const uint32_t *sketch, int W, int64_t n_sets,
+                                   const int64_t *ids, int64_t n, uint32_t *out,
+                                   cudaStream_t st);
+cudaError_t launch_gather_counts(const uint8_t *count, int m, int64_t n_sets,
+                                 const int64_t *ids, int64_t n, uint8_t *out,
+                                 cudaStream_t st);
+
+// ---- scan.cu ----------------------------------------------------------------
+// Alg. 6 lines 5-12: h[q][i] = popc(S_Q ^ S_i) for sets passing the gate.
+// gate_mode: 0 = every set passes (M = 0), 1 = gate planes, 2 = no set passes.
+// h rows have stride hs (a multiple of 64 elements).
+cudaError_t launch_scan(const uint32_t *sketch, int64_t n_sets, int W,
+                        const uint32_t *plane, int64_t NW, int gate_mode,
+                        const uint32_t *sq, const uint16_t *plist, int A, int n_q,
+                        uint16_t *h, int64_t hs, cudaStream_t st);
+
+// ---- select.cu --------------------------------------------------------------
+// Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.
+cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, int n_q,
+                          int C, uint32_t *hist, int32_t *thr, int32_t *chunk,
+                          int32_t *cand, cudaStream_t st);
+
+// ---- refine.cu --------------------------------------------------------------
+// Alg. 6 lines 19-23: exact Hausdorff of each candidate, then top-k.
+cudaError_t launch_refine(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
+                          const float *vec, const float *vnorm, const int64_t *set_off,
+                          int d, const int32_t *cand, const int32_t *thr, int C,
+                          float *cand_dist, cudaStream_t st);
+// also pads cand_dist[q][n_sel..C) with +inf
+cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *thr,
+                        int n_q, int C, int k, int64_t *out_ids, float *out_dist,
+                        cudaStream_t st);
+
+// ---- shared device helpers ---------------------------------------------------
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace bvss

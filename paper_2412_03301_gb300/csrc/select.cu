@@ -1,0 +1,230 @@
+// select.cu -- the candidate stage of Alg. 6 (lines 10-18) of arXiv 2412.03301.
+//
+// The bounded max-heap over (Hamming distance, set id) keeps the T smallest
+// pairs of F1.  Here it is computed as an exact threshold select over the
+// scores of all sets:
+//   1. histogram of h over [0, m] per query                    (k_hist)
+//   2. H* = smallest value whose cumulative count reaches
+//      C' = min(C, |F1|); sets with h < H* all qualify, and the
+//      first (C' - #{h < H*}) sets with h == H* in id order      (k_thresh)
+//   3. per chunk of sets: counts of h < H* and h == H*          (k_count)
+//   4. per query: exclusive scans over chunks                     (k_offsets)
+//   5. stable compaction in id order                              (k_write)
+// The result lists the C' candidate ids in ascending id order, -1 padded.
+#include "block_util.cuh"
+#include "bvss_internal.cuh"
+
+namespace bvss {
+
+namespace {
+
+constexpr int kSelThreads = 256;
+
+__global__ void __launch_bounds__(kSelThreads)
+k_hist(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs, int m,
+       uint32_t *__restrict__ hist) {
+    extern __shared__ uint32_t sh[];   // m + 1 bins
+    const int q = blockIdx.y;
+    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
+    const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    for (int b = threadIdx.x; b <= m; b += kSelThreads) sh[b] = 0;
+    __syncthreads();
+    const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+    for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
+        const uint4 v = row4[i8];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t val = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
+            if (i8 * 8 + e < end && val != kGatedOut) atomicAdd(&sh[val], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t *hq = hist + (int64_t)q * (m + 1);
+    for (int b = threadIdx.x; b <= m; b += kSelThreads)
+        if (sh[b]) atomicAdd(&hq[b], sh[b]);
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+k_thresh(const uint32_t *__restrict__ hist, int m, int C, int32_t *__restrict__ thr,
+         int32_t *__restrict__ cand) {
+    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    __shared__ int res[4];
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const uint32_t *hq = hist + (int64_t)q * (m + 1);
+    const int nb = m + 1;
+    const int B = (nb + kSelThreads - 1) / kSelThreads;
+    const int b0 = tid * B, b1 = min(nb, b0 + B);
+    int s = 0;
+    for (int b = b0; b < b1; ++b) s += (int)hq[b];
+    int tot;
+    const int excl = block_excl_scan<kSelThreads>(s, scan_sh, &tot);
+    const int cp = min(C, tot);
+    if (tid == 0) {
+        res[0] = -1;
+        res[1] = 0;
+        res[2] = 0;
+        res[3] = cp;
+    }
+    __syncthreads();
+    if (cp > 0 && excl < cp && excl + s >= cp) {
+        int cum = excl;
+        for (int b = b0; b < b1; ++b) {
+            const int c = (int)hq[b];
+            if (cum + c >= cp) {
+                res[0] = b;
+                res[1] = cum;
+                res[2] = cp - cum;
+                break;
+            }
+            cum += c;
+        }
+    }
+    __syncthreads();
+    if (tid < 4) thr[q * 4 + tid] = res[tid];
+    for (int j = cp + tid; j < C; j += kSelThreads) cand[(int64_t)q * C + j] = -1;
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
+        const int32_t *__restrict__ thr, int32_t *__restrict__ chunk) {
+    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    const int q = blockIdx.y;
+    const int n_chunks = gridDim.x;
+    const int H = thr[q * 4];
+    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
+    const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    int lt = 0, eq = 0;
+    if (H >= 0) {
+        const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+        for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
+            const uint4 v = row4[i8];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int val = (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
+                const bool in = i8 * 8 + e < end;
+                lt += in && val < H;
+                eq += in && val == H;
+            }
+        }
+    }
+    int tl, te;
+    block_excl_scan<kSelThreads>(lt, scan_sh, &tl);
+    block_excl_scan<kSelThreads>(eq, scan_sh, &te);
+    if (threadIdx.x == 0) {
+        int32_t *o = chunk + ((int64_t)q * n_chunks + blockIdx.x) * 4;
+        o[0] = tl;
+        o[1] = te;
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+k_offsets(const int32_t *__restrict__ thr, int n_chunks, int32_t *__restrict__ chunk) {
+    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    const int q = blockIdx.x;
+    const int take = thr[q * 4 + 2];
+    int run_eq = 0, run_sel = 0;
+    for (int base = 0; base < n_chunks; base += kSelThreads) {
+        const int c = base + threadIdx.x;
+        int32_t *o = chunk + ((int64_t)q * n_chunks + c) * 4;
+        int lt = 0, eq = 0;
+        if (c < n_chunks) {
+            lt = o[0];
+            eq = o[1];
+        }
+        int te;
+        const int ex_eq = block_excl_scan<kSelThreads>(eq, scan_sh, &te);
+        const int eqb = run_eq + ex_eq;
+        const int sel = lt + max(0, min(take - eqb, eq));
+        int ts;
+        const int ex_sel = block_excl_scan<kSelThreads>(sel, scan_sh, &ts);
+        if (c < n_chunks) {
+            o[2] = eqb;
+            o[3] = run_sel + ex_sel;
+        }
+        run_eq += te;
+        run_sel += ts;
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
+        const int32_t *__restrict__ thr, const int32_t *__restrict__ chunk, int C,
+        int32_t *__restrict__ cand) {
+    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    const int q = blockIdx.y;
+    const int n_chunks = gridDim.x;
+    const int H = thr[q * 4];
+    if (H < 0) return;   // uniform over the CTA
+    const int take = thr[q * 4 + 2];
+    const int32_t *o = chunk + ((int64_t)q * n_chunks + blockIdx.x) * 4;
+    const int eqb = o[2];
+    const int off = o[3];
+    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
+    const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+    int32_t *out = cand + (int64_t)q * C;
+    int run_eq = 0, run_sel = 0;
+    for (int64_t r0 = c0; r0 < end; r0 += kSelThreads * 8) {
+        const int64_t i0 = r0 + threadIdx.x * 8;
+        int val[8];
+        if (i0 < end) {
+            const uint4 v = row4[i0 / 8];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                val[e] = i0 + e < end ? (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu) : 0xFFFF;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) val[e] = 0xFFFF;
+        }
+        int n_lt = 0, n_eq = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            n_lt += val[e] < H;
+            n_eq += val[e] == H;
+        }
+        int te;
+        const int ex_eq = block_excl_scan<kSelThreads>(n_eq, scan_sh, &te);
+        int rank = eqb + run_eq + ex_eq;   // id-order rank of my first tie
+        const int n_sel = n_lt + max(0, min(take - rank, n_eq));
+        int ts;
+        const int ex_sel = block_excl_scan<kSelThreads>(n_sel, scan_sh, &ts);
+        int pos = off + run_sel + ex_sel;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            bool s = val[e] < H;
+            if (val[e] == H) {
+                s = rank < take;
+                ++rank;
+            }
+            if (s && pos < C) out[pos++] = (int32_t)(i0 + e);
+        }
+        run_eq += te;
+        run_sel += ts;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, int n_q, int C,
+                          uint32_t *hist, int32_t *thr, int32_t *chunk, int32_t *cand,
+                          cudaStream_t st) {
+    if (n_q <= 0) return cudaSuccess;
+    const int n_chunks = (int)((n_sets + kSelChunk - 1) / kSelChunk);
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n_q * (m + 1), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(uint32_t) * (size_t)(m + 1);
+    e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 g2(n_chunks, n_q);
+    k_hist<<<g2, kSelThreads, smem, st>>>(h, n_sets, hs, m, hist);
+    k_thresh<<<n_q, kSelThreads, 0, st>>>(hist, m, C, thr, cand);
+    k_count<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk);
+    k_offsets<<<n_q, kSelThreads, 0, st>>>(thr, n_chunks, chunk);
+    k_write<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk, C, cand);
+    return cudaGetLastError();
+}
+
+}  // namespace bvss

@@ -1,0 +1,179 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Codes, filters, query filters, gate, Hamming scores and candidate lists are
+compared bit for bit; Hausdorff distances within 1e-5 relative of the FP64
+oracle (on these grid-valued inputs the FP32 sums are exact, so the only
+difference is the final square root's rounding); result ids exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_03301_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def _np(t, dtype=None):
+    a = t.detach().cpu().numpy()
+    return a.view(dtype) if dtype is not None else a
+
+
+@pytest.fixture(scope="module")
+def bv():
+    from paper_2412_03301_gb300 import build, bvss
+    build.build()
+    bvss.load()
+    return bvss
+
+
+def _workload(n_sets, lo, hi, d, K, nq, qlo, qhi, m, F, seed):
+    return datagen.workload(n_sets=n_sets, size_lo=lo, size_hi=hi, d=d, n_components=K,
+                            n_queries=nq, q_lo=qlo, q_hi=qhi, m=m, fanin=F, seed=seed)
+
+
+class Case:
+    """A database built both ways: the CUDA index and the oracle index."""
+
+    def __init__(self, bv, orc, w, L):
+        self.w = w
+        self.L = L
+        self.vec = w["vectors"].numpy()
+        self.qvec = w["q_vectors"].numpy()
+        self.ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=L)
+        self.orc_ix = orc.Index(self.vec, w["offsets"], w["proj"], L)
+        self.qv_cuda = w["q_vectors"].cuda()
+
+
+@pytest.fixture(scope="module")
+def small(bv, orc):
+    s = datagen.SMALL
+    w = _workload(s["n_sets"], s["size_lo"], s["size_hi"], s["d"], s["n_components"],
+                  s["n_queries"], s["q_lo"], s["q_hi"], s["m"], s["fanin"], seed=0)
+    return Case(bv, orc, w, s["L"])
+
+
+def test_database_codes(bv, small):
+    got = _np(bv.bvss_get_codes(small.ix, 0, small.ix.n_vectors), np.uint16)
+    assert np.array_equal(got, small.orc_ix.pos)
+    pos, mask = bv.bvss_encode(small.ix, torch.from_numpy(small.vec[:3000]).cuda())
+    assert np.array_equal(_np(pos, np.uint16), small.orc_ix.pos[:3000])
+    assert np.array_equal(_np(mask, np.uint32), small.orc_ix.mask[:3000])
+
+
+def test_database_filters(bv, small):
+    ids = torch.arange(small.ix.n_sets)
+    sk = _np(bv.bvss_get_sketches(small.ix, ids), np.uint32)
+    assert np.array_equal(sk, small.orc_ix.sketch)
+    cnt = _np(bv.bvss_get_counts(small.ix, ids))
+    assert np.array_equal(cnt, small.orc_ix.count.T)
+
+
+def _check_query(bv, orc, case, k, C, A, M, nq=None):
+    w = case.w
+    qo = w["q_offsets"] if nq is None else w["q_offsets"][:nq + 1]
+    nq = qo.shape[0] - 1
+    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M)
+    torch.cuda.synchronize()
+    qpos = _np(t["qpos"], np.uint16)
+    h = _np(t["h"], np.uint16)
+    cand = _np(t["cand"])
+    ncand = _np(t["n_cand"])
+    cdist = _np(t["cand_dist"])
+    ids, dist = _np(t["ids"]), _np(t["dist"])
+    for q in range(nq):
+        Q = case.qvec[qo[q]:qo[q + 1]]
+        r = orc.query(case.orc_ix, Q, k=k, C=C, A=A, M=M)
+        assert np.array_equal(qpos[qo[q]:qo[q + 1]], r["qpos"]), q
+        assert np.array_equal(_np(t["cq"])[q], r["cq"]), q
+        assert np.array_equal(_np(t["sq"], np.uint32)[q], r["sq"]), q
+        assert np.array_equal(_np(t["plist"], np.uint16)[q], r["plist"]), q
+        want_h = np.where(r["gate"] == 1, r["h"], 0xFFFF)
+        assert np.array_equal(h[q].astype(np.int64), want_h.astype(np.int64)), q
+        n = int(ncand[q])
+        assert n == r["cand"].shape[0], q
+        assert np.array_equal(cand[q, :n], r["cand"]), q
+        assert np.all(cand[q, n:] == -1)
+        np.testing.assert_allclose(cdist[q, :n], r["cand_dist"], rtol=RTOL, atol=0)
+        assert np.all(np.isinf(cdist[q, n:]))
+        assert ids[q].tolist() == r["ids"].tolist(), q
+        fin = np.isfinite(r["dist"])
+        np.testing.assert_allclose(dist[q][fin], r["dist"][fin], rtol=RTOL, atol=0)
+        assert np.all(np.isinf(dist[q][~fin]))
+
+
+def test_query_parity_default(bv, orc, small):
+    s = datagen.SMALL
+    _check_query(bv, orc, small, k=s["k"], C=s["C"], A=3, M=1)
+
+
+def test_query_results_without_trace_match(bv, small):
+    s = datagen.SMALL
+    w = small.w
+    t = bv.bvss_query_trace(small.ix, small.qv_cuda, w["q_offsets"], k=10, C=s["C"], A=3, M=1)
+    ids, dist = bv.bvss_query(small.ix, small.qv_cuda, w["q_offsets"], k=10, C=s["C"], A=3, M=1)
+    assert torch.equal(ids, t["ids"]) and torch.equal(dist, t["dist"])
+    # host buffers in and out give the same answer
+    hq = w["q_vectors"].pin_memory()
+    hi = torch.empty_like(ids, device="cpu").pin_memory()
+    hd = torch.empty_like(dist, device="cpu").pin_memory()
+    bv.bvss_query(small.ix, hq, w["q_offsets"], k=10, C=s["C"], A=3, M=1, out_ids=hi,
+                  out_dist=hd)
+    assert torch.equal(hi, ids.cpu()) and torch.equal(hd, dist.cpu())
+
+
+@pytest.mark.parametrize("A,M,C", [(1, 1, 200), (3, 0, 200), (3, 2, 50), (32, 1, 200),
+                                   (3, 300, 200), (3, 1, 2000), (2, 1, 10)])
+def test_query_parity_knobs(bv, orc, small, A, M, C):
+    _check_query(bv, orc, small, k=10, C=C, A=A, M=M, nq=25)
+
+
+def test_edge_shapes(bv, orc):
+    """Single-vector sets and queries, duplicate sets, a ragged set count, m = 128."""
+    w = _workload(77, 1, 3, 16, 8, 9, 1, 4, 128, 3, seed=4)
+    # set 5 duplicates set 2 exactly, so their distances tie and ids decide
+    off = w["offsets"]
+    vec = w["vectors"].clone()
+    n2 = off[3] - off[2]
+    sizes = np.diff(off)
+    sizes[5] = n2
+    off2 = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    parts = [vec[off[i]:off[i + 1]] if i != 5 else vec[off[2]:off[3]] for i in range(77)]
+    w["vectors"] = torch.cat(parts).contiguous()
+    w["offsets"] = off2
+    case = Case(bv, orc, w, 5)
+    for A, M, C, k in ((3, 1, 20, 5), (5, 0, 77, 10), (1, 2, 8, 8), (2, 1, 100, 3)):
+        _check_query(bv, orc, case, k=k, C=C, A=A, M=M)
+
+
+def test_large_code_length(bv, orc):
+    """m = 8192 (two sketch chunks per lane) and L = 200 with fan-in 1."""
+    w = _workload(300, 2, 6, 64, 16, 6, 2, 5, 8192, 1, seed=6)
+    case = Case(bv, orc, w, 200)
+    got = _np(bv.bvss_get_codes(case.ix, 0, case.ix.n_vectors), np.uint16)
+    assert np.array_equal(got, case.orc_ix.pos)
+    _check_query(bv, orc, case, k=7, C=40, A=4, M=1)
+
+
+def test_invalid_query_arguments(bv, small):
+    w = small.w
+    for kw in (dict(k=0, C=10), dict(k=20, C=10), dict(k=5, C=10, A=0),
+               dict(k=5, C=10, A=33), dict(k=5, C=10, M=-1), dict(k=5, C=20000)):
+        with pytest.raises(bv.BvssError) as e:
+            bv.bvss_query(small.ix, small.qv_cuda, w["q_offsets"], **kw)
+        assert e.value.code == bv.BVSS_EINVAL
+    bad = w["q_offsets"].copy()
+    bad[3] = bad[2]
+    with pytest.raises(bv.BvssError):
+        bv.bvss_query(small.ix, small.qv_cuda, bad, k=5, C=10)
+
+
+def test_nonfinite_database_rejected(bv):
+    x = torch.zeros(8, 8, device="cuda")
+    x[3, 2] = float("nan")
+    proj = datagen.projection(8, 128, 2, seed=1)
+    with pytest.raises(bv.BvssError) as e:
+        bv.bvss_build(x, np.array([0, 4, 8]), proj, wta_l=4)
+    assert e.value.code == bv.BVSS_EINVAL
