@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large", "small"], default="large")
+    ap.add_argument("--workload", choices=["large", "small", "profile"], default="large",
+                    help="large: the 1M-set workload; small: the 2000-set test case; "
+                         "profile: large-case shapes at 120k sets and 100 query sets, a few GB "
+                         "on the device, for profiler captures")
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--cpu-sample-sets", type=int, default=2000)
     ap.add_argument("--cpu-sample-queries", type=int, default=20)
@@ -57,7 +60,9 @@ def parse():
 
 def workload_cfg(name):
     from paper_2412_03301_gb300 import datagen
-    c = dict(datagen.LARGE if name == "large" else datagen.SMALL)
+    c = dict(datagen.SMALL if name == "small" else datagen.LARGE)
+    if name == "profile":
+        c["n_sets"], c["n_queries"] = 120_000, 100
     c["A"], c["M"] = 3, 1
     return c
 
