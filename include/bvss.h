@@ -187,6 +187,42 @@ int bvss_profile_enable(bvss_index *ix, int on);
  * reset != 0 clears the sums afterwards. */
 int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int reset);
 
+/*
+ * bvss_select_noalloc -- the candidate select of bvss_query (the min(C, |F1|)
+ * smallest (Hamming, id) pairs, listed by ascending id) for callers that
+ * cannot allocate GPU memory.  The paper has no counterpart: it exists for
+ * programs in which cudaMalloc is not an option, for example a host process
+ * whose device memory is already reserved in full by another framework's
+ * caching allocator, or a latency-bound serving loop that must not call
+ * cudaMalloc / cudaFree (which can synchronise the whole device).  It calls
+ * neither, nor any allocating library routine: its scratch memory is one
+ * fixed array of about 1.6 MB compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   h          device, n_queries rows of h_stride uint16 Hamming scores
+ *              (0xFFFF = set outside F1), 16-byte aligned; the layout of
+ *              bvss_trace.h with rows padded to h_stride
+ *   n_sets     1 .. BVSS_NOALLOC_MAX_SETS
+ *   h_stride   row stride in elements, >= n_sets, multiple of 8
+ *   m          code length (largest valid score), 1 .. BVSS_NOALLOC_MAX_M
+ *   n_queries  0 .. BVSS_NOALLOC_MAX_QUERIES
+ *   C          candidate budget, 1 .. BVSS_MAX_C
+ *   cand       device, n_queries x C int32: ids ascending, -1 padded
+ *   n_cand     device, n_queries int32 (may be NULL): min(C, |F1|)
+ * Sizes beyond the limits return BVSS_EINVAL with a message.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind (the call
+ * clears what has to start at zero), so calls that overlap on the GPU --
+ * on two streams, or from two host threads -- race and must be serialised
+ * by the caller.
+ */
+#define BVSS_NOALLOC_MAX_QUERIES 32
+#define BVSS_NOALLOC_MAX_M 8192
+#define BVSS_NOALLOC_MAX_SETS 16777216LL
+int bvss_select_noalloc(const uint16_t *h, int64_t n_sets, int64_t h_stride, int32_t m,
+                        int32_t n_queries, int32_t C, int32_t *cand, int32_t *n_cand,
+                        void *stream);
+
 /* Release an index and all its device memory (NULL is a no-op).  Work that
  * uses the index must have finished. */
 void bvss_free(bvss_index *ix);

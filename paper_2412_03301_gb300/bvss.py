@@ -58,6 +58,8 @@ SYMBOLS = {
     "bvss_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bvss_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(_c_i64), ctypes.c_int]),
+    "bvss_select_noalloc": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i32, _c_i32, _c_i32, _vp,
+                                           _vp, _vp]),
     "bvss_free": (None, [_vp]),
     "bvss_last_error": (ctypes.c_char_p, []),
 }
@@ -255,6 +257,25 @@ def bvss_get_counts(ix: Index, ids: torch.Tensor, stream=None):
     _check(lib.bvss_get_counts(ix.handle, _dptr(ids), ids.shape[0], _dptr(out),
                                _stream(stream)))
     return out
+
+
+def bvss_select_noalloc(h: torch.Tensor, n_sets: int, m: int, C: int, cand=None,
+                        n_cand=None, stream=None):
+    """Candidate select without any GPU allocation inside the library.
+
+    For callers that cannot call cudaMalloc (device memory fully reserved by
+    another allocator, or a loop that must not synchronise the device).
+    h: (n_q, h_stride) int16 CUDA tensor holding uint16 scores, 0xFFFF for
+    sets outside F1.  Returns (cand (n_q, C) int32, n_cand (n_q,) int32);
+    pass preallocated tensors to keep the call allocation-free end to end."""
+    nq, hs = h.shape
+    if cand is None:
+        cand = torch.empty((nq, C), dtype=torch.int32, device=h.device)
+    if n_cand is None:
+        n_cand = torch.empty((nq,), dtype=torch.int32, device=h.device)
+    _check(load().bvss_select_noalloc(_dptr(h), n_sets, hs, m, nq, C, _dptr(cand),
+                                      _dptr(n_cand), _stream(stream)))
+    return cand, n_cand
 
 
 STAGES = ("encode", "scan", "select", "refine", "topk")

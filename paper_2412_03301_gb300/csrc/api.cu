@@ -374,6 +374,18 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
 
 }  // namespace
 
+namespace bvss {
+
+int record_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace bvss
+
 extern "C" {
 
 int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,

@@ -128,6 +128,10 @@ cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *th
                         int n_q, int C, int k, int64_t *out_ids, float *out_dist,
                         cudaStream_t st);
 
+// ---- api.cu -------------------------------------------------------------------
+// Records a message for bvss_last_error() on this thread and returns code.
+int record_error(int code, const char *fmt, ...);
+
 // ---- shared device helpers ---------------------------------------------------
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

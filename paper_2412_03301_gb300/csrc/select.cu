@@ -11,6 +11,8 @@
 //   4. per query: exclusive scans over chunks                     (k_offsets)
 //   5. stable compaction in id order                              (k_write)
 // The result lists the C' candidate ids in ascending id order, -1 padded.
+#include <mutex>
+
 #include "block_util.cuh"
 #include "bvss_internal.cuh"
 
@@ -227,4 +229,93 @@ cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Candidate select that allocates nothing (bvss_select_noalloc).
+//
+// Its scratch -- the per-query histograms, thresholds and per-chunk counts
+// that launch_select needs -- lives in one file-scope device array of fixed
+// size instead of memory obtained from cudaMalloc.  Every GPU that loads the
+// library holds this array until the process exits.  Host code must not pass
+// the array's name to a kernel (on the host it is only a stand-in); the
+// device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxQ = 32;
+constexpr int kNoAllocMaxM = 8192;
+constexpr int kNoAllocMaxChunks = 1024;
+constexpr size_t kNoAllocHistWords = (size_t)kNoAllocMaxQ * (kNoAllocMaxM + 1);
+constexpr size_t kNoAllocThrWords = (size_t)kNoAllocMaxQ * 4;
+constexpr size_t kNoAllocChunkWords = (size_t)kNoAllocMaxQ * kNoAllocMaxChunks * 4;
+constexpr size_t kNoAllocWords = kNoAllocHistWords + kNoAllocThrWords + kNoAllocChunkWords;
+constexpr int kNoAllocMaxDevices = 64;
+
+static_assert(BVSS_NOALLOC_MAX_QUERIES == kNoAllocMaxQ, "header limit");
+static_assert(BVSS_NOALLOC_MAX_M == kNoAllocMaxM, "header limit");
+static_assert(BVSS_NOALLOC_MAX_SETS == (int64_t)kNoAllocMaxChunks * kSelChunk, "header limit");
+
+static __device__ __align__(256) uint32_t g_select_scratch[kNoAllocWords];
+
+std::mutex g_scratch_mu;
+uint32_t *g_scratch_ptr[kNoAllocMaxDevices] = {};
+
+// device address of g_select_scratch on the current device (looked up once)
+cudaError_t scratch_for_current_device(uint32_t **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_select_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace bvss
+
+extern "C" int bvss_select_noalloc(const uint16_t *h, int64_t n_sets, int64_t h_stride,
+                                   int32_t m, int32_t n_queries, int32_t C, int32_t *cand,
+                                   int32_t *n_cand, void *stream) {
+    using namespace bvss;
+    if (n_queries < 0 || n_queries > kNoAllocMaxQ)
+        return record_error(BVSS_EINVAL, "bvss_select_noalloc: n_queries = %d, limit %d",
+                            n_queries, kNoAllocMaxQ);
+    if (m < 1 || m > kNoAllocMaxM)
+        return record_error(BVSS_EINVAL, "bvss_select_noalloc: m = %d, limit %d", m, kNoAllocMaxM);
+    if (n_sets < 1 || n_sets > (int64_t)kNoAllocMaxChunks * kSelChunk)
+        return record_error(BVSS_EINVAL, "bvss_select_noalloc: n_sets = %lld, limit %lld",
+                            (long long)n_sets, (long long)kNoAllocMaxChunks * kSelChunk);
+    if (h_stride < n_sets || h_stride % 8 != 0)
+        return record_error(BVSS_EINVAL,
+                            "bvss_select_noalloc: h_stride must be >= n_sets and a multiple of 8");
+    if (C < 1 || C > BVSS_MAX_C)
+        return record_error(BVSS_EINVAL, "bvss_select_noalloc: C = %d, need 1..%d", C, BVSS_MAX_C);
+    if (n_queries == 0) return BVSS_OK;
+    if (!h || !cand || (reinterpret_cast<uintptr_t>(h) & 15) != 0)
+        return record_error(BVSS_EINVAL, "bvss_select_noalloc: h must be 16-byte aligned, "
+                                         "h and cand non-NULL");
+    uint32_t *scratch = nullptr;
+    cudaError_t e = scratch_for_current_device(&scratch);
+    if (e != cudaSuccess)
+        return record_error(BVSS_ECUDA, "bvss_select_noalloc: scratch lookup failed: %s",
+                            cudaGetErrorString(e));
+    uint32_t *hist = scratch;
+    int32_t *thr = reinterpret_cast<int32_t *>(scratch + kNoAllocHistWords);
+    int32_t *chunk = thr + kNoAllocThrWords;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // launch_select clears the histograms it uses before counting
+    e = launch_select(h, n_sets, h_stride, m, n_queries, C, hist, thr, chunk, cand, st);
+    if (e == cudaSuccess && n_cand)
+        e = cudaMemcpy2DAsync(n_cand, sizeof(int32_t), thr + 3, 4 * sizeof(int32_t),
+                              sizeof(int32_t), n_queries, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess)
+        return record_error(BVSS_ECUDA, "bvss_select_noalloc: %s", cudaGetErrorString(e));
+    return BVSS_OK;
+}
