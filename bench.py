@@ -231,6 +231,80 @@ def oracle_description(c, n_sets_s, n_q):
             "candidate x C=%d" % (n_sets_s, c["n_sets"], n_q, c["n_sets"], n_sets_s, c["C"]))
 
 
+# --------------------------------------------------------------------------
+# roofline
+# --------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def traffic_per_unit(kernel):
+    """DRAM bytes per unit of work from profiles/traffic.md, if the kernel's
+    source still has the SHA-256 the capture was taken with (else None)."""
+    import hashlib
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.md")):
+            f = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(f) >= 5 and f[0] == kernel:
+                src = os.path.join(ROOT, f[1])
+                sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+                return float(f[3]) if sha == f[2] else None
+    except Exception:
+        return None
+    return None
+
+
+def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
+    """Roofline of the dominant kernel (scan or refine) of the timed region.
+
+    Each kernel has an ALU roof and an HBM roof; the one with the longer time at
+    peak binds.  scan: 32-bit popcounts = (query, gated set) pairs x m/32 at
+    152 SMs x 16/clk x 2070 MHz; bytes = sketch matrix once + A gate-plane words
+    per (query, 32 sets) + the h scores written.  refine: FLOPs = 2 x (query
+    vector, candidate vector) pairs x d at 152 x 128 FP32 lanes x 2 x 2070 MHz;
+    bytes = candidate rows x d x 4."""
+    hbm, hbm_basis = measured_peaks()
+    per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
+    clock = SM_MAX_MHZ * 1e6
+    kern = {
+        "scan": dict(
+            name="k_scan", t=per["scan"],
+            alu=(gated_pairs * (c["m"] // 32), SM_COUNT * POPC_PER_CLK_PER_SM * clock, "Tpopc/s",
+                 "152 SMs x 16 popc/clk x 2070 MHz (nominal)"),
+            hbm_bytes=c["n_sets"] * c["m"] / 8 + nq * c["A"] * c["n_sets"] / 8
+            + nq * c["n_sets"] * 2, units=None),
+        "refine": dict(
+            name="k_refine", t=per["refine"],
+            alu=(2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock, "TFLOP/s",
+                 "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)"),
+            hbm_bytes=cand_rows * c["d"] * 4.0, units=cand_rows),
+    }
+    dom = max(kern, key=lambda k: kern[k]["t"])
+    k = kern[dom]
+    t = k["t"] / 1e3
+    ops, peak_ops, unit, basis = k["alu"]
+    t_alu, t_hbm = ops / peak_ops, k["hbm_bytes"] / (hbm * 1e9)
+    tpu = traffic_per_unit(k["name"])
+    traffic = tpu * k["units"] if (tpu is not None and k["units"]) else None
+    if t_hbm >= t_alu:
+        ach = k["hbm_bytes"] / t / 1e9
+        return {"kernel": k["name"], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic, "algorithmic_bytes": k["hbm_bytes"],
+                "peak_basis": hbm_basis + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_basis ==
+                "of measured" else hbm_basis,
+                "alu_roof": {"achieved": ops / t / 1e12, "peak": peak_ops / 1e12, "unit": unit}}
+    ach = ops / t / 1e12
+    return {"kernel": k["name"], "bound": "alu", "achieved": ach, "peak": peak_ops / 1e12,
+            "unit": unit, "frac": ach / (peak_ops / 1e12), "traffic": traffic,
+            "peak_basis": basis, "algorithmic_bytes": k["hbm_bytes"],
+            "hbm_roof": {"achieved": k["hbm_bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s"}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -407,26 +481,7 @@ def run_ours(args, rank, world, local_rank):
                            "refine_scaled": float(parts[2])}}
 
     # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
-    per_launch = {k: v / max(1, nbatch) for k, v in stage_ms.items()}
-    dominant = max(("scan", "refine"), key=lambda s: per_launch[s])
-    clock_hz = SM_MAX_MHZ * 1e6
-    if dominant == "scan":
-        popc = gated_pairs * (c["m"] // 32)             # one 32-bit popcount per sketch word
-        achieved = popc / (per_launch["scan"] / 1e3) / 1e12
-        peak = SM_COUNT * POPC_PER_CLK_PER_SM * clock_hz / 1e12
-        roof = {"kernel": "k_scan", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
-                "units_per_launch": "%d (query, gated set) pairs x %d words" % (gated_pairs,
-                                                                              c["m"] // 32),
-                "peak_basis": "152 SMs x 16 popc/clk x 2070 MHz (nominal unit count)"}
-    else:
-        flops = 2.0 * pair_elems * c["d"]
-        achieved = flops / (per_launch["refine"] / 1e3) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_hz / 1e12
-        roof = {"kernel": "k_refine", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "units_per_launch": "%d vector pairs x d=%d" % (pair_elems, c["d"]),
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FP32 FMA)"}
+    roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
