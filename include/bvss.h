@@ -51,6 +51,8 @@ extern "C" {
 #define BVSS_EINVAL (-1)   /* an argument is out of range or inconsistent */
 #define BVSS_ENOMEM (-2)   /* a device or host allocation failed */
 #define BVSS_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+#define BVSS_ETIMEOUT (-4) /* a kernel's bounded wait gave up; reported by a later
+                              synchronising call (bvss_sync, or a call with host outputs) */
 
 /* limits of this implementation */
 #define BVSS_MAX_D 4096        /* vector dimension */
@@ -169,6 +171,17 @@ int bvss_get_sketches(const bvss_index *ix, const int64_t *ids, int64_t n,
  * ids (device, n int64) into out (device, n x m uint8, set-major). */
 int bvss_get_counts(const bvss_index *ix, const int64_t *ids, int64_t n,
                     uint8_t *out, void *stream);
+
+/* Wait for `stream`, then report device-side failures of earlier work on this
+ * index: BVSS_ETIMEOUT if a kernel's bounded wait gave up (the flag is then
+ * cleared), BVSS_ECUDA on a CUDA error, else BVSS_OK. */
+int bvss_sync(bvss_index *ix, void *stream);
+
+/* Failure-detection self-test: launches one kernel that waits, with the given
+ * limit (nanoseconds, <= 10^9), on an mbarrier that nothing completes.  The
+ * wait must give up and report, so the expected result is BVSS_ETIMEOUT with
+ * the CUDA context still usable.  Synchronises the device; allocates 4 bytes. */
+int bvss_selftest_wait_timeout(int64_t limit_ns);
 
 /* Stages of bvss_query timed by the profiler (CUDA events on the query
  * stream, recorded between the kernels of every batch). */

@@ -16,7 +16,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libbvss.so")
 
-BVSS_OK, BVSS_EINVAL, BVSS_ENOMEM, BVSS_ECUDA = 0, -1, -2, -3
+BVSS_OK, BVSS_EINVAL, BVSS_ENOMEM, BVSS_ECUDA, BVSS_ETIMEOUT = 0, -1, -2, -3, -4
 GATED_OUT = 0xFFFF
 
 _c_i32, _c_i64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
@@ -60,6 +60,8 @@ SYMBOLS = {
                                          ctypes.POINTER(_c_i64), ctypes.c_int]),
     "bvss_select_noalloc": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i32, _c_i32, _c_i32, _vp,
                                            _vp, _vp]),
+    "bvss_sync": (ctypes.c_int, [_vp, _vp]),
+    "bvss_selftest_wait_timeout": (ctypes.c_int, [_c_i64]),
     "bvss_free": (None, [_vp]),
     "bvss_last_error": (ctypes.c_char_p, []),
 }
@@ -276,6 +278,16 @@ def bvss_select_noalloc(h: torch.Tensor, n_sets: int, m: int, C: int, cand=None,
     _check(load().bvss_select_noalloc(_dptr(h), n_sets, hs, m, nq, C, _dptr(cand),
                                       _dptr(n_cand), _stream(stream)))
     return cand, n_cand
+
+
+def bvss_sync(ix: Index, stream=None):
+    """Wait for the stream; raise BvssError if a kernel's bounded wait gave up."""
+    _check(load().bvss_sync(ix.handle, _stream(stream)))
+
+
+def bvss_selftest_wait_timeout(limit_ns: int = 10_000_000) -> int:
+    """Run the bounded-wait self-test; returns the status (BVSS_ETIMEOUT expected)."""
+    return load().bvss_selftest_wait_timeout(limit_ns)
 
 
 STAGES = ("encode", "scan", "select", "refine", "topk")

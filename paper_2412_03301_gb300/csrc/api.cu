@@ -96,6 +96,7 @@ void free_index(bvss_index *ix) {
     dfree(ix->sketch);
     dfree(ix->count);
     dfree(ix->flag);
+    dfree(ix->err);
     for (int i = 0; i < ix->n_planes; ++i) dfree(ix->planes[i].words);
     free_workspace(ix->ws);
     for (int i = 0; i < kOffRing; ++i) {
@@ -223,6 +224,18 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
     return BVSS_OK;
 }
 
+// wait for the stream, then report (and clear) the device error word
+int sync_and_check(bvss_index *ix, cudaStream_t st) {
+    BVSS_CU(cudaStreamSynchronize(st));
+    int e = 0;
+    BVSS_CU(cudaMemcpy(&e, ix->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        BVSS_CU(cudaMemset(ix->err, 0, sizeof(int)));
+        return fail(BVSS_ETIMEOUT, "a kernel's bounded wait gave up (device status %d)", e);
+    }
+    return BVSS_OK;
+}
+
 // reserve kProfEvents timing events for one batch; returns their base or null
 cudaEvent_t *prof_reserve(bvss_index *ix) {
     if (ix->prof_used + kProfEvents > ix->prof_cap) {
@@ -333,8 +346,12 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
         BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
         // lines 19-23
-        BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d, w.cand,
-                              w.thr, C, w.cand_dist, st));
+        if (refine2_supported(d, max_mq, ix->max_set))
+            BVSS_CU(launch_refine2(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
+                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
+        else
+            BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
+                                  w.cand, w.thr, C, w.cand_dist, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
         int64_t *ids = ids_dev ? out_ids + b0 * k : w.out_ids;
         float *dist = dist_dev ? out_dist + b0 * k : w.out_dist;
@@ -368,7 +385,7 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
                                         sizeof(float) * nb * C, dd, st));
         }
     }
-    if (!ids_dev || !dist_dev) BVSS_CU(cudaStreamSynchronize(st));
+    if (!ids_dev || !dist_dev) return sync_and_check(ix, st);
     return BVSS_OK;
 }
 
@@ -428,6 +445,11 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         BVSS_CU(dalloc(&ix->sketch, (size_t)n_sets * ix->W));
         BVSS_CU(dalloc(&ix->count, (size_t)n_sets * p.m));
         BVSS_CU(dalloc(&ix->flag, 1));
+        BVSS_CU(dalloc(&ix->err, 1));
+        BVSS_CU(cudaMemsetAsync(ix->err, 0, sizeof(int), st));
+        for (int64_t i = 0; i < n_sets; ++i)
+            if (set_offsets[i + 1] - set_offsets[i] > ix->max_set)
+                ix->max_set = set_offsets[i + 1] - set_offsets[i];
         const cudaMemcpyKind kind =
             is_device_ptr(vectors) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         BVSS_CU(cudaMemcpyAsync(ix->vec, vectors, sizeof(float) * (size_t)nv * p.d, kind, st));
@@ -533,6 +555,27 @@ int bvss_get_counts(const bvss_index *ix, const int64_t *ids, int64_t n, uint8_t
         return fail(BVSS_EINVAL, "ids and out must be device memory");
     BVSS_CU(launch_gather_counts(ix->count, ix->p.m, ix->n_sets, ids, n, out,
                                  reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_sync(bvss_index *ix, void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    return sync_and_check(ix, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int bvss_selftest_wait_timeout(int64_t limit_ns) {
+    if (limit_ns < 0 || limit_ns > 1000000000LL)
+        return fail(BVSS_EINVAL, "limit_ns must lie in [0, 1e9]");
+    int *err = nullptr;
+    BVSS_CU(dalloc(&err, 1));
+    int e = 0;
+    cudaError_t ce = cudaMemset(err, 0, sizeof(int));
+    if (ce == cudaSuccess) ce = launch_wait_selftest(err, (uint64_t)limit_ns, 0);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+    if (ce == cudaSuccess) ce = cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (ce != cudaSuccess) return fail(BVSS_ECUDA, "selftest: %s", cudaGetErrorString(ce));
+    if (e) return fail(BVSS_ETIMEOUT, "selftest: the bounded wait gave up as intended");
     return BVSS_OK;
 }
 

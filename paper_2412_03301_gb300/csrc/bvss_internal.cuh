@@ -59,6 +59,8 @@ struct bvss_index {
     uint32_t *sketch = nullptr;  // n_sets x W
     uint8_t *count = nullptr;    // m x n_sets, position-major, saturated at 255
     int *flag = nullptr;         // device status word (build-time checks)
+    int *err = nullptr;          // device error word: set when a kernel's bounded wait gives up
+    int64_t max_set = 0;         // largest set size (vectors)
     bvss::GatePlane planes[bvss::kMaxPlanes];
     int n_planes = 0;
     bvss::Workspace ws;
@@ -123,6 +125,15 @@ cudaError_t launch_refine(const float *qvec, const int64_t *qoff, int n_q, int m
                           const float *vec, const float *vnorm, const int64_t *set_off,
                           int d, const int32_t *cand, const int32_t *thr, int C,
                           float *cand_dist, cudaStream_t st);
+// refine2.cu: the same, with candidate rows staged by TMA bulk copies
+bool refine2_supported(int d, int max_mq, int64_t max_set);
+int refine2_stages(int d, int max_mq);
+cudaError_t launch_refine2(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
+                           const float *vec, const float *vnorm, const int64_t *set_off, int d,
+                           const int32_t *cand, const int32_t *thr, int C, float *cand_dist,
+                           int *err, cudaStream_t st);
+// a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
+cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf
 cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *thr,
                         int n_q, int C, int k, int64_t *out_ids, float *out_dist,

@@ -177,3 +177,24 @@ def test_nonfinite_database_rejected(bv):
     with pytest.raises(bv.BvssError) as e:
         bv.bvss_build(x, np.array([0, 4, 8]), proj, wta_l=4)
     assert e.value.code == bv.BVSS_EINVAL
+
+
+@pytest.mark.parametrize("qlo,qhi,d", [(33, 64, 64), (65, 100, 32), (3, 9, 1024), (1, 40, 516)])
+def test_refine_paths(bv, orc, qlo, qhi, d):
+    """Query sets over one and two tiles of 32 query vectors in the TMA-staged
+    refine, and the general refine it falls back to (more than 64 query
+    vectors, or rows too wide for its shared-memory stages)."""
+    w = _workload(120, 2, 40, d, 16, 6, qlo, qhi, 256, 4, seed=9)
+    case = Case(bv, orc, w, 8)
+    _check_query(bv, orc, case, k=6, C=90, A=3, M=1)
+
+
+def test_bounded_wait_reports_timeout(bv, small):
+    """A kernel waits on an mbarrier nothing completes; its 10 ms limit must
+    run out, the status must say so, and the context must stay usable."""
+    assert bv.bvss_selftest_wait_timeout(10_000_000) == bv.BVSS_ETIMEOUT
+    assert "gave up" in bv.bvss_last_error()
+    w = small.w
+    ids, _ = bv.bvss_query(small.ix, small.qv_cuda, w["q_offsets"], k=5, C=50)
+    bv.bvss_sync(small.ix)
+    assert ids.shape == (w["q_offsets"].shape[0] - 1, 5)
