@@ -310,6 +310,8 @@ k_refine2(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 pa = (int)(cm & 0xffffull);
                 pr = (int)((cm >> 16) & 0xffffull);
             }
+            pa = min(max(pa, 0), mq - 1);
+            pr = min(max(pr, 0), s_n[c] - 1);
             const float4 *x4 = reinterpret_cast<const float4 *>(Qs + (size_t)pa * dp);
             const float4 *y4 = reinterpret_cast<const float4 *>(vec + (s_grow0[c] + pr) * d);
             float sacc = 0.0f;
