@@ -271,6 +271,9 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
     hbm, hbm_basis = measured_peaks()
     per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
     clock = SM_MAX_MHZ * 1e6
+    # the library runs the TMA-staged refine when its shared-memory stages fit
+    refine_name = ("k_refine2" if c["d"] % 4 == 0 and c["d"] <= 516 and c["q_hi"] <= 64
+                   and c["size_hi"] <= 0xffff else "k_refine")
     kern = {
         "scan": dict(
             name="k_scan", t=per["scan"],
@@ -279,7 +282,7 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
             hbm_bytes=c["n_sets"] * c["m"] / 8 + nq * c["A"] * c["n_sets"] / 8
             + nq * c["n_sets"] * 2, units=None),
         "refine": dict(
-            name="k_refine", t=per["refine"],
+            name=refine_name, t=per["refine"],
             alu=(2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock, "TFLOP/s",
                  "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)"),
             hbm_bytes=cand_rows * c["d"] * 4.0, units=cand_rows),
