@@ -272,8 +272,7 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
     per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
     clock = SM_MAX_MHZ * 1e6
     # the library runs the TMA-staged refine when its shared-memory stages fit
-    refine_name = ("k_refine2" if c["d"] % 4 == 0 and c["d"] <= 516 and c["q_hi"] <= 64
-                   and c["size_hi"] <= 0xffff else "k_refine")
+    refine_name = "k_refine_tma" if c["d"] % 4 == 0 and c["q_hi"] <= 64 else "k_refine"
     kern = {
         "scan": dict(
             name="k_scan", t=per["scan"],

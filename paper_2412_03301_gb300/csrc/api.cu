@@ -346,9 +346,9 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
         BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
         // lines 19-23
-        if (refine2_supported(d, max_mq, ix->max_set))
-            BVSS_CU(launch_refine2(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
-                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
+        if (refine_tma_supported(d, max_mq))
+            BVSS_CU(launch_refine_tma(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off,
+                                      d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
         else
             BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, st));

@@ -125,13 +125,13 @@ cudaError_t launch_refine(const float *qvec, const int64_t *qoff, int n_q, int m
                           const float *vec, const float *vnorm, const int64_t *set_off,
                           int d, const int32_t *cand, const int32_t *thr, int C,
                           float *cand_dist, cudaStream_t st);
-// refine2.cu: the same, with candidate rows staged by TMA bulk copies
-bool refine2_supported(int d, int max_mq, int64_t max_set);
-int refine2_stages(int d, int max_mq);
-cudaError_t launch_refine2(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
-                           const float *vec, const float *vnorm, const int64_t *set_off, int d,
-                           const int32_t *cand, const int32_t *thr, int C, float *cand_dist,
-                           int *err, cudaStream_t st);
+// refine_tma.cu: the same, candidate rows streamed by TMA bulk copies, one
+// pipeline per warp (query sets of at most 64 vectors)
+bool refine_tma_supported(int d, int max_mq);
+cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
+                              const float *vec, const float *vnorm, const int64_t *set_off,
+                              int d, const int32_t *cand, const int32_t *thr, int C,
+                              float *cand_dist, int *err, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf
