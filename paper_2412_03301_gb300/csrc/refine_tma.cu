@@ -221,43 +221,30 @@ k_refine_tma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         const float *St = stg + (u & 1) * kRowsT * kKCP;
         const float *qb = Qs + kc * kKC;
         const int w4 = min(kKC, d - kc * kKC) / 4;
-        // operands of step k4 + 1 are loaded while step k4's FMAs issue
-        float4 vv[8], qv[NAT][4];
-        auto load = [&](int k4, float4 (&v)[8], float4 (&qq)[NAT][4]) {
+        for (int k4 = 0; k4 < w4; ++k4) {
+            float4 vv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                v[j] = *reinterpret_cast<const float4 *>(St + (lr + 4 * j) * kKCP + 4 * k4);
+                vv[j] = *reinterpret_cast<const float4 *>(St + (lr + 4 * j) * kKCP + 4 * k4);
 #pragma unroll
-            for (int at = 0; at < NAT; ++at)
+            for (int at = 0; at < NAT; ++at) {
+                float4 qv[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    qq[at][i] = *reinterpret_cast<const float4 *>(
+                    qv[i] = *reinterpret_cast<const float4 *>(
                         qb + (size_t)(at * 32 + la + 8 * i) * dq + 4 * k4);
-        };
-        load(0, vv, qv);
-#pragma unroll 1
-        for (int k4 = 0; k4 < w4; ++k4) {
-            float4 vn[8], qnx[NAT][4];
-            load(k4 + 1 < w4 ? k4 + 1 : k4, vn, qnx);
-#pragma unroll
-            for (int at = 0; at < NAT; ++at)
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         float a = acc[at][i][j];
-                        a = fmaf(qv[at][i].x, vv[j].x, a);
-                        a = fmaf(qv[at][i].y, vv[j].y, a);
-                        a = fmaf(qv[at][i].z, vv[j].z, a);
-                        a = fmaf(qv[at][i].w, vv[j].w, a);
+                        a = fmaf(qv[i].x, vv[j].x, a);
+                        a = fmaf(qv[i].y, vv[j].y, a);
+                        a = fmaf(qv[i].z, vv[j].z, a);
+                        a = fmaf(qv[i].w, vv[j].w, a);
                         acc[at][i][j] = a;
                     }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) vv[j] = vn[j];
-#pragma unroll
-            for (int at = 0; at < NAT; ++at)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) qv[at][i] = qnx[at][i];
+            }
         }
         __syncwarp();                  // every lane is done with this stage
         if (u + 2 < total) issue(u + 2);
