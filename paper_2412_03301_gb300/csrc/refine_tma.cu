@@ -233,17 +233,23 @@ k_refine_tma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 for (int i = 0; i < 4; ++i)
                     qv[i] = *reinterpret_cast<const float4 *>(
                         qb + (size_t)(at * 32 + la + 8 * i) * dq + 4 * k4);
+                // component-major: 32 independent accumulators between dependent FMAs
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float a = acc[at][i][j];
-                        a = fmaf(qv[i].x, vv[j].x, a);
-                        a = fmaf(qv[i].y, vv[j].y, a);
-                        a = fmaf(qv[i].z, vv[j].z, a);
-                        a = fmaf(qv[i].w, vv[j].w, a);
-                        acc[at][i][j] = a;
-                    }
+                    for (int j = 0; j < 8; ++j) acc[at][i][j] = fmaf(qv[i].x, vv[j].x, acc[at][i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[at][i][j] = fmaf(qv[i].y, vv[j].y, acc[at][i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[at][i][j] = fmaf(qv[i].z, vv[j].z, acc[at][i][j]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[at][i][j] = fmaf(qv[i].w, vv[j].w, acc[at][i][j]);
             }
         }
         __syncwarp();                  // every lane is done with this stage
