@@ -26,10 +26,10 @@ namespace bvss {
 namespace {
 
 constexpr int kRowsT = 32;        // rows per tile
-constexpr int kKC = 32;           // dimensions per chunk
+constexpr int kKC = 64;           // dimensions per chunk
 constexpr int kKCP = kKC + 4;     // padded stage row (floats): bank-conflict-free reads
 constexpr int kCandW = 32;        // candidates per warp
-constexpr int kMaxWarps = 14;     // 14 x 32 threads x <= 146 registers fit the register file
+constexpr int kMaxWarps = 8;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kSmemMax = 232448;  // 227 KB opt-in limit per CTA
 
@@ -38,10 +38,8 @@ __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int q_bytes(int d, int nat) {
     return align16((32 * nat * (d + 4) + 32 * nat) * 4);
 }
-// with one tile of 32 query vectors the distance scratch D reuses the stage
-// buffer the tile's last chunk came from; with two it has its own region
 __host__ __device__ inline int warp_bytes(int nat) {
-    return align16(16 + 2 * kRowsT * kKCP * 4 + (nat == 1 ? 0 : kRowsT * (32 * nat + 1) * 4));
+    return align16(16 + 2 * kRowsT * kKCP * 4 + kRowsT * (32 * nat + 1) * 4);
 }
 
 template <int NAT>
@@ -65,9 +63,8 @@ k_refine_tma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     unsigned char *wb = smem + q_bytes(d, NAT) + warp * warp_bytes(NAT);
     uint64_t *bars = reinterpret_cast<uint64_t *>(wb);
     float *stg = reinterpret_cast<float *>(wb + 16);
-    float *const Dsep = stg + 2 * kRowsT * kKCP;
+    float *D = stg + 2 * kRowsT * kKCP;
     constexpr int DS = 32 * NAT + 1;
-    static_assert(NAT == 2 || kRowsT * DS <= kRowsT * kKCP, "D must fit a stage");
     const float INF = __int_as_float(0x7f800000);
 
     // the query set, zero rows past its end, and its squared norms
@@ -256,11 +253,8 @@ k_refine_tma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             }
         }
         __syncwarp();                  // every lane is done with this stage
-        if (kc != KCH - 1) {
-            if (u + 2 < total) issue(u + 2);
-            continue;
-        }
-        float *D = NAT == 1 ? const_cast<float *>(St) : Dsep;
+        if (u + 2 < total) issue(u + 2);
+        if (kc != KCH - 1) continue;
 
         // tile t complete: squared distances into D[row][a]
         const int nr = min(kRowsT, R - kRowsT * t);
@@ -315,8 +309,7 @@ k_refine_tma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             const long long key = ((long long)cm << 32) | ((long long)row_in << 8) | cma;
             if (key > cmax_key) cmax_key = key;
         }
-        __syncwarp();                  // D (possibly the stage buffer) is free again
-        if (u + 2 < total) issue(u + 2);
+        __syncwarp();                  // D is rewritten by the next tile
     }
     if (failed) {
         if (lane == 0) {
