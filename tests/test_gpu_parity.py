@@ -198,3 +198,11 @@ def test_bounded_wait_reports_timeout(bv, small):
     ids, _ = bv.bvss_query(small.ix, small.qv_cuda, w["q_offsets"], k=5, C=50)
     bv.bvss_sync(small.ix)
     assert ids.shape == (w["q_offsets"].shape[0] - 1, 5)
+
+
+@pytest.mark.parametrize("m", [16384, 32768])
+def test_longest_codes(bv, orc, m):
+    """Sketches long enough that the scan stages 64- or 32-set tiles."""
+    w = _workload(70, 1, 4, 32, 8, 4, 1, 4, m, 8, seed=12)
+    case = Case(bv, orc, w, 40)
+    _check_query(bv, orc, case, k=5, C=30, A=3, M=1)
