@@ -64,21 +64,35 @@ extern "C" {
 #define BVSS_MAX_QSET 128      /* vectors per query set */
 
 /* Build parameters (Def. 7 and Alg. 6's Theta minus the search knobs). */
+/* bvss_params.flags */
+#define BVSS_BUILD_BF16 1   /* also keep a BF16 copy of the vectors (2 bytes per value) for
+                               the tensor-core refine of BVSS_SEARCH_FAST; needs d % 64 == 0 */
+
 typedef struct bvss_params {
     int32_t d;       /* vector dimension, 4..BVSS_MAX_D, multiple of 4 */
     int32_t m;       /* code length b = Bloom filter length; multiple of 128, <= BVSS_MAX_M */
     int32_t fanin;   /* F: input dims summed by each output of W, 1..min(d, BVSS_MAX_FANIN) */
     int32_t wta_l;   /* L_wta: winners kept by WTA, 1..min(m, BVSS_MAX_L) */
-    int32_t flags;   /* must be 0 */
+    int32_t flags;   /* 0 or BVSS_BUILD_BF16 */
     int32_t reserved[3];
 } bvss_params;
 
 /* Search parameters of Alg. 6 (Theta's A, M, c = T) and Def. 5's k. */
+/* bvss_search.flags */
+#define BVSS_SEARCH_FAST 1  /* refine on the tensor cores: squared distances in the GEMM form
+                               from BF16 vectors with FP32 accumulation (tcgen05), the pair that
+                               attains each Hausdorff value re-scored in FP32.  Exact for inputs
+                               on the 2^-8 grid; otherwise BF16 rounding can pick a slightly
+                               different pair.  Needs an index built with BVSS_BUILD_BF16 and
+                               query sets of at most 32 vectors (larger sets use the FP32 refine) */
+
 typedef struct bvss_search {
-    int32_t k;   /* results per query set, >= 1 */
-    int32_t C;   /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
-    int32_t A;   /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
-    int32_t M;   /* minimum count; 0 lets every set through the first layer */
+    int32_t k;      /* results per query set, >= 1 */
+    int32_t C;      /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
+    int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
+    int32_t M;      /* minimum count; 0 lets every set through the first layer */
+    int32_t flags;  /* 0 or BVSS_SEARCH_FAST */
+    int32_t reserved;
 } bvss_search;
 
 typedef struct bvss_index bvss_index;   /* opaque; owns its device memory */

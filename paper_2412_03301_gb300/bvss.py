@@ -28,7 +28,12 @@ class bvss_params(ctypes.Structure):
 
 
 class bvss_search(ctypes.Structure):
-    _fields_ = [("k", _c_i32), ("C", _c_i32), ("A", _c_i32), ("M", _c_i32)]
+    _fields_ = [("k", _c_i32), ("C", _c_i32), ("A", _c_i32), ("M", _c_i32), ("flags", _c_i32),
+                ("reserved", _c_i32)]
+
+
+BVSS_BUILD_BF16 = 1
+BVSS_SEARCH_FAST = 1
 
 
 class bvss_trace(ctypes.Structure):
@@ -146,14 +151,15 @@ class Index:
 
 
 def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: int,
-               stream=None) -> Index:
+               bf16: bool = False, stream=None) -> Index:
     """Build an index (Alg. 1, 3, 4, 5). vectors: (V, d) float32, host or CUDA."""
     lib = load()
     assert vectors.dtype == torch.float32 and vectors.is_contiguous()
     off, off_p = _host_i64(set_offsets)
     proj = np.ascontiguousarray(proj, dtype=np.uint16)
     p = bvss_params(d=vectors.shape[1], m=proj.shape[0],
-                    fanin=proj.shape[1] if fanin is None else fanin, wta_l=wta_l, flags=0)
+                    fanin=proj.shape[1] if fanin is None else fanin, wta_l=wta_l,
+                    flags=BVSS_BUILD_BF16 if bf16 else 0)
     h = ctypes.c_void_p()
     dev = vectors.device if vectors.is_cuda else torch.device("cuda", torch.cuda.current_device())
     with torch.cuda.device(dev):
@@ -164,7 +170,7 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
 
 
 def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
-               M: int = 1, out_ids=None, out_dist=None, stream=None):
+               M: int = 1, fast: bool = False, out_ids=None, out_dist=None, stream=None):
     """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
 
     q_vectors and the outputs may live on the host or on the index's GPU."""
@@ -176,14 +182,14 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
         out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M)
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=BVSS_SEARCH_FAST if fast else 0)
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
 
 
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
-                     A: int = 3, M: int = 1, stream=None):
+                     A: int = 3, M: int = 1, fast: bool = False, stream=None):
     """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
 
     Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
@@ -206,7 +212,7 @@ def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C
     tr = bvss_trace(**{name: t[name].data_ptr() for name in t})
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M)
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=BVSS_SEARCH_FAST if fast else 0)
     _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                                 _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
     t["ids"] = ids

@@ -90,6 +90,8 @@ void free_index(bvss_index *ix) {
     if (!ix) return;
     dfree(ix->vec);
     dfree(ix->vnorm);
+    dfree(ix->vec16);
+    dfree(ix->vnorm16);
     dfree(ix->set_off);
     dfree(ix->proj);
     dfree(ix->codes);
@@ -120,7 +122,9 @@ int check_params(const bvss_params *p) {
                     BVSS_MAX_FANIN);
     if (p->wta_l < 1 || p->wta_l > BVSS_MAX_L || p->wta_l > p->m)
         return fail(BVSS_EINVAL, "wta_l = %d: need 1 <= L <= min(m, %d)", p->wta_l, BVSS_MAX_L);
-    if (p->flags != 0) return fail(BVSS_EINVAL, "flags must be 0");
+    if (p->flags & ~BVSS_BUILD_BF16) return fail(BVSS_EINVAL, "unknown build flags");
+    if ((p->flags & BVSS_BUILD_BF16) && p->d % 64 != 0)
+        return fail(BVSS_EINVAL, "BVSS_BUILD_BF16 needs d %% 64 == 0 (d = %d)", p->d);
     return BVSS_OK;
 }
 
@@ -270,6 +274,10 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (s->A < 1 || s->A > L || s->A > BVSS_MAX_A)
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
+    if (s->flags & ~BVSS_SEARCH_FAST) return fail(BVSS_EINVAL, "unknown search flags");
+    const bool fast = (s->flags & BVSS_SEARCH_FAST) != 0;
+    if (fast && !ix->vec16)
+        return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
     if (n_queries < 0) return fail(BVSS_EINVAL, "n_queries < 0");
     if (n_queries == 0) return BVSS_OK;
     if (!q_vectors || !out_ids || !out_dist)
@@ -346,7 +354,10 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
         BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
         // lines 19-23
-        if (refine_tma_supported(d, max_mq))
+        if (fast && refine_mma_supported(d, max_mq))
+            BVSS_CU(launch_refine_mma(qv, w.qoff, nb, ix->vec, ix->vec16, ix->vnorm16, ix->set_off,
+                                      d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
+        else if (refine_tma_supported(d, max_mq))
             BVSS_CU(launch_refine_tma(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off,
                                       d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
         else
@@ -465,6 +476,11 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         if (bad) return fail(BVSS_EINVAL, "database vectors hold non-finite values");
         // Alg. 1 over the database, then Alg. 3 / Alg. 5 from the same codes
         BVSS_CU(launch_norms(ix->vec, nv, p.d, ix->vnorm, st));
+        if (p.flags & BVSS_BUILD_BF16) {
+            BVSS_CU(dalloc(&ix->vec16, (size_t)nv * p.d));
+            BVSS_CU(dalloc(&ix->vnorm16, (size_t)nv));
+            BVSS_CU(launch_to_bf16(ix->vec, nv, p.d, ix->vec16, ix->vnorm16, st));
+        }
         BVSS_CU(launch_encode(ix->vec, nv, p.d, ix->proj, p.m, p.fanin, p.wta_l, ix->codes,
                               nullptr, st));
         BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,

@@ -2,6 +2,7 @@
 // CUDA translation units of the BioVSS++ query path (arXiv 2412.03301).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,6 +54,8 @@ struct bvss_index {
     int64_t NW = 0;              // ceil(n_sets / 32) words per gate-plane row
     float *vec = nullptr;        // n_vec x d FP32 (set-contiguous)
     float *vnorm = nullptr;      // n_vec squared norms (FP32)
+    __nv_bfloat16 *vec16 = nullptr;   // n_vec x d BF16 copy (BVSS_BUILD_BF16)
+    float *vnorm16 = nullptr;         // squared norms of the BF16 values
     int64_t *set_off = nullptr;  // n_sets + 1
     uint16_t *proj = nullptr;    // m x F
     uint16_t *codes = nullptr;   // n_vec x L, ascending positions
@@ -132,6 +135,15 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
                               const float *vec, const float *vnorm, const int64_t *set_off,
                               int d, const int32_t *cand, const int32_t *thr, int C,
                               float *cand_dist, int *err, cudaStream_t st);
+// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 32)
+bool refine_mma_supported(int d, int max_mq);
+cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
+                           cudaStream_t st);
+cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
+                              const float *vec, const __nv_bfloat16 *vec16,
+                              const float *vnorm16, const int64_t *set_off, int d,
+                              const int32_t *cand, const int32_t *thr, int C, float *cand_dist,
+                              int *err, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf

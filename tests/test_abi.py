@@ -46,7 +46,7 @@ def test_binding_covers_header():
 def test_struct_layouts_match_header():
     from paper_2412_03301_gb300 import bvss
     assert ctypes.sizeof(bvss.bvss_params) == 32
-    assert ctypes.sizeof(bvss.bvss_search) == 16
+    assert ctypes.sizeof(bvss.bvss_search) == 24
     assert ctypes.sizeof(bvss.bvss_trace) == 8 * ctypes.sizeof(ctypes.c_void_p)
     src = open(HEADER).read()
     for field in ("d", "m", "fanin", "wta_l", "flags"):

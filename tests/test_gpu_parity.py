@@ -37,12 +37,12 @@ def _workload(n_sets, lo, hi, d, K, nq, qlo, qhi, m, F, seed):
 class Case:
     """A database built both ways: the CUDA index and the oracle index."""
 
-    def __init__(self, bv, orc, w, L):
+    def __init__(self, bv, orc, w, L, bf16=False):
         self.w = w
         self.L = L
         self.vec = w["vectors"].numpy()
         self.qvec = w["q_vectors"].numpy()
-        self.ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=L)
+        self.ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=L, bf16=bf16)
         self.orc_ix = orc.Index(self.vec, w["offsets"], w["proj"], L)
         self.qv_cuda = w["q_vectors"].cuda()
 
@@ -71,11 +71,11 @@ def test_database_filters(bv, small):
     assert np.array_equal(cnt, small.orc_ix.count.T)
 
 
-def _check_query(bv, orc, case, k, C, A, M, nq=None):
+def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False):
     w = case.w
     qo = w["q_offsets"] if nq is None else w["q_offsets"][:nq + 1]
     nq = qo.shape[0] - 1
-    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M)
+    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M, fast=fast)
     torch.cuda.synchronize()
     qpos = _np(t["qpos"], np.uint16)
     h = _np(t["h"], np.uint16)
@@ -206,3 +206,36 @@ def test_longest_codes(bv, orc, m):
     w = _workload(70, 1, 4, 32, 8, 4, 1, 4, m, 8, seed=12)
     case = Case(bv, orc, w, 40)
     _check_query(bv, orc, case, k=5, C=30, A=3, M=1)
+
+
+# ---- fast form: tensor-core refine from BF16 vectors --------------------------------
+# On grid-valued inputs BF16 holds every value exactly and the FP32 tensor-core
+# accumulation is exact, so the fast form must match the oracle like the plain one.
+
+@pytest.mark.parametrize("n_sets,lo,hi,d,qlo,qhi,C,seed", [
+    (2000, 4, 16, 128, 4, 16, 200, 0),     # the small workload's shapes
+    (3000, 8, 32, 384, 8, 32, 1000, 13),   # the large workload's shapes, 8 CTAs per query
+    (300, 1, 3, 64, 1, 5, 300, 14),        # one 64-dim block, tiny sets, C > |F1|
+    (500, 20, 140, 192, 2, 32, 150, 15),   # sets longer than one 128-row tile
+])
+def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
+    w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
+    case = Case(bv, orc, w, 24, bf16=True)
+    _check_query(bv, orc, case, k=10, C=C, A=3, M=1, fast=True)
+    _check_query(bv, orc, case, k=10, C=C, A=2, M=0, nq=4, fast=True)
+
+
+def test_fast_form_falls_back_and_validates(bv, orc):
+    # query sets of more than 32 vectors use the FP32 refine
+    w = _workload(150, 2, 10, 128, 16, 5, 33, 50, 512, 8, seed=16)
+    case = Case(bv, orc, w, 16, bf16=True)
+    _check_query(bv, orc, case, k=5, C=60, A=3, M=1, fast=True)
+    # the fast form needs the BF16 copy, which needs d % 64 == 0
+    w2 = _workload(50, 2, 4, 48, 8, 3, 2, 4, 256, 4, seed=17)
+    ix = bv.bvss_build(w2["vectors"].cuda(), w2["offsets"], w2["proj"], wta_l=8)
+    with pytest.raises(bv.BvssError) as e:
+        bv.bvss_query(ix, w2["q_vectors"].cuda(), w2["q_offsets"], k=3, C=10, fast=True)
+    assert e.value.code == bv.BVSS_EINVAL
+    with pytest.raises(bv.BvssError) as e:
+        bv.bvss_build(w2["vectors"].cuda(), w2["offsets"], w2["proj"], wta_l=8, bf16=True)
+    assert e.value.code == bv.BVSS_EINVAL
