@@ -259,7 +259,7 @@ def traffic_per_unit(kernel):
     return None
 
 
-def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
+def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=False):
     """Roofline of the dominant kernel (scan or refine) of the timed region.
 
     Each kernel has an ALU roof and an HBM roof; the one with the longer time at
@@ -271,25 +271,36 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
     hbm, hbm_basis = measured_peaks()
     per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
     clock = SM_MAX_MHZ * 1e6
-    # the library runs the TMA-staged refine when its shared-memory stages fit
-    refine_name = "k_refine_tma" if c["d"] % 4 == 0 and c["q_hi"] <= 64 else "k_refine"
+    # the refine kernel the library runs for this workload
+    if fast and c["d"] % 64 == 0 and c["q_hi"] <= 32:
+        refine_name, vbytes = "k_refine_mma", 2
+    else:
+        refine_name = "k_refine_tma" if c["d"] % 4 == 0 and c["q_hi"] <= 64 else "k_refine"
+        vbytes = 4
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16_peak, bf16_basis = float(mp["bf16_tflops_sustained"]) * 1e12, "of measured (sustained bf16)"
+    except Exception:
+        bf16_peak, bf16_basis = 1.7e15, "of fallback (sustained bf16)"
+    if refine_name == "k_refine_mma":
+        refine_alu = (2.0 * pair_elems * c["d"], bf16_peak, "TFLOP/s", bf16_basis, "tensor")
+    else:
+        refine_alu = (2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock,
+                      "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)", "alu")
     kern = {
         "scan": dict(
             name="k_scan", t=per["scan"],
             alu=(gated_pairs * (c["m"] // 32), SM_COUNT * POPC_PER_CLK_PER_SM * clock, "Tpopc/s",
-                 "152 SMs x 16 popc/clk x 2070 MHz (nominal)"),
+                 "152 SMs x 16 popc/clk x 2070 MHz (nominal, measured 15.1)", "alu"),
             hbm_bytes=c["n_sets"] * c["m"] / 8 + nq * c["A"] * c["n_sets"] / 8
             + nq * c["n_sets"] * 2, units=None),
-        "refine": dict(
-            name=refine_name, t=per["refine"],
-            alu=(2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock, "TFLOP/s",
-                 "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)"),
-            hbm_bytes=cand_rows * c["d"] * 4.0, units=cand_rows),
+        "refine": dict(name=refine_name, t=per["refine"], alu=refine_alu,
+                       hbm_bytes=cand_rows * c["d"] * float(vbytes), units=cand_rows),
     }
     dom = max(kern, key=lambda k: kern[k]["t"])
     k = kern[dom]
     t = k["t"] / 1e3
-    ops, peak_ops, unit, basis = k["alu"]
+    ops, peak_ops, unit, basis, alu_bound = k["alu"]
     t_alu, t_hbm = ops / peak_ops, k["hbm_bytes"] / (hbm * 1e9)
     tpu = traffic_per_unit(k["name"])
     traffic = tpu * k["units"] if (tpu is not None and k["units"]) else None
@@ -301,7 +312,7 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows):
                 "of measured" else hbm_basis,
                 "alu_roof": {"achieved": ops / t / 1e12, "peak": peak_ops / 1e12, "unit": unit}}
     ach = ops / t / 1e12
-    return {"kernel": k["name"], "bound": "alu", "achieved": ach, "peak": peak_ops / 1e12,
+    return {"kernel": k["name"], "bound": alu_bound, "achieved": ach, "peak": peak_ops / 1e12,
             "unit": unit, "frac": ach / (peak_ops / 1e12), "traffic": traffic,
             "peak_basis": basis, "algorithmic_bytes": k["hbm_bytes"],
             "hbm_roof": {"achieved": k["hbm_bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s"}}
@@ -365,13 +376,15 @@ def run_ours(args, rank, world, local_rank):
         w["q_offsets"] = datagen.offsets_from_sizes(qs)
     off = w["offsets"]
     t0 = time.perf_counter()
-    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"])
+    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=c["d"] % 64 == 0)
+    fast_ok = c["d"] % 64 == 0
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - t0
     qv, qoff = w["q_vectors"], w["q_offsets"]
     nq = qoff.shape[0] - 1
     kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"])
 
+    kw_fast = dict(kw, fast=fast_ok)
     # one traced pass (outside the timed region): |F1| per query for the roofline
     tr = bvss.bvss_query_trace(ix, qv, qoff, **kw)
     torch.cuda.synchronize(dev)
@@ -387,6 +400,9 @@ def run_ours(args, rank, world, local_rank):
                       * qsz[:, None]).sum().item())
     ids_ref = tr["ids"].clone()
     del tr, h, cand
+    ids_fast, _ = bvss.bvss_query(ix, qv, qoff, **kw_fast)
+    torch.cuda.synchronize(dev)
+    fast_same = bool(torch.equal(ids_fast, ids_ref))
 
     # recall@10 against exact brute force (rank 0, subset of the query sets)
     rec = None
@@ -397,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
                                              torch.from_numpy(np.diff(off)).to(dev))
         qids = list(range(min(args.recall_queries, nq)))
         gt_ids, gt_d2 = exact_topk(vec, vnorm, set_of_row, c["n_sets"], qv, qoff, qids, c["k"])
-        got = ids_ref[qids].cpu().numpy()
+        got = ids_fast[qids].cpu().numpy()
         got_d2 = true_d2_of(vec, vnorm, qv, qoff, off, qids, got)
         rs, rt = recall_at_k(got, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(), got_d2, c["k"])
         rec = {"recall_at_10": rs, "recall_at_10_ties": rt, "queries": len(qids)}
@@ -412,38 +428,47 @@ def run_ours(args, rank, world, local_rank):
     del w["vectors"]
     torch.cuda.empty_cache()
 
-    # device-resident inputs: the timed region
+    # device-resident inputs: the timed regions, plain form then fast form
     out_ids = torch.empty((nq, c["k"]), dtype=torch.int64, device=dev)
     out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw)
-    torch.cuda.synchronize(dev)
-    assert torch.equal(out_ids, ids_ref)
-    bvss.bvss_profile_enable(ix, True)
-    bvss.bvss_profile_read(ix, reset=True)
-    clocks = ClockSampler(dev)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    stage_ms, nbatch = bvss.bvss_profile_read(ix, reset=True)
-    bvss.bvss_profile_enable(ix, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+
+    def timed(kwq, sample_clocks):
+        for _ in range(args.warmup):
+            bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream, **kwq)
+        torch.cuda.synchronize(dev)
+        assert torch.equal(out_ids, ids_ref)
+        bvss.bvss_profile_enable(ix, True)
+        bvss.bvss_profile_read(ix, reset=True)
+        clocks = ClockSampler(dev) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            bvss.bvss_query(ix, qv, qoff, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kwq)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        t_ms = e0.elapsed_time(e1) / args.steps
+        st_ms, nb = bvss.bvss_profile_read(ix, reset=True)
+        bvss.bvss_profile_enable(ix, False)
+        bvss.bvss_sync(ix, stream)
+        if world > 1:
+            t = torch.tensor([t_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return t_ms, st_ms, nb, clk
+
+    ms_plain, stage_plain, _, _ = timed(kw, False)
+    ms, stage_ms, nbatch, clk = timed(kw_fast, True)
     value = world * nq / (ms / 1e3)
 
     # end to end through the same API: pinned host query vectors in, host results out
@@ -451,13 +476,13 @@ def run_ours(args, rank, world, local_rank):
     hi = torch.empty((nq, c["k"]), dtype=torch.int64).pin_memory()
     hd = torch.empty((nq, c["k"]), dtype=torch.float32).pin_memory()
     for _ in range(max(1, args.warmup)):
-        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw)
+        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw_fast)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw)
+        bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw_fast)
     torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     if world > 1:
@@ -483,17 +508,23 @@ def run_ours(args, rank, world, local_rank):
                            "refine_scaled": float(parts[2])}}
 
     # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
-    roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows)
+    roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(c), "form": "plain (FP32 refine, random FlyHash)",
+        "vs_baseline": None, "dtype": "bf16" if fast_ok else "f32", "data": "synthetic",
+        "config": {"workload": workload_name(c),
+                   "form": ("fast: BF16 tensor-core refine (tcgen05) with FP32 re-score of the "
+                            "critical pair; random FlyHash" if fast_ok else
+                            "plain: FP32 refine, random FlyHash"),
                    "query_sets_per_step_per_gpu": nq,
                    "l2": "inputs larger than L2 (sketch matrix %.0f MB, vectors %.1f GB)"
                          % (c["n_sets"] * c["m"] / 8 / 1e6, off[-1] * c["d"] * 4 / 1e9),
                    "parallelism": "replicated index, query sets split over ranks"},
         "recall": rec,
+        "plain_form": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                       "stages_ms_per_step": {k: v / args.steps for k, v in stage_plain.items()},
+                       "dtype": "f32", "same_ids_as_fast": fast_same},
         "roofline": roof,
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "cpu_baseline": cpu,
