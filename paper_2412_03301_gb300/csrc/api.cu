@@ -81,6 +81,7 @@ void free_workspace(Workspace &w) {
     dfree(w.chunk);
     dfree(w.cand);
     dfree(w.cand_dist);
+    dfree(w.pair);
     dfree(w.out_ids);
     dfree(w.out_dist);
     w = Workspace();
@@ -201,6 +202,7 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * 4));
         BVSS_CU(dalloc(&w.cand, (size_t)cq * cC));
         BVSS_CU(dalloc(&w.cand_dist, (size_t)cq * cC));
+        BVSS_CU(dalloc(&w.pair, (size_t)cq * cC));
         if (need_qvec || had_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)cvq * d));
         if (need_out || had_out) {
             BVSS_CU(dalloc(&w.out_ids, (size_t)cq * ck));
@@ -356,7 +358,7 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
         // lines 19-23
         if (fast && refine_mma_supported(d, max_mq))
             BVSS_CU(launch_refine_mma(qv, w.qoff, nb, ix->vec, ix->vec16, ix->vnorm16, ix->set_off,
-                                      d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
+                                      d, w.cand, w.thr, C, w.pair, w.cand_dist, ix->err, st));
         else if (refine_tma_supported(d, max_mq))
             BVSS_CU(launch_refine_tma(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off,
                                       d, w.cand, w.thr, C, w.cand_dist, ix->err, st));

@@ -39,6 +39,7 @@ struct Workspace {
     int32_t *chunk = nullptr;     // per (query, chunk): lt, eq, eq_before, out_off
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
+    int2 *pair = nullptr;         // (query vector, row) attaining each candidate's value
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
     float *out_dist = nullptr;
     int cap_k = 0;
@@ -142,8 +143,8 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
                               const float *vec, const __nv_bfloat16 *vec16,
                               const float *vnorm16, const int64_t *set_off, int d,
-                              const int32_t *cand, const int32_t *thr, int C, float *cand_dist,
-                              int *err, cudaStream_t st);
+                              const int32_t *cand, const int32_t *thr, int C, int2 *pair,
+                              float *cand_dist, int *err, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf

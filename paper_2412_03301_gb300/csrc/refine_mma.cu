@@ -22,9 +22,11 @@
 //              vectors, 128 columns = rows), forms |q|^2 + |v|^2 - 2 q.v and
 //              keeps, for the open candidate, the minimum over its rows per
 //              query vector and the maximum over rows of the minimum over query
-//              vectors; when a candidate ends, the pair attaining its Hausdorff
-//              value (Def. 4) is re-scored directly in FP32 from the original
-//              vectors and the square root written.
+//              vectors; when a candidate ends, it records the pair attaining
+//              the candidate's Hausdorff value (Def. 4).
+// k_rescore then computes that pair's distance directly in FP32 from the
+// original vectors (one warp per candidate, many rows in flight) and writes
+// the square root as the candidate's distance.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include <cuda_bf16.h>
@@ -104,7 +106,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const float *__restrict__ vec, const __nv_bfloat16 *__restrict__ vec16,
              const float *__restrict__ vnorm16, const int64_t *__restrict__ set_off, int d,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C,
-             float *__restrict__ cand_dist, int *__restrict__ err) {
+             int2 *__restrict__ pair, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     const int q = blockIdx.y;
     const int n_sel = thr[q * 4 + 3];
@@ -313,23 +315,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 pa = (int)(cmax_key & 0xff);
                 pr = (int)((cmax_key >> 8) & 0xffffff);
             }
-            const float4 *x4 = reinterpret_cast<const float4 *>(qvec + (a0 + pa) * d);
-            const float4 *y4 = reinterpret_cast<const float4 *>(vec + (grow0[c] + pr) * d);
-            float s = 0.0f;
-            for (int k = lane; k < d / 4; k += 32) {
-                const float4 x = x4[k], y = y4[k];
-                float u = x.x - y.x;
-                s = fmaf(u, u, s);
-                u = x.y - y.y;
-                s = fmaf(u, u, s);
-                u = x.z - y.z;
-                s = fmaf(u, u, s);
-                u = x.w - y.w;
-                s = fmaf(u, u, s);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) cand_dist[(int64_t)q * C + c0 + c] = sqrtf(s);
+            if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
         };
         bool ok = true;
         for (int t = 0; t < n_tiles && ok; ++t) {
@@ -383,6 +369,41 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// distance of each candidate's recorded pair, directly in FP32; one warp per candidate
+__global__ void __launch_bounds__(256)
+k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
+          const float *__restrict__ vec, const int64_t *__restrict__ set_off,
+          const int32_t *__restrict__ cand, const int32_t *__restrict__ thr,
+          const int2 *__restrict__ pair, int C, int d, float *__restrict__ cand_dist) {
+    const int q = blockIdx.y;
+    const int n_sel = thr[q * 4 + 3];
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= n_sel) return;
+    int2 pr = pair[(int64_t)q * C + c];
+    const int64_t id = cand[(int64_t)q * C + c];
+    // keep the pair inside its sets whatever the array holds
+    pr.x = min(max(pr.x, 0), (int)(qoff[q + 1] - qoff[q]) - 1);
+    pr.y = min(max(pr.y, 0), (int)(set_off[id + 1] - set_off[id]) - 1);
+    const float4 *x4 = reinterpret_cast<const float4 *>(qvec + (qoff[q] + pr.x) * d);
+    const float4 *y4 = reinterpret_cast<const float4 *>(vec + (set_off[id] + pr.y) * d);
+    float s = 0.0f;
+    for (int k = lane; k < d / 4; k += 32) {
+        const float4 x = x4[k], y = y4[k];
+        float u = x.x - y.x;
+        s = fmaf(u, u, s);
+        u = x.y - y.y;
+        s = fmaf(u, u, s);
+        u = x.z - y.z;
+        s = fmaf(u, u, s);
+        u = x.w - y.w;
+        s = fmaf(u, u, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) cand_dist[(int64_t)q * C + c] = sqrtf(s);
+}
+
 // FP32 -> BF16 copy of the vectors and the squared norms of the BF16 values
 __global__ void k_to_bf16(const float *__restrict__ x, int64_t n, int d,
                           __nv_bfloat16 *__restrict__ y, float *__restrict__ norm) {
@@ -431,8 +452,8 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
                               const float *vec, const __nv_bfloat16 *vec16,
                               const float *vnorm16, const int64_t *set_off, int d,
-                              const int32_t *cand, const int32_t *thr, int C, float *cand_dist,
-                              int *err, cudaStream_t st) {
+                              const int32_t *cand, const int32_t *thr, int C, int2 *pair,
+                              float *cand_dist, int *err, cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
     const Layout Lo = make_layout(d);
     cudaError_t e = cudaFuncSetAttribute(k_refine_mma,
@@ -440,8 +461,11 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
     if (e != cudaSuccess) return e;
     const int gx = (C + kCandCTA - 1) / kCandCTA;
     k_refine_mma<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec, vec16, vnorm16,
-                                                            set_off, d, cand, thr, C, cand_dist,
-                                                            err);
+                                                            set_off, d, cand, thr, C, pair, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, set_off, cand, thr, pair,
+                                                       C, d, cand_dist);
     return cudaGetLastError();
 }
 
