@@ -91,6 +91,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// ---- named barriers over a subset of the block's warps (ids 1-15) ----
+__device__ __forceinline__ void named_barrier_sync(int id, int n_threads) {
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(n_threads) : "memory");
+}
+// barrier that also returns whether pred held in every participating thread
+__device__ __forceinline__ bool named_barrier_and(int id, int n_threads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n_threads)
+        : "memory");
+    return r != 0;
+}
+
 // ---- tcgen05 (5th-generation tensor cores, accumulators in tensor memory) ----
 // Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout,
 // 8-row groups 1024 bytes apart, tile base 1024-byte aligned.

@@ -10,20 +10,27 @@
 // K-major in the 128-byte swizzle layout, accumulated in FP32 in tensor memory
 // (TMEM lane = query vector, column = row).
 //
+// The same stage also feeds a second, four times smaller MMA with the roles
+// swapped (rows as M = 128, the 32 query vectors as N), so tensor memory holds
+// the tile both ways round and every reduction of the epilogue stays inside a
+// thread.
+//
 // Warp roles (no block-wide barrier between set-up and tear-down):
-//   warps 1-4  producers: each thread gathers one row of every tile, one
+//   warps 4-7  producers: each thread gathers one row of every tile, one
 //              64-dimension block at a time, with 16-byte cp.async copies
 //              straight into the swizzled stage (a ring of 8 stages, 5 kept in
 //              flight per thread), then signals the stage's mbarrier;
-//   warp 5     one thread issues the MMAs (K = 16 each) and commits them to the
+//   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
-//              one of two TMEM accumulators;
-//   warp 0     owns TMEM; reads a finished accumulator (32 lanes = query
-//              vectors, 128 columns = rows), forms |q|^2 + |v|^2 - 2 q.v and
-//              keeps, for the open candidate, the minimum over its rows per
-//              query vector and the maximum over rows of the minimum over query
-//              vectors; when a candidate ends, it records the pair attaining
-//              the candidate's Hausdorff value (Def. 4).
+//              one of two pairs of TMEM accumulators;
+//   warps 0-3  epilogue.  Warp w reads the swapped tile for rows 32w..32w+31
+//              and takes each row's minimum over the query vectors of
+//              |q|^2 + |v|^2 - 2 q.v (with its arg-min).  Warp 0 then reads the
+//              tile with lane = query vector and walks the rows in order,
+//              keeping for the open candidate the minimum over its rows per
+//              query vector and the maximum of the rows' minima; when a
+//              candidate ends it records the pair attaining the candidate's
+//              Hausdorff value (Def. 4).
 // k_rescore then computes that pair's distance directly in FP32 from the
 // original vectors (one warp per candidate, many rows in flight) and writes
 // the square root as the candidate's distance.
@@ -44,9 +51,11 @@ constexpr int kNS = 8;               // stages in the ring
 constexpr int kLag = 5;              // stages a producer thread keeps in flight
 constexpr int kCandCTA = 128;        // candidates per CTA
 constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
-constexpr int kThreads = 6 * 32;     // warp 0 epilogue, 1-4 producers, 5 MMA
+constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
 constexpr int kProd = 128;
-constexpr uint32_t kTmemCols = 256;  // two accumulators of 128 columns
+constexpr int kEpi = 128;
+constexpr uint32_t kTmemCols = 512;  // D: 2 x 128 columns at 0; swapped D: 2 x 32 at 256
+constexpr uint32_t kTmemT = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kStageBytes = kRowsN * 128;
 constexpr int kQBlock = 4096;        // 32 query rows x 128 bytes per K-block
@@ -60,7 +69,7 @@ struct Meta {
 };
 
 struct Layout {
-    int q, stages, meta, bars, grow0, vrow0, qn, misc, total;
+    int q, stages, meta, colkey, bars, grow0, vrow0, qn, misc, total;
 };
 
 // Tiles of row metadata the ring must hold: producers run at most kNS stages
@@ -76,6 +85,7 @@ __host__ __device__ inline Layout make_layout(int d) {
     o = (o + 1023) & ~1023;
     L.stages = o;  o += kNS * kStageBytes;         // >= 12 KB follow the last Q block
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
+    L.colkey = o;  o += 2 * kRowsN * 8;            // per-row minima over the query, 2 tiles
     L.bars = o;    o += (2 * kNS + 4 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
@@ -130,6 +140,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     int64_t *grow0 = reinterpret_cast<int64_t *>(smem + Lo.grow0);
     int *vrow0 = reinterpret_cast<int *>(smem + Lo.vrow0);
     float *qn = reinterpret_cast<float *>(smem + Lo.qn);
+    unsigned long long *colkey = reinterpret_cast<unsigned long long *>(smem + Lo.colkey);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lo.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lo.misc + 4);
 
@@ -162,18 +173,6 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             run += n4[i];
         }
         if (lane == 31) vrow0[kCandCTA] = incl;    // rows of the CTA
-        // squared norms of the BF16-rounded query vectors
-        for (int a = 0; a < kMaxQ; ++a) {
-            float sq = 0.0f;
-            if (a < mq)
-                for (int k = lane; k < d; k += 32) {
-                    const float x = __bfloat162float(__float2bfloat16_rn(qvec[(a0 + a) * d + k]));
-                    sq = fmaf(x, x, sq);
-                }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0) qn[a] = sq;
-        }
         tmem_alloc(tmem_slot, kTmemCols);
     }
     // query rows 0..31 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
@@ -213,6 +212,25 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         *abort_flag = 0;
         fence_mbar_init();
     }
+    __syncthreads();
+    // squared norms of the staged BF16 query rows, one warp per row
+    for (int a = warp; a < kMaxQ; a += kThreads / 32) {
+        float sq = 0.0f;
+        for (int ch = lane; ch < nch; ch += 32) {
+            const uint4 pk =
+                *reinterpret_cast<const uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7));
+            const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[i]));
+                sq = fmaf(f.x, f.x, sq);
+                sq = fmaf(f.y, f.y, sq);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) qn[a] = sq;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -221,34 +239,46 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     const int n_tiles = (R + kRowsN - 1) / kRowsN;
     const int total = n_tiles * KB;
 
-    if (warp >= 1 && warp <= 4) {
+    if (warp >= 4 && warp <= 7) {
         // ---- producers: thread p fills row p of every tile ----------------------
-        const int p = tid - 32;
+        const int p = tid - 128;
+        // where row p of tile t lives; its norm is loaded one tile ahead of use
+        int n_slot = -1, n_row = 0;
+        int64_t n_grow = 0;
+        float n_vn = 0.0f;
+        auto locate = [&](int t) {
+            const int v = t * kRowsN + p;
+            n_slot = -1;
+            n_row = 0;
+            n_vn = 0.0f;
+            if (v < R) {
+                int c = 0;
+#pragma unroll
+                for (int b = 64; b > 0; b >>= 1)
+                    if (c + b < ncand && vrow0[c + b] <= v) c += b;
+                n_slot = c;
+                n_row = v - vrow0[c];
+                n_grow = grow0[c] + n_row;
+                n_vn = vnorm16[n_grow];
+            }
+        };
+        locate(0);
         int64_t grow = 0;
         bool rv = false;
         bool ok = true;
         for (int u = 0; u < total && ok; ++u) {
             const int t = u / KB, kb = u - (u / KB) * KB, s = u % kNS;
             if (kb == 0) {
-                const int v = t * kRowsN + p;
-                rv = v < R;
                 Meta m;
-                m.slot = -1;
-                m.row_in = 0;
-                m.vn = 0.0f;
+                m.slot = n_slot;
+                m.row_in = n_row;
+                m.vn = n_vn;
                 m.pad = 0;
-                if (rv) {
-                    int c = 0;
-#pragma unroll
-                    for (int b = 64; b > 0; b >>= 1)
-                        if (c + b < ncand && vrow0[c + b] <= v) c += b;
-                    m.slot = c;
-                    m.row_in = v - vrow0[c];
-                    grow = grow0[c] + m.row_in;
-                    m.vn = vnorm16[grow];
-                }
+                rv = n_slot >= 0;
+                grow = n_grow;
                 meta[(t % MR) * kRowsN + p] = m;
                 mbar_arrive(&mfull[t % MR]);
+                if (t + 1 < n_tiles) locate(t + 1);
             }
             ok = wait_or_abort(&empty[s], (uint32_t)(((u / kNS) & 1) ^ 1), abort_flag, err);
             if (ok && rv) {
@@ -269,10 +299,11 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         fence_proxy_async();
         if (ok)
             for (int u = total > kLag ? total - kLag : 0; u < total; ++u) mbar_arrive(&full[u % kNS]);
-    } else if (warp == 5) {
+    } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
             constexpr uint32_t idesc = umma_idesc_bf16(128, kRowsN);
+            constexpr uint32_t idesc_t = umma_idesc_bf16(kRowsN, kMaxQ);
             const uint32_t qaddr = smem_u32(Qs), saddr = smem_u32(stages);
             bool ok = true;
             for (int t = 0; t < n_tiles && ok; ++t) {
@@ -281,26 +312,29 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(buf * kRowsN);
+                const uint32_t dtt = tmem + kTmemT + (uint32_t)(buf * kMaxQ);
                 for (int kb = 0; kb < KB && ok; ++kb) {
                     const int u = t * KB + kb, s = u % kNS;
                     ok = wait_or_abort(&full[s], (uint32_t)((u / kNS) & 1), abort_flag, err);
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        umma_bf16(dt, umma_desc_sw128(qaddr + kb * kQBlock + 32 * k),
-                                  umma_desc_sw128(saddr + s * kStageBytes + 32 * k), idesc,
-                                  (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t dq = umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
+                        const uint64_t dv = umma_desc_sw128(saddr + s * kStageBytes + 32 * k);
+                        const uint32_t acc = (kb | k) != 0 ? 1u : 0u;
+                        umma_bf16(dt, dq, dv, idesc, acc);      // lane = query vector
+                        umma_bf16(dtt, dv, dq, idesc_t, acc);   // lane = row
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&tfull[buf]);
             }
         }
     } else {
-        // ---- epilogue: warp 0, lane = query vector -------------------------------
+        // ---- epilogue: warps 0-3 ---------------------------------------------------
         const float INF = __int_as_float(0x7f800000);
         const bool va = lane < mq;
-        const float qna = qn[lane];
         int open = -1;
         float rmin = INF;
         int rrow = 0;
@@ -322,44 +356,71 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             const int buf = t & 1;
             ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
                  wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
-            if (!ok) break;
+            // all four epilogue warps take the same exit
+            if (!named_barrier_and(1, kEpi, ok)) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
             const Meta *mt = meta + (t % MR) * kRowsN;
-            for (int cc = 0; cc < kRowsN / 32; ++cc) {
+            const int rows_t = min(kRowsN, R - t * kRowsN);
+            unsigned long long *ck = colkey + buf * kRowsN;
+            {
+                // row 32w + lane: minimum over the query vectors, from the swapped tile
+                const int r = warp * 32 + lane;
+                const Meta m = mt[r];
                 uint32_t v[32];
-                tmem_ld32(tmem + (uint32_t)(buf * kRowsN + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + kTmemT + (uint32_t)(buf * kMaxQ), v);
+                float best = INF;
+                int ba = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const Meta m = mt[cc * 32 + j];
-                    if (m.slot >= 0) {
-                        if (m.slot != open) {
+                for (int a = 0; a < kMaxQ; ++a) {
+                    float d2 = qn[a] + m.vn - 2.0f * __uint_as_float(v[a]);
+                    d2 = d2 > 0.0f ? d2 : 0.0f;
+                    if (a < mq && d2 < best) {
+                        best = d2;
+                        ba = a;
+                    }
+                }
+                ck[r] = ((unsigned long long)__float_as_uint(best) << 32) |
+                        ((unsigned long long)(m.row_in & 0xffffff) << 8) | (unsigned)ba;
+            }
+            tc_fence_before();
+            named_barrier_sync(2, kEpi);
+            if (warp == 0) {
+                tc_fence_after();
+                const float qna = qn[lane];
+                for (int cc = 0; cc < (rows_t + 31) / 32; ++cc) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + (uint32_t)(buf * kRowsN + cc * 32), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int r = cc * 32 + j;
+                        const int slot = mt[r].slot;
+                        if (slot < 0) break;
+                        if (slot != open) {
                             if (open >= 0) finalize(open);
-                            open = m.slot;
+                            open = slot;
                             rmin = INF;
                             rrow = 0;
                             cmax_key = -1;
                         }
-                        float d2 = qna + m.vn - 2.0f * __uint_as_float(v[j]);
+                        float d2 = qna + mt[r].vn - 2.0f * __uint_as_float(v[j]);
                         d2 = d2 > 0.0f ? d2 : 0.0f;
-                        if (!va) d2 = INF;
-                        if (d2 < rmin) {
+                        if (va && d2 < rmin) {
                             rmin = d2;
-                            rrow = m.row_in;
+                            rrow = mt[r].row_in;
                         }
-                        const uint32_t b = __float_as_uint(d2);
-                        const uint32_t mn = __reduce_min_sync(0xffffffffu, b);
-                        const int am = __ffs(__ballot_sync(0xffffffffu, b == mn)) - 1;
-                        const long long key =
-                            ((long long)mn << 32) | ((long long)m.row_in << 8) | am;
+                        const long long key = (long long)ck[r];
                         if (key > cmax_key) cmax_key = key;
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        if (ok && open >= 0) finalize(open);
+        if (warp == 0 && ok && open >= 0) finalize(open);
     }
 
     // ---- tear-down --------------------------------------------------------------
