@@ -3,36 +3,33 @@
 //
 // One CTA takes one query set (at most 32 vectors) and up to 128 of its
 // candidates, whose rows, concatenated in candidate order, are cut into tiles
-// of 128 rows.  For every tile the dot products of all (query vector, row)
-// pairs are one 128 x 128 x d GEMM: the query vectors are the A operand
-// (M = 128 rows of shared memory, of which the first 32 hold the query; the
-// rest are never read back), the tile rows the B operand (N = 128), both
-// K-major in the 128-byte swizzle layout, accumulated in FP32 in tensor memory
-// (TMEM lane = query vector, column = row).
-//
-// The same stage also feeds a second, four times smaller MMA with the roles
-// swapped (rows as M = 128, the 32 query vectors as N), so tensor memory holds
-// the tile both ways round and every reduction of the epilogue stays inside a
-// thread.
+// of 128 rows.  For every tile the dot products of all (row, query vector)
+// pairs are one 128 x 32 x d GEMM: the tile rows are the A operand (M = 128),
+// the query vectors the B operand (N = 32), both K-major in the 128-byte
+// swizzle layout, accumulated in FP32 in tensor memory (TMEM lane = row,
+// column = query vector).
 //
 // Warp roles (no block-wide barrier between set-up and tear-down):
 //   warps 4-7  producers: each thread gathers one row of every tile, one
 //              64-dimension block at a time, with 16-byte cp.async copies
-//              straight into the swizzled stage (a ring of 8 stages, 5 kept in
-//              flight per thread), then signals the stage's mbarrier;
+//              straight into the swizzled stage (a ring of 6-8 stages, 5 kept
+//              in flight per thread), then signals the stage's mbarrier;
 //   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
-//              one of two pairs of TMEM accumulators;
-//   warps 0-3  epilogue.  Warp w reads the swapped tile for rows 32w..32w+31
-//              and takes each row's minimum over the query vectors of
-//              |q|^2 + |v|^2 - 2 q.v (with its arg-min).  Warp 0 then reads the
-//              tile with lane = query vector and walks the rows in order,
-//              keeping for the open candidate the minimum over its rows per
-//              query vector and the maximum of the rows' minima; when a
-//              candidate ends it records the pair attaining the candidate's
-//              Hausdorff value (Def. 4).
-// k_rescore then computes that pair's distance directly in FP32 from the
-// original vectors (one warp per candidate, many rows in flight) and writes
+//              one of two TMEM accumulators;
+//   warps 0-3  epilogue; warp w owns rows 32w..32w+31 of every tile.  Row
+//              phase (lane = row): squared distances |q|^2 + |v|^2 - 2 q.v to
+//              all query vectors from one tensor-memory load, their minimum
+//              (with its arg-min), and the distances written to a swizzled
+//              shared-memory block.  Column phase (lane = query vector): walk
+//              the 32 rows in order, keeping per candidate the minimum over its
+//              rows and the maximum of the rows' minima, merged into
+//              per-candidate slots with shared-memory atomics (a candidate's
+//              rows may span warps and tiles).
+// After the last tile, each candidate's Hausdorff value (Def. 4) is the larger
+// of max over query vectors of the slot minima and the slot maximum; the pair
+// attaining it is recorded, and k_rescore computes that pair's distance
+// directly in FP32 from the original vectors (one warp per candidate) and writes
 // the square root as the candidate's distance.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
@@ -45,21 +42,21 @@ namespace bvss {
 
 namespace {
 
-constexpr int kRowsN = 128;          // candidate rows per tile (MMA N)
+constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
 constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
-constexpr int kNS = 8;               // stages in the ring
+constexpr int kMaxNS = 8;            // stages in the ring, at most
 constexpr int kLag = 5;              // stages a producer thread keeps in flight
 constexpr int kCandCTA = 128;        // candidates per CTA
 constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
 constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
 constexpr int kProd = 128;
 constexpr int kEpi = 128;
-constexpr uint32_t kTmemCols = 512;  // D: 2 x 128 columns at 0; swapped D: 2 x 32 at 256
-constexpr uint32_t kTmemT = 256;
+constexpr int kMaxQ = 32;
+constexpr uint32_t kTmemCols = 64;   // two accumulators of 32 columns
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kStageBytes = kRowsN * 128;
-constexpr int kQBlock = 4096;        // 32 query rows x 128 bytes per K-block
-constexpr int kMaxQ = 32;
+constexpr int kQBlock = kMaxQ * 128; // 32 query rows x 128 bytes per K-block
+constexpr int kSmemMax = 232448;
 
 struct Meta {
     int slot;     // candidate slot of the row, -1 past the end
@@ -69,30 +66,39 @@ struct Meta {
 };
 
 struct Layout {
-    int q, stages, meta, colkey, bars, grow0, vrow0, qn, misc, total;
+    int q, stages, meta, dist, cmin, ckey, rkey, bars, grow0, vrow0, qn, misc, total;
 };
 
-// Tiles of row metadata the ring must hold: producers run at most kNS stages
+// Tiles of row metadata the ring must hold: producers run at most ns stages
 // ahead of the MMA, which runs at most two tiles ahead of the epilogue.
-__host__ __device__ inline int meta_ring(int KB) { return (kNS + 1 + KB - 1) / KB + 3; }
+__host__ __device__ inline int meta_ring(int KB, int ns) { return (ns + KB) / KB + 3; }
 
-__host__ __device__ inline Layout make_layout(int d) {
+__host__ __device__ inline Layout make_layout(int d, int ns) {
     Layout L;
     const int KB = d / kKB;
-    const int MR = meta_ring(KB);
+    const int MR = meta_ring(KB, ns);
     int o = 0;
-    L.q = o;       o += KB * kQBlock;              // rows 32..127 of a block read on into the next
-    o = (o + 1023) & ~1023;
-    L.stages = o;  o += kNS * kStageBytes;         // >= 12 KB follow the last Q block
+    L.q = o;       o += KB * kQBlock;
+    L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
-    L.colkey = o;  o += 2 * kRowsN * 8;            // per-row minima over the query, 2 tiles
-    L.bars = o;    o += (2 * kNS + 4 + kMaxMeta) * 8;
+    L.dist = o;    o += kRowsN * 128;              // row-phase distances, 32 per row
+    L.cmin = o;    o += kCandCTA * kMaxQ * 8;      // per (candidate, query vector) minimum
+    L.ckey = o;    o += kCandCTA * 8;              // per candidate maximum of row minima
+    L.rkey = o;    o += kRowsN * 8;                // per row minimum, this tile
+    L.bars = o;    o += (2 * kMaxNS + 4 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
     L.qn = o;      o += kMaxQ * 4;
     L.misc = o;    o += 16;                        // TMEM address, abort flag
     L.total = o + 1024;                            // slack to align the base to 1024 bytes
     return L;
+}
+
+// most stages that fit, at least kLag + 1 (a producer holds kLag arrivals back)
+inline int pick_stages(int d) {
+    for (int ns = kMaxNS; ns > kLag; --ns)
+        if (make_layout(d, ns).total <= kSmemMax && meta_ring(d / kKB, ns) <= kMaxMeta) return ns;
+    return 0;
 }
 
 // wait for a phase, or give up when the limit passes or another role gave up
@@ -111,10 +117,14 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
     return true;
 }
 
+__device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | low;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-             const float *__restrict__ vec, const __nv_bfloat16 *__restrict__ vec16,
-             const float *__restrict__ vnorm16, const int64_t *__restrict__ set_off, int d,
+             const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
+             const int64_t *__restrict__ set_off, int d, int ns,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C,
              int2 *__restrict__ pair, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
@@ -127,20 +137,23 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     const int64_t a0 = qoff[q];
     const int mq = (int)(qoff[q + 1] - a0);
     const int KB = d / kKB;
-    const int MR = meta_ring(KB);
-    const Layout Lo = make_layout(d);
+    const int MR = meta_ring(KB, ns);
+    const Layout Lo = make_layout(d, ns);
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *Qs = smem + Lo.q;
     unsigned char *stages = smem + Lo.stages;
     Meta *meta = reinterpret_cast<Meta *>(smem + Lo.meta);
+    unsigned char *dist = smem + Lo.dist;
+    unsigned long long *cmin = reinterpret_cast<unsigned long long *>(smem + Lo.cmin);
+    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem + Lo.ckey);
+    unsigned long long *rkey = reinterpret_cast<unsigned long long *>(smem + Lo.rkey);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bars);
-    uint64_t *full = bars, *empty = bars + kNS, *tfull = bars + 2 * kNS,
-             *tempty = bars + 2 * kNS + 2, *mfull = bars + 2 * kNS + 4;
+    uint64_t *full = bars, *empty = bars + kMaxNS, *tfull = bars + 2 * kMaxNS,
+             *tempty = bars + 2 * kMaxNS + 2, *mfull = bars + 2 * kMaxNS + 4;
     int64_t *grow0 = reinterpret_cast<int64_t *>(smem + Lo.grow0);
     int *vrow0 = reinterpret_cast<int *>(smem + Lo.vrow0);
     float *qn = reinterpret_cast<float *>(smem + Lo.qn);
-    unsigned long long *colkey = reinterpret_cast<unsigned long long *>(smem + Lo.colkey);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lo.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lo.misc + 4);
 
@@ -175,6 +188,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         if (lane == 31) vrow0[kCandCTA] = incl;    // rows of the CTA
         tmem_alloc(tmem_slot, kTmemCols);
     }
+    for (int e = tid; e < kCandCTA * kMaxQ; e += kThreads) cmin[e] = ~0ull;
+    for (int e = tid; e < kCandCTA; e += kThreads) ckey[e] = 0ull;
     // query rows 0..31 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
     const int nch = d / 8;                         // 16-byte chunks per row
     for (int e = tid; e < kMaxQ * nch; e += kThreads) {
@@ -200,13 +215,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     }
     fence_proxy_async();
     if (tid == 0) {
-        for (int s = 0; s < kNS; ++s) {
+        for (int s = 0; s < ns; ++s) {
             mbar_init(&full[s], kProd);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 1);
+            mbar_init(&tempty[b], kEpi / 32);
         }
         for (int i = 0; i < MR; ++i) mbar_init(&mfull[i], kProd);
         *abort_flag = 0;
@@ -267,7 +282,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         bool rv = false;
         bool ok = true;
         for (int u = 0; u < total && ok; ++u) {
-            const int t = u / KB, kb = u - (u / KB) * KB, s = u % kNS;
+            const int t = u / KB, kb = u - t * KB, s = u % ns;
             if (kb == 0) {
                 Meta m;
                 m.slot = n_slot;
@@ -280,7 +295,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 mbar_arrive(&mfull[t % MR]);
                 if (t + 1 < n_tiles) locate(t + 1);
             }
-            ok = wait_or_abort(&empty[s], (uint32_t)(((u / kNS) & 1) ^ 1), abort_flag, err);
+            ok = wait_or_abort(&empty[s], (uint32_t)(((u / ns) & 1) ^ 1), abort_flag, err);
             if (ok && rv) {
                 const unsigned char *src =
                     reinterpret_cast<const unsigned char *>(vec16 + grow * d + kb * kKB);
@@ -292,18 +307,17 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             if (u >= kLag) {
                 cp_async_wait<kLag>();
                 fence_proxy_async();
-                mbar_arrive(&full[(u - kLag) % kNS]);
+                mbar_arrive(&full[(u - kLag) % ns]);
             }
         }
         cp_async_wait<0>();
         fence_proxy_async();
         if (ok)
-            for (int u = total > kLag ? total - kLag : 0; u < total; ++u) mbar_arrive(&full[u % kNS]);
+            for (int u = total > kLag ? total - kLag : 0; u < total; ++u) mbar_arrive(&full[u % ns]);
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(128, kRowsN);
-            constexpr uint32_t idesc_t = umma_idesc_bf16(kRowsN, kMaxQ);
+            constexpr uint32_t idesc = umma_idesc_bf16(kRowsN, kMaxQ);
             const uint32_t qaddr = smem_u32(Qs), saddr = smem_u32(stages);
             bool ok = true;
             for (int t = 0; t < n_tiles && ok; ++t) {
@@ -311,116 +325,125 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 ok = wait_or_abort(&tempty[buf], (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag, err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * kRowsN);
-                const uint32_t dtt = tmem + kTmemT + (uint32_t)(buf * kMaxQ);
+                const uint32_t dt = tmem + (uint32_t)(buf * kMaxQ);
                 for (int kb = 0; kb < KB && ok; ++kb) {
-                    const int u = t * KB + kb, s = u % kNS;
-                    ok = wait_or_abort(&full[s], (uint32_t)((u / kNS) & 1), abort_flag, err);
+                    const int u = t * KB + kb, s = u % ns;
+                    ok = wait_or_abort(&full[s], (uint32_t)((u / ns) & 1), abort_flag, err);
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t dq = umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
-                        const uint64_t dv = umma_desc_sw128(saddr + s * kStageBytes + 32 * k);
-                        const uint32_t acc = (kb | k) != 0 ? 1u : 0u;
-                        umma_bf16(dt, dq, dv, idesc, acc);      // lane = query vector
-                        umma_bf16(dtt, dv, dq, idesc_t, acc);   // lane = row
-                    }
+                    for (int k = 0; k < 4; ++k)
+                        umma_bf16(dt, umma_desc_sw128(saddr + s * kStageBytes + 32 * k),
+                                  umma_desc_sw128(qaddr + kb * kQBlock + 32 * k), idesc,
+                                  (kb | k) != 0 ? 1u : 0u);
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&tfull[buf]);
             }
         }
     } else {
-        // ---- epilogue: warps 0-3 ---------------------------------------------------
+        // ---- epilogue: warps 0-3, warp w owns rows 32w..32w+31 ---------------------
         const float INF = __int_as_float(0x7f800000);
-        const bool va = lane < mq;
-        int open = -1;
-        float rmin = INF;
-        int rrow = 0;
-        long long cmax_key = -1;   // (d2 bits << 32) | (row << 8) | query vector
-        auto finalize = [&](int c) {
-            const uint32_t bits = va ? __float_as_uint(rmin) : 0u;
-            const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-            const uint32_t who = __ballot_sync(0xffffffffu, va && bits == mx);
-            const int src = __ffs(who) - 1;
-            int pa = src, pr = __shfl_sync(0xffffffffu, rrow, src);
-            if ((long long)mx < (cmax_key >> 32)) {
-                pa = (int)(cmax_key & 0xff);
-                pr = (int)((cmax_key >> 8) & 0xffffff);
-            }
-            if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
-        };
+        float qreg[kMaxQ];
+#pragma unroll
+        for (int a = 0; a < kMaxQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
+        unsigned char *dw = dist + warp * 32 * 128;
+        const int r = warp * 32 + lane;
         bool ok = true;
         for (int t = 0; t < n_tiles && ok; ++t) {
             const int buf = t & 1;
             ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
                  wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
-            // all four epilogue warps take the same exit
-            if (!named_barrier_and(1, kEpi, ok)) {
-                ok = false;
-                break;
-            }
+            if (!ok) break;
             tc_fence_after();
             const Meta *mt = meta + (t % MR) * kRowsN;
-            const int rows_t = min(kRowsN, R - t * kRowsN);
-            unsigned long long *ck = colkey + buf * kRowsN;
-            {
-                // row 32w + lane: minimum over the query vectors, from the swapped tile
-                const int r = warp * 32 + lane;
-                const Meta m = mt[r];
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + kTmemT + (uint32_t)(buf * kMaxQ), v);
-                float best = INF;
-                int ba = 0;
-#pragma unroll
-                for (int a = 0; a < kMaxQ; ++a) {
-                    float d2 = qn[a] + m.vn - 2.0f * __uint_as_float(v[a]);
-                    d2 = d2 > 0.0f ? d2 : 0.0f;
-                    if (a < mq && d2 < best) {
-                        best = d2;
-                        ba = a;
-                    }
-                }
-                ck[r] = ((unsigned long long)__float_as_uint(best) << 32) |
-                        ((unsigned long long)(m.row_in & 0xffffff) << 8) | (unsigned)ba;
-            }
-            tc_fence_before();
-            named_barrier_sync(2, kEpi);
-            if (warp == 0) {
-                tc_fence_after();
-                const float qna = qn[lane];
-                for (int cc = 0; cc < (rows_t + 31) / 32; ++cc) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + (uint32_t)(buf * kRowsN + cc * 32), v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int r = cc * 32 + j;
-                        const int slot = mt[r].slot;
-                        if (slot < 0) break;
-                        if (slot != open) {
-                            if (open >= 0) finalize(open);
-                            open = slot;
-                            rmin = INF;
-                            rrow = 0;
-                            cmax_key = -1;
-                        }
-                        float d2 = qna + mt[r].vn - 2.0f * __uint_as_float(v[j]);
-                        d2 = d2 > 0.0f ? d2 : 0.0f;
-                        if (va && d2 < rmin) {
-                            rmin = d2;
-                            rrow = mt[r].row_in;
-                        }
-                        const long long key = (long long)ck[r];
-                        if (key > cmax_key) cmax_key = key;
-                    }
-                }
+            const int rows_w = min(32, R - t * kRowsN - warp * 32);
+            if (rows_w <= 0) {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
+                continue;
+            }
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kMaxQ), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            // row phase: lane = row r
+            {
+                const Meta m = mt[r];
+                float best = INF;
+                int ba = 0;
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    float x[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = c4 * 4 + i;
+                        // qreg is +inf past the query, which keeps those entries out
+                        const float d2 = fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
+                        x[i] = d2;
+                        if (d2 < best) {
+                            best = d2;
+                            ba = a;
+                        }
+                    }
+                    *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                        make_float4(x[0], x[1], x[2], x[3]);
+                }
+                rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
+            }
+            __syncwarp();
+            // column phase: lane = query vector a, rows of this warp in order
+            {
+                const int a = lane;
+                int cur = -1;
+                float bmin = INF;
+                int brow = 0;
+                unsigned long long kmax = 0;
+                const int coff = ((a >> 2) << 4) + (a & 3) * 4;
+                for (int j = 0; j < rows_w; ++j) {
+                    const Meta mj = mt[warp * 32 + j];
+                    if (mj.slot != cur) {
+                        if (cur >= 0) {
+                            if (a < mq) atomicMin(&cmin[cur * kMaxQ + a], dkey(bmin, (uint32_t)brow));
+                            if (a == 0) atomicMax(&ckey[cur], kmax);
+                        }
+                        cur = mj.slot;
+                        bmin = INF;
+                        brow = 0;
+                        kmax = 0;
+                    }
+                    const float x = *reinterpret_cast<const float *>(dw + j * 128 + (coff ^ ((j & 7) << 4)));
+                    if (x < bmin) {
+                        bmin = x;
+                        brow = mj.row_in;
+                    }
+                    const unsigned long long kj = rkey[warp * 32 + j];
+                    kmax = kj > kmax ? kj : kmax;
+                }
+                if (a < mq) atomicMin(&cmin[cur * kMaxQ + a], dkey(bmin, (uint32_t)brow));
+                if (a == 0) atomicMax(&ckey[cur], kmax);
+            }
+            __syncwarp();
+        }
+        // every epilogue warp is done with the per-candidate slots
+        if (named_barrier_and(1, kEpi, ok)) {
+            for (int c = warp; c < ncand; c += kEpi / 32) {
+                const unsigned long long kc = lane < mq ? cmin[c * kMaxQ + lane] : 0ull;
+                const uint32_t bits = (uint32_t)(kc >> 32);
+                const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
+                const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
+                const int src = __ffs(who) - 1;
+                int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)kc, src);
+                const unsigned long long kr = ckey[c];
+                if (mx < (uint32_t)(kr >> 32)) {
+                    pa = (int)(kr & 0xff);
+                    pr = (int)((kr >> 8) & 0xffffff);
+                }
+                if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
             }
         }
-        if (warp == 0 && ok && open >= 0) finalize(open);
     }
 
     // ---- tear-down --------------------------------------------------------------
@@ -497,8 +520,7 @@ __global__ void k_to_bf16(const float *__restrict__ x, int64_t n, int d,
 
 bool refine_mma_supported(int d, int max_mq) {
     if (d % kKB != 0 || d < kKB || max_mq < 1 || max_mq > kMaxQ) return false;
-    if (meta_ring(d / kKB) > kMaxMeta) return false;
-    return make_layout(d).total <= 232448;
+    return pick_stages(d) > 0;
 }
 
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
@@ -516,13 +538,15 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
                               const int32_t *cand, const int32_t *thr, int C, int2 *pair,
                               float *cand_dist, int *err, cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
-    const Layout Lo = make_layout(d);
+    const int ns = pick_stages(d);
+    if (ns == 0) return cudaErrorInvalidValue;
+    const Layout Lo = make_layout(d, ns);
     cudaError_t e = cudaFuncSetAttribute(k_refine_mma,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     const int gx = (C + kCandCTA - 1) / kCandCTA;
-    k_refine_mma<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec, vec16, vnorm16,
-                                                            set_off, d, cand, thr, C, pair, err);
+    k_refine_mma<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off,
+                                                            d, ns, cand, thr, C, pair, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, set_off, cand, thr, pair,
