@@ -50,6 +50,8 @@ def parse():
                     help="large: the 1M-set workload; small: the 2000-set test case; "
                          "profile: large-case shapes at 120k sets and 100 query sets, a few GB "
                          "on the device, for profiler captures")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="override the number of query sets of the workload (profiling)")
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--cpu-sample-sets", type=int, default=2000)
     ap.add_argument("--cpu-sample-queries", type=int, default=20)
@@ -58,11 +60,13 @@ def parse():
     return ap.parse_args()
 
 
-def workload_cfg(name):
+def workload_cfg(name, n_queries=0):
     from paper_2412_03301_gb300 import datagen
     c = dict(datagen.SMALL if name == "small" else datagen.LARGE)
     if name == "profile":
         c["n_sets"], c["n_queries"] = 120_000, 100
+    if n_queries > 0:
+        c["n_queries"] = n_queries
     c["A"], c["M"] = 3, 1
     return c
 
@@ -324,7 +328,7 @@ def run_reference(args, rank, world):
     from paper_2412_03301_gb300 import datagen
     from oracle import oracle
     oracle.build()
-    c = workload_cfg(args.workload)
+    c = workload_cfg(args.workload, args.queries)
     n_s = min(args.cpu_sample_sets, c["n_sets"])
     gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
     w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
@@ -363,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2412_03301_gb300 import bvss, datagen
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    c = workload_cfg(args.workload)
+    c = workload_cfg(args.workload, args.queries)
     stream = torch.cuda.current_stream(dev)
     w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
                          d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],

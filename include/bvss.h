@@ -86,12 +86,17 @@ typedef struct bvss_params {
                                different pair.  Needs an index built with BVSS_BUILD_BF16 and
                                query sets of at most 32 vectors (larger sets use the FP32 refine) */
 
+#define BVSS_SEARCH_POPC_SCAN 2  /* score sketches (Alg. 6 line 12) with CUDA-core popcounts over
+                                    the sets that pass layer 1, instead of the default tensor-core
+                                    form (one FP8 GEMM over all pairs, masked by layer 1); both
+                                    give identical h */
+
 typedef struct bvss_search {
     int32_t k;      /* results per query set, >= 1 */
     int32_t C;      /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
-    int32_t flags;  /* 0 or BVSS_SEARCH_FAST */
+    int32_t flags;  /* 0, or BVSS_SEARCH_FAST and/or BVSS_SEARCH_POPC_SCAN */
     int32_t reserved;
 } bvss_search;
 

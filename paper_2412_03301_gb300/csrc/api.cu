@@ -76,6 +76,9 @@ void free_workspace(Workspace &w) {
     dfree(w.sq);
     dfree(w.plist);
     dfree(w.h);
+    dfree(w.gate);
+    dfree(w.q8);
+    dfree(w.qpop);
     dfree(w.hist);
     dfree(w.thr);
     dfree(w.chunk);
@@ -97,6 +100,7 @@ void free_index(bvss_index *ix) {
     dfree(ix->proj);
     dfree(ix->codes);
     dfree(ix->sketch);
+    dfree(ix->spop);
     dfree(ix->count);
     dfree(ix->flag);
     dfree(ix->err);
@@ -197,6 +201,9 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         BVSS_CU(dalloc(&w.sq, (size_t)cq * W));
         BVSS_CU(dalloc(&w.plist, (size_t)cq * cA));
         BVSS_CU(dalloc(&w.h, (size_t)cq * hs));
+        BVSS_CU(dalloc(&w.gate, (size_t)cq * ix->NW));
+        BVSS_CU(dalloc(&w.q8, scan_mma_q8_bytes(cq, m)));
+        BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 128)));
         BVSS_CU(dalloc(&w.hist, (size_t)cq * (m + 1)));
         BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
         BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * 4));
@@ -276,8 +283,10 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (s->A < 1 || s->A > L || s->A > BVSS_MAX_A)
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
-    if (s->flags & ~BVSS_SEARCH_FAST) return fail(BVSS_EINVAL, "unknown search flags");
+    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN))
+        return fail(BVSS_EINVAL, "unknown search flags");
     const bool fast = (s->flags & BVSS_SEARCH_FAST) != 0;
+    const bool tensor_scan = (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
     if (fast && !ix->vec16)
         return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
     if (n_queries < 0) return fail(BVSS_EINVAL, "n_queries < 0");
@@ -349,8 +358,9 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
                                   tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
         // lines 5-12
-        BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, plane, ix->NW, gate_mode, w.sq, w.plist,
-                            A, nb, w.h, hs, st));
+        BVSS_CU(launch_scan(ix->sketch, ix->spop, ix->n_sets, W, plane, ix->NW, gate_mode, w.sq,
+                            w.plist, A, nb, w.gate, tensor_scan, w.q8, w.qpop, w.h, hs, ix->err,
+                            st));
         if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
         // lines 10-18
         BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
@@ -456,6 +466,7 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         BVSS_CU(dalloc(&ix->proj, (size_t)p.m * p.fanin));
         BVSS_CU(dalloc(&ix->codes, (size_t)nv * p.wta_l));
         BVSS_CU(dalloc(&ix->sketch, (size_t)n_sets * ix->W));
+        BVSS_CU(dalloc(&ix->spop, (size_t)n_sets));
         BVSS_CU(dalloc(&ix->count, (size_t)n_sets * p.m));
         BVSS_CU(dalloc(&ix->flag, 1));
         BVSS_CU(dalloc(&ix->err, 1));
@@ -487,6 +498,7 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
                               nullptr, st));
         BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,
                                      ix->count, st));
+        BVSS_CU(launch_sketch_pop(ix->sketch, n_sets, ix->W, ix->spop, st));
         const uint32_t *pl = nullptr;
         int r = get_plane(ix, 1, st, &pl);
         if (r) return r;

@@ -34,6 +34,9 @@ struct Workspace {
     uint32_t *sq = nullptr;       // query sketches                      cap_q x W
     uint16_t *plist = nullptr;    // top-A positions                     cap_q x cap_A
     uint16_t *h = nullptr;        // Hamming scores                      cap_q x N
+    uint32_t *gate = nullptr;     // layer-1 mask per 32-set tile        cap_q x NW
+    uint8_t *q8 = nullptr;        // query sketches as FP8 MMA operand   scan_mma_q8_bytes
+    int32_t *qpop = nullptr;      // |S_Q|                               cap_q rounded to 128
     uint32_t *hist = nullptr;     // histogram of h                      cap_q x (m + 1)
     int32_t *thr = nullptr;       // per query: H*, n_lt, take_eq, n_sel cap_q x 4
     int32_t *chunk = nullptr;     // per (query, chunk): lt, eq, eq_before, out_off
@@ -61,6 +64,7 @@ struct bvss_index {
     uint16_t *proj = nullptr;    // m x F
     uint16_t *codes = nullptr;   // n_vec x L, ascending positions
     uint32_t *sketch = nullptr;  // n_sets x W
+    int32_t *spop = nullptr;     // |S_i| per set
     uint8_t *count = nullptr;    // m x n_sets, position-major, saturated at 255
     int *flag = nullptr;         // device status word (build-time checks)
     int *err = nullptr;          // device error word: set when a kernel's bounded wait gives up
@@ -111,11 +115,24 @@ cudaError_t launch_gather_counts(const uint8_t *count, int m, int64_t n_sets,
 // ---- scan.cu ----------------------------------------------------------------
 // Alg. 6 lines 5-12: h[q][i] = popc(S_Q ^ S_i) for sets passing the gate.
 // gate_mode: 0 = every set passes (M = 0), 1 = gate planes, 2 = no set passes.
-// h rows have stride hs (a multiple of 64 elements).
-cudaError_t launch_scan(const uint32_t *sketch, int64_t n_sets, int W,
-                        const uint32_t *plane, int64_t NW, int gate_mode,
-                        const uint32_t *sq, const uint16_t *plist, int A, int n_q,
-                        uint16_t *h, int64_t hs, cudaStream_t st);
+// h rows have stride hs (a multiple of 64 elements).  gate: n_q x NW words of
+// scratch for the per-tile layer-1 masks (gate_mode 1 only).  tensor: score on
+// the tensor cores (scan_mma.cu; needs spop, q8 of scan_mma_q8_bytes(n_q, m)
+// bytes and qpop of n_q rounded up to 128 ints), else with CUDA-core popcounts.
+cudaError_t launch_scan(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
+                        const uint32_t *plane, int64_t NW, int gate_mode, const uint32_t *sq,
+                        const uint16_t *plist, int A, int n_q, uint32_t *gate, bool tensor,
+                        uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs, int *err,
+                        cudaStream_t st);
+
+// ---- scan_mma.cu ------------------------------------------------------------
+size_t scan_mma_q8_bytes(int64_t n_q, int m);
+cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int32_t *spop,
+                              cudaStream_t st);
+cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
+                            const uint32_t *gate, int64_t NW, int gate_mode, const uint32_t *sq,
+                            int n_q, uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs,
+                            int *err, cudaStream_t st);
 
 // ---- select.cu --------------------------------------------------------------
 // Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.

@@ -354,6 +354,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             const int buf = t & 1;
             ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
                  wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
+            ok = __all_sync(0xffffffffu, ok);   // the tensor-memory load below is warp-wide
             if (!ok) break;
             tc_fence_after();
             const Meta *mt = meta + (t % MR) * kRowsN;

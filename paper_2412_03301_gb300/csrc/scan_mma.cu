@@ -1,0 +1,374 @@
+// scan_mma.cu -- layer 2 of Alg. 6 (line 12) of arXiv 2412.03301 on the
+// 5th-generation tensor cores: Hamming scores of a batch of query sketches
+// against every database sketch as one dense binary contraction.
+//
+// For 0/1 vectors, popcount(S_Q xor S_i) = |S_Q| + |S_i| - 2 <S_Q, S_i>, and
+// the inner products of all (query, set) pairs are a GEMM with K = m.  A set
+// bit is encoded as the FP8 E4M3 value 2^-6 (byte 0x08), so each product is
+// 2^-12 and every partial sum (at most m * 2^-12 <= 8) is exact in the FP32
+// accumulator; <S_Q, S_i> = 4096 x accumulator.  Computing every pair and
+// masking with layer 1 (line 9) gives the same h as scoring only the sets of
+// F1: sets outside F1 get 0xFFFF.
+//
+// Tile: 128 query sketches (MMA M) x 256 set sketches (MMA N); K-blocks of
+// 128 bits (one 128-byte swizzle row of FP8).  Persistent CTAs walk the tiles
+// set-tile-major, so the query blocks of one set tile run side by side and
+// share its packed words through L2.
+//
+// Warp roles:
+//   warps 4-7  producers: per K-block, thread p copies the packed 16 bytes of
+//              set rows p and p + 128 into a private ring with cp.async (4
+//              K-blocks ahead), expands each bit to one FP8 byte into the
+//              swizzled stage, and thread 0 also starts the bulk copy of the
+//              query block's pre-expanded 16 KB;
+//   warp 8     one thread issues 4 MMAs (K = 32) per K-block into one of two
+//              TMEM accumulators of 256 columns;
+//   warps 0-3  epilogue: lane = query row; per 32 sets, one tensor-memory load,
+//              h = |S_Q| + |S_i| - 2 <S_Q, S_i>, the layer-1 bit, and 64-byte
+//              row stores into h.
+// Every wait gives up after 2 s (or when another role gave up), sets the error
+// word and lets all roles reach tear-down, where TMEM is released.
+#include "bvss_internal.cuh"
+#include "ptx_util.cuh"
+
+namespace bvss {
+
+namespace {
+
+constexpr int kQM = 128;              // query sketches per tile (MMA M)
+constexpr int kSN = 256;              // set sketches per tile (MMA N)
+constexpr int kNS = 4;                // stages
+constexpr int kPR = 6;                // packed-word ring slots per producer thread
+constexpr int kPLag = 4;              // packed-word copies in flight per producer thread
+constexpr int kThreads = 9 * 32;      // warps 0-3 epilogue, 4-7 producers, 8 MMA
+constexpr int kProd = 128;
+constexpr int kEpi = 128;
+constexpr uint32_t kTmemCols = 512;   // two accumulators of 256 columns
+constexpr int kAStage = kQM * 128;    // 16 KB
+constexpr int kBStage = kSN * 128;    // 32 KB
+constexpr float kDotScale = 4096.0f;  // 1 / (2^-6 * 2^-6)
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+constexpr int kOffA = 0;
+constexpr int kOffB = kOffA + kNS * kAStage;
+constexpr int kOffRing = kOffB + kNS * kBStage;
+constexpr int kOffSpop = kOffRing + kPR * 2 * kProd * 16;
+constexpr int kOffBars = kOffSpop + kSN * 4;
+constexpr int kOffMisc = kOffBars + (2 * kNS + 4) * 8;
+constexpr int kSmemBytes = kOffMisc + 16 + 1024;   // slack to align the base to 1024 bytes
+
+// 4 bits -> 4 bytes, each 0x08 (FP8 E4M3 2^-6) for a set bit, 0 otherwise.  The
+// four partial products of the multiply land in disjoint bit ranges (no carries).
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) {
+    return (nib * 0x01020408u) & 0x08080808u;
+}
+// 16 bits -> 16 FP8 bytes
+__device__ __forceinline__ uint4 spread16(uint32_t x) {
+    return make_uint4(spread4(x & 0xF), spread4((x >> 4) & 0xF), spread4((x >> 8) & 0xF),
+                      spread4((x >> 12) & 0xF));
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
+                                              volatile int *abort_flag, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (global_timer_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(err, 2);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Query sketches -> FP8 rows in the blocked, swizzled layout of the MMA's A
+// operand: block (qb, kb) holds query rows 128 qb .. 128 qb + 127, bits
+// 128 kb .. 128 kb + 127, as 16 KB exactly as the stage expects.  Rows past
+// n_q are zero.  Also |S_Q| per query.
+__global__ void k_expand_q(const uint32_t *__restrict__ sq, int n_q, int W, int QBK,
+                           uint8_t *__restrict__ q8, int32_t *__restrict__ qpop) {
+    const int KB = W / 4;
+    const int64_t total = (int64_t)QBK * kQM * KB;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / KB), kb = (int)(e - (e / KB) * KB);
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (r < n_q) w = *reinterpret_cast<const uint4 *>(sq + (int64_t)r * W + 4 * kb);
+        uint8_t *blk = q8 + ((int64_t)(r / kQM) * KB + kb) * kAStage;
+        const int rr = r % kQM;
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(blk + sw128_off(rr, c)) =
+                spread16(ws[c >> 1] >> (16 * (c & 1)));
+        if (kb == 0) {
+            int pc = 0;
+            if (r < n_q)
+                for (int i = 0; i < W; ++i) pc += __popc(sq[(int64_t)r * W + i]);
+            qpop[r] = pc;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, int64_t n_sets,
+           int W, const uint32_t *__restrict__ gate, int64_t NW, int gate_mode,
+           const uint8_t *__restrict__ q8, const int32_t *__restrict__ qpop, int n_q, int QBK,
+           uint16_t *__restrict__ h, int64_t hs, int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *stA = smem + kOffA;
+    unsigned char *stB = smem + kOffB;
+    unsigned char *ring = smem + kOffRing;
+    int32_t *sp_s = reinterpret_cast<int32_t *>(smem + kOffSpop);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBars);
+    uint64_t *full = bars, *empty = bars + kNS, *tfull = bars + 2 * kNS, *tempty = bars + 2 * kNS + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int KB = W / 4;
+    const int64_t n_st = (n_sets + kSN - 1) / kSN;
+    const int64_t n_tiles = n_st * QBK;
+    const int n_it = n_tiles > blockIdx.x
+                         ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x) + 1
+                         : 0;
+    const int64_t total = (int64_t)n_it * KB;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kNS; ++s) {
+            mbar_init(&full[s], kProd + 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpi / 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp >= 4 && warp <= 7) {
+        // ---- producers ------------------------------------------------------------
+        const int p = tid - 128;
+        auto issue = [&](int64_t u) {
+            if (u < total) {
+                const int it = (int)(u / KB), kb = (int)(u - (u / KB) * KB);
+                const int64_t st = (blockIdx.x + (int64_t)it * gridDim.x) / QBK;
+                const int slot = (int)(u % kPR);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int64_t n = st * kSN + p + 128 * j;
+                    if (n < n_sets)
+                        cp_async16(ring + ((slot * 2 + j) * kProd + p) * 16, sk + n * W + 4 * kb);
+                }
+            }
+            cp_async_commit();
+        };
+        for (int u = 0; u < kPLag; ++u) issue(u);
+        bool ok = true;
+        for (int64_t u = 0; u < total && ok; ++u) {
+            issue(u + kPLag);
+            cp_async_wait<kPLag>();
+            const int it = (int)(u / KB), kb = (int)(u - (u / KB) * KB);
+            const int64_t tau = blockIdx.x + (int64_t)it * gridDim.x;
+            const int64_t st = tau / QBK;
+            const int qb = (int)(tau - st * QBK);
+            const int s = (int)(u % kNS);
+            ok = wait_or_abort(&empty[s], (uint32_t)(((u / kNS) & 1) ^ 1), abort_flag, err);
+            if (!ok) break;
+            if (p == 0) {
+                mbar_arrive_expect_tx(&full[s], kAStage);
+                bulk_g2s(stA + s * kAStage, q8 + ((int64_t)qb * KB + kb) * kAStage, kAStage, &full[s]);
+            }
+            const int slot = (int)(u % kPR);
+            unsigned char *dst = stB + s * kBStage;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int nl = p + 128 * j;
+                uint4 w = make_uint4(0, 0, 0, 0);
+                if (st * kSN + nl < n_sets)
+                    w = *reinterpret_cast<const uint4 *>(ring + ((slot * 2 + j) * kProd + p) * 16);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<uint4 *>(dst + sw128_off(nl, c)) =
+                        spread16(ws[c >> 1] >> (16 * (c & 1)));
+            }
+            fence_proxy_async();
+            mbar_arrive(&full[s]);
+        }
+        cp_async_wait<0>();
+    } else if (warp == 8) {
+        // ---- MMA issue: one thread ------------------------------------------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_e4m3(kQM, kSN);
+            const uint32_t aaddr = smem_u32(stA), baddr = smem_u32(stB);
+            bool ok = true;
+            for (int it = 0; it < n_it && ok; ++it) {
+                const int buf = it & 1;
+                ok = wait_or_abort(&tempty[buf], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, err);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(buf * kSN);
+                for (int kb = 0; kb < KB && ok; ++kb) {
+                    const int64_t u = (int64_t)it * KB + kb;
+                    const int s = (int)(u % kNS);
+                    ok = wait_or_abort(&full[s], (uint32_t)((u / kNS) & 1), abort_flag, err);
+                    if (!ok) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        umma_f8(dt, umma_desc_sw128(aaddr + s * kAStage + 32 * k),
+                                umma_desc_sw128(baddr + s * kBStage + 32 * k), idesc,
+                                (kb | k) != 0 ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        // ---- epilogue: warps 0-3, lane = query row 32w + lane ------------------------
+        const int r = warp * 32 + lane;
+        const uint32_t g_const = gate_mode == 0 ? 0xffffffffu : 0u;
+        bool ok = true;
+        for (int it = 0; it < n_it; ++it) {
+            // all four warps leave together if one of them gave up
+            if (!named_barrier_and(1, kEpi, ok)) break;
+            const int64_t tau = blockIdx.x + (int64_t)it * gridDim.x;
+            const int64_t st = tau / QBK;
+            const int qb = (int)(tau - st * QBK);
+            const int64_t s0 = st * kSN;
+            for (int i = r; i < kSN; i += kEpi) sp_s[i] = s0 + i < n_sets ? spop[s0 + i] : 0;
+            named_barrier_sync(2, kEpi);
+            const int q = qb * kQM + r;
+            const bool qv = q < n_q;
+            const int qp = qv ? qpop[q] : 0;
+            const int buf = it & 1;
+            ok = __all_sync(0xffffffffu,
+                            wait_or_abort(&tfull[buf], (uint32_t)((it >> 1) & 1), abort_flag, err));
+            if (!ok) continue;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < kSN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kSN + c * 32), v);
+                const int64_t sb = s0 + 32 * c;
+                if (qv && sb < n_sets) {
+                    const uint32_t g = gate_mode == 1 ? gate[(int64_t)q * NW + sb / 32] : g_const;
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const int d0 = __float2int_rn(__uint_as_float(v[j]) * kDotScale);
+                        const int d1 = __float2int_rn(__uint_as_float(v[j + 1]) * kDotScale);
+                        const uint32_t h0 = ((g >> j) & 1) ? (uint32_t)(qp + sp_s[32 * c + j] - 2 * d0)
+                                                           : (uint32_t)kGatedOut;
+                        const uint32_t h1 = ((g >> (j + 1)) & 1)
+                                                ? (uint32_t)(qp + sp_s[32 * c + j + 1] - 2 * d1)
+                                                : (uint32_t)kGatedOut;
+                        pk[j >> 1] = (h0 & 0xffffu) | (h1 << 16);
+                    }
+                    uint16_t *dst = h + (int64_t)q * hs + sb;
+                    if (sb + 32 <= n_sets) {
+                        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                    } else {
+                        const int nv = (int)(n_sets - sb);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < nv) dst[j] = (uint16_t)(pk[j >> 1] >> (16 * (j & 1)));
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+
+    // ---- tear-down ----------------------------------------------------------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// |S_i| per database sketch, one warp per set
+__global__ void k_sketch_pop(const uint32_t *__restrict__ sk, int64_t n_sets, int W,
+                             int32_t *__restrict__ spop) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n_sets;
+         i += warps) {
+        int c = 0;
+        for (int k = lane; k < W; k += 32) c += __popc(sk[i * W + k]);
+        c = __reduce_add_sync(0xffffffffu, (uint32_t)c);
+        if (lane == 0) spop[i] = c;
+    }
+}
+
+int sm_count_mma() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+size_t scan_mma_q8_bytes(int64_t n_q, int m) {
+    return (size_t)((n_q + kQM - 1) / kQM) * kQM * (size_t)m;
+}
+
+cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int32_t *spop,
+                              cudaStream_t st) {
+    if (n_sets <= 0) return cudaSuccess;
+    int64_t g = (n_sets + 7) / 8;
+    if (g > (1 << 16)) g = 1 << 16;
+    k_sketch_pop<<<(unsigned)g, 256, 0, st>>>(sketch, n_sets, W, spop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
+                            const uint32_t *gate, int64_t NW, int gate_mode, const uint32_t *sq,
+                            int n_q, uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs,
+                            int *err, cudaStream_t st) {
+    if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
+    const int QBK = (n_q + kQM - 1) / kQM;
+    const int KB = W / 4;
+    {
+        const int64_t total = (int64_t)QBK * kQM * KB;
+        int64_t g = (total + 255) / 256;
+        if (g > 4096) g = 4096;
+        k_expand_q<<<(unsigned)g, 256, 0, st>>>(sq, n_q, W, QBK, q8, qpop);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_scan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int64_t n_tiles = ((n_sets + kSN - 1) / kSN) * QBK;
+    int64_t grid = sm_count_mma();
+    if (grid > n_tiles) grid = n_tiles;
+    k_scan_mma<<<(unsigned)grid, kThreads, kSmemBytes, st>>>(sketch, spop, n_sets, W, gate, NW,
+                                                             gate_mode, q8, qpop, n_q, QBK, h,
+                                                             hs, err);
+    return cudaGetLastError();
+}
+
+}  // namespace bvss

@@ -71,11 +71,12 @@ def test_database_filters(bv, small):
     assert np.array_equal(cnt, small.orc_ix.count.T)
 
 
-def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False):
+def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False, popc_scan=False):
     w = case.w
     qo = w["q_offsets"] if nq is None else w["q_offsets"][:nq + 1]
     nq = qo.shape[0] - 1
-    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M, fast=fast)
+    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M, fast=fast,
+                            popc_scan=popc_scan)
     torch.cuda.synchronize()
     qpos = _np(t["qpos"], np.uint16)
     h = _np(t["h"], np.uint16)
@@ -107,6 +108,41 @@ def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False):
 def test_query_parity_default(bv, orc, small):
     s = datagen.SMALL
     _check_query(bv, orc, small, k=s["k"], C=s["C"], A=3, M=1)
+
+
+def test_query_parity_popcount_scan(bv, orc, small):
+    """The CUDA-core popcount scan (gated sets only) against the oracle."""
+    s = datagen.SMALL
+    _check_query(bv, orc, small, k=s["k"], C=s["C"], A=3, M=1, popc_scan=True)
+    _check_query(bv, orc, small, k=10, C=50, A=2, M=0, nq=20, popc_scan=True)
+
+
+@pytest.mark.parametrize("n_sets,nq,m,L,A,M", [
+    (1000, 300, 4096, 64, 3, 1),     # ragged set tiles, three query blocks (last ragged)
+    (257, 129, 128, 8, 2, 1),        # one K-block, one set past a tile, one query past a block
+    (600, 40, 8192, 100, 5, 0),      # every set passes layer 1
+    (600, 40, 2048, 32, 3, 300),     # no set passes layer 1
+    (300, 1, 1024, 16, 1, 2),        # a single query
+])
+def test_scan_forms_agree(bv, orc, n_sets, nq, m, L, A, M):
+    """Tensor-core scan (all pairs, masked by layer 1) and popcount scan give the
+    same h bit for bit; the tensor-core form also matches the oracle on a sample."""
+    w = _workload(n_sets, 3, 12, 32, 16, nq, 2, 9, m, 4, seed=n_sets + nq)
+    ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=L)
+    qv = w["q_vectors"].cuda()
+    C = min(50, n_sets)
+    a = bv.bvss_query_trace(ix, qv, w["q_offsets"], k=5, C=C, A=A, M=M)
+    b = bv.bvss_query_trace(ix, qv, w["q_offsets"], k=5, C=C, A=A, M=M, popc_scan=True)
+    torch.cuda.synchronize()
+    ha, hb = _np(a["h"], np.uint16), _np(b["h"], np.uint16)
+    assert np.array_equal(ha, hb)
+    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"])
+    oix = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], L)
+    qo = w["q_offsets"]
+    for q in sorted({0, nq // 2, nq - 1}):
+        r = orc.query(oix, w["q_vectors"].numpy()[qo[q]:qo[q + 1]], k=5, C=C, A=A, M=M)
+        want = np.where(r["gate"] == 1, r["h"], 0xFFFF)
+        assert np.array_equal(ha[q].astype(np.int64), want.astype(np.int64)), q
 
 
 def test_query_results_without_trace_match(bv, small):
