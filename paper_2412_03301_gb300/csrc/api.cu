@@ -203,7 +203,7 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         BVSS_CU(dalloc(&w.h, (size_t)cq * hs));
         BVSS_CU(dalloc(&w.gate, (size_t)cq * ix->NW));
         BVSS_CU(dalloc(&w.q8, scan_mma_q8_bytes(cq, m)));
-        BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 128)));
+        BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 256)));
         BVSS_CU(dalloc(&w.hist, (size_t)cq * (m + 1)));
         BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
         BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * 4));

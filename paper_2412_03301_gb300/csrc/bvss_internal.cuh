@@ -36,7 +36,7 @@ struct Workspace {
     uint16_t *h = nullptr;        // Hamming scores                      cap_q x N
     uint32_t *gate = nullptr;     // layer-1 mask per 32-set tile        cap_q x NW
     uint8_t *q8 = nullptr;        // query sketches as FP8 MMA operand   scan_mma_q8_bytes
-    int32_t *qpop = nullptr;      // |S_Q|                               cap_q rounded to 128
+    int32_t *qpop = nullptr;      // |S_Q|                               cap_q rounded to 256
     uint32_t *hist = nullptr;     // histogram of h                      cap_q x (m + 1)
     int32_t *thr = nullptr;       // per query: H*, n_lt, take_eq, n_sel cap_q x 4
     int32_t *chunk = nullptr;     // per (query, chunk): lt, eq, eq_before, out_off
@@ -118,7 +118,7 @@ cudaError_t launch_gather_counts(const uint8_t *count, int m, int64_t n_sets,
 // h rows have stride hs (a multiple of 64 elements).  gate: n_q x NW words of
 // scratch for the per-tile layer-1 masks (gate_mode 1 only).  tensor: score on
 // the tensor cores (scan_mma.cu; needs spop, q8 of scan_mma_q8_bytes(n_q, m)
-// bytes and qpop of n_q rounded up to 128 ints), else with CUDA-core popcounts.
+// bytes and qpop of n_q rounded up to 256 ints), else with CUDA-core popcounts.
 cudaError_t launch_scan(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
                         const uint32_t *plane, int64_t NW, int gate_mode, const uint32_t *sq,
                         const uint16_t *plist, int A, int n_q, uint32_t *gate, bool tensor,

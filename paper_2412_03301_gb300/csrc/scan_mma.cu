@@ -10,22 +10,23 @@
 // masking with layer 1 (line 9) gives the same h as scoring only the sets of
 // F1: sets outside F1 get 0xFFFF.
 //
-// Tile: 128 query sketches (MMA M) x 256 set sketches (MMA N); K-blocks of
-// 128 bits (one 128-byte swizzle row of FP8).  Persistent CTAs walk the tiles
+// Tile: 256 query sketches (two MMAs of M = 128) x 128 set sketches (MMA N),
+// so every expanded set row feeds 256 queries; K-blocks of 128 bits (one
+// 128-byte swizzle row of FP8).  Persistent CTAs walk the tiles
 // set-tile-major, so the query blocks of one set tile run side by side and
 // share its packed words through L2.
 //
 // Warp roles:
-//   warps 4-7  producers: per K-block, thread p copies the packed 16 bytes of
-//              set rows p and p + 128 into a private ring with cp.async (4
+//   warps 4-11 producers: per K-block, thread p copies 8 packed bytes (half
+//              of set row p mod 128) into a private ring with cp.async (6
 //              K-blocks ahead), expands each bit to one FP8 byte into the
 //              swizzled stage, and thread 0 also starts the bulk copy of the
-//              query block's pre-expanded 16 KB;
-//   warp 8     one thread issues 4 MMAs (K = 32) per K-block into one of two
-//              TMEM accumulators of 256 columns;
-//   warps 0-3  epilogue: lane = query row; per 32 sets, one tensor-memory load,
-//              h = |S_Q| + |S_i| - 2 <S_Q, S_i>, the layer-1 bit, and 64-byte
-//              row stores into h.
+//              query block pair's pre-expanded 32 KB;
+//   warp 12    one thread issues 2 x 4 MMAs (K = 32) per K-block into one of
+//              two pairs of TMEM accumulators of 128 columns;
+//   warps 0-3  epilogue: lane = query row of each block; per 32 sets, one
+//              tensor-memory load, h = |S_Q| + |S_i| - 2 <S_Q, S_i>, the
+//              layer-1 bit, and 64-byte row stores into h.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include "bvss_internal.cuh"
@@ -35,24 +36,25 @@ namespace bvss {
 
 namespace {
 
-constexpr int kQM = 128;              // query sketches per tile (MMA M)
-constexpr int kSN = 256;              // set sketches per tile (MMA N)
+constexpr int kQM = 128;              // query sketches per MMA (M); a tile holds two blocks
+constexpr int kSN = 128;              // set sketches per tile (MMA N)
 constexpr int kNS = 4;                // stages
-constexpr int kPR = 6;                // packed-word ring slots per producer thread
-constexpr int kPLag = 4;              // packed-word copies in flight per producer thread
-constexpr int kThreads = 9 * 32;      // warps 0-3 epilogue, 4-7 producers, 8 MMA
-constexpr int kProd = 128;
+constexpr int kPR = 8;                // packed-word ring slots per producer thread
+constexpr int kPLag = 6;              // packed-word copies in flight per producer thread
+constexpr int kThreads = 13 * 32;     // warps 0-3 epilogue, 4-11 producers, 12 MMA
+constexpr int kProd = 2 * kSN;        // two producer threads per set row (8 bytes each)
 constexpr int kEpi = 128;
-constexpr uint32_t kTmemCols = 512;   // two accumulators of 256 columns
-constexpr int kAStage = kQM * 128;    // 16 KB
-constexpr int kBStage = kSN * 128;    // 32 KB
+constexpr uint32_t kTmemCols = 512;   // two buffers x two query blocks x 128 columns
+constexpr int kQBlk = kQM * 128;      // 16 KB: one query block's K-block
+constexpr int kAStage = 2 * kQBlk;    // 32 KB: the pair
+constexpr int kBStage = kSN * 128;    // 16 KB
 constexpr float kDotScale = 4096.0f;  // 1 / (2^-6 * 2^-6)
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kNS * kAStage;
 constexpr int kOffRing = kOffB + kNS * kBStage;
-constexpr int kOffSpop = kOffRing + kPR * 2 * kProd * 16;
+constexpr int kOffSpop = kOffRing + kPR * kProd * 8;
 constexpr int kOffBars = kOffSpop + kSN * 4;
 constexpr int kOffMisc = kOffBars + (2 * kNS + 4) * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;   // slack to align the base to 1024 bytes
@@ -84,19 +86,20 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
 }
 
 // Query sketches -> FP8 rows in the blocked, swizzled layout of the MMA's A
-// operand: block (qb, kb) holds query rows 128 qb .. 128 qb + 127, bits
-// 128 kb .. 128 kb + 127, as 16 KB exactly as the stage expects.  Rows past
-// n_q are zero.  Also |S_Q| per query.
-__global__ void k_expand_q(const uint32_t *__restrict__ sq, int n_q, int W, int QBK,
+// operand: block (qp, kb) holds query rows 256 qp .. 256 qp + 255, bits
+// 128 kb .. 128 kb + 127, as two 16 KB halves of 128 rows exactly as the stage
+// expects.  Rows past n_q are zero.  Also |S_Q| per query.
+__global__ void k_expand_q(const uint32_t *__restrict__ sq, int n_q, int W, int QP,
                            uint8_t *__restrict__ q8, int32_t *__restrict__ qpop) {
     const int KB = W / 4;
-    const int64_t total = (int64_t)QBK * kQM * KB;
+    const int64_t total = (int64_t)QP * 2 * kQM * KB;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / KB), kb = (int)(e - (e / KB) * KB);
         uint4 w = make_uint4(0, 0, 0, 0);
         if (r < n_q) w = *reinterpret_cast<const uint4 *>(sq + (int64_t)r * W + 4 * kb);
-        uint8_t *blk = q8 + ((int64_t)(r / kQM) * KB + kb) * kAStage;
+        uint8_t *blk = q8 + ((int64_t)(r / (2 * kQM)) * KB + kb) * kAStage +
+                       ((r / kQM) & 1) * kQBlk;
         const int rr = r % kQM;
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -115,7 +118,7 @@ __global__ void k_expand_q(const uint32_t *__restrict__ sq, int n_q, int W, int 
 __global__ void __launch_bounds__(kThreads, 1)
 k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, int64_t n_sets,
            int W, const uint32_t *__restrict__ gate, int64_t NW, int gate_mode,
-           const uint8_t *__restrict__ q8, const int32_t *__restrict__ qpop, int n_q, int QBK,
+           const uint8_t *__restrict__ q8, const int32_t *__restrict__ qpop, int n_q, int QP,
            uint16_t *__restrict__ h, int64_t hs, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -131,12 +134,8 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int KB = W / 4;
-    const int64_t n_st = (n_sets + kSN - 1) / kSN;
-    const int64_t n_tiles = n_st * QBK;
-    const int n_it = n_tiles > blockIdx.x
-                         ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x) + 1
-                         : 0;
-    const int64_t total = (int64_t)n_it * KB;
+    const int n_tiles = (int)((n_sets + kSN - 1) / kSN) * QP;   // < 2^31 (host check)
+    const int n_it = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     if (tid == 0) {
@@ -156,140 +155,160 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 4 && warp <= 7) {
-        // ---- producers ------------------------------------------------------------
+    if (warp >= 4 && warp <= 11) {
+        // ---- producers: thread p expands half (p >> 7) of set row p & 127 ----------
         const int p = tid - 128;
-        auto issue = [&](int64_t u) {
-            if (u < total) {
-                const int it = (int)(u / KB), kb = (int)(u - (u / KB) * KB);
-                const int64_t st = (blockIdx.x + (int64_t)it * gridDim.x) / QBK;
-                const int slot = (int)(u % kPR);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int64_t n = st * kSN + p + 128 * j;
-                    if (n < n_sets)
-                        cp_async16(ring + ((slot * 2 + j) * kProd + p) * 16, sk + n * W + 4 * kb);
+        const int pr = p & (kSN - 1), ph = p >> 7;
+        // the unit (tile, K-block) whose packed words are copied next
+        int i_it = 0, i_kb = 0, i_u = 0;
+        int64_t i_row = (int64_t)((int)blockIdx.x / QP) * kSN + pr;
+        auto issue = [&]() {
+            if (i_it < n_it) {
+                if (i_row < n_sets)
+                    cp_async8(ring + ((i_u % kPR) * kProd + p) * 8, sk + i_row * W + 4 * i_kb + 2 * ph);
+                if (++i_kb == KB) {
+                    i_kb = 0;
+                    ++i_it;
+                    i_row = (int64_t)(((int)blockIdx.x + i_it * (int)gridDim.x) / QP) * kSN + pr;
                 }
             }
+            ++i_u;
             cp_async_commit();
         };
-        for (int u = 0; u < kPLag; ++u) issue(u);
+        for (int i = 0; i < kPLag; ++i) issue();
         bool ok = true;
-        for (int64_t u = 0; u < total && ok; ++u) {
-            issue(u + kPLag);
-            cp_async_wait<kPLag>();
-            const int it = (int)(u / KB), kb = (int)(u - (u / KB) * KB);
-            const int64_t tau = blockIdx.x + (int64_t)it * gridDim.x;
-            const int64_t st = tau / QBK;
-            const int qb = (int)(tau - st * QBK);
-            const int s = (int)(u % kNS);
-            ok = wait_or_abort(&empty[s], (uint32_t)(((u / kNS) & 1) ^ 1), abort_flag, err);
-            if (!ok) break;
-            if (p == 0) {
-                mbar_arrive_expect_tx(&full[s], kAStage);
-                bulk_g2s(stA + s * kAStage, q8 + ((int64_t)qb * KB + kb) * kAStage, kAStage, &full[s]);
-            }
-            const int slot = (int)(u % kPR);
-            unsigned char *dst = stB + s * kBStage;
+        int u = 0;
+        for (int it = 0; it < n_it && ok; ++it) {
+            const int tau = (int)blockIdx.x + it * (int)gridDim.x;
+            const int st = tau / QP, qp = tau - st * QP;
+            const bool row_ok = (int64_t)st * kSN + pr < n_sets;
+            const uint8_t *qsrc = q8 + (int64_t)qp * KB * kAStage;
+            for (int kb = 0; kb < KB; ++kb, ++u) {
+                issue();
+                cp_async_wait<kPLag>();
+                const int s = u % kNS;
+                ok = wait_or_abort(&empty[s], (uint32_t)(((u / kNS) & 1) ^ 1), abort_flag, err);
+                if (!ok) break;
+                if (p == 0) {
+                    mbar_arrive_expect_tx(&full[s], kAStage);
+                    bulk_g2s(stA + s * kAStage, qsrc + (int64_t)kb * kAStage, kAStage, &full[s]);
+                }
+                uint2 w = make_uint2(0, 0);
+                if (row_ok) w = *reinterpret_cast<const uint2 *>(ring + ((u % kPR) * kProd + p) * 8);
+                unsigned char *dst = stB + s * kBStage;
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int nl = p + 128 * j;
-                uint4 w = make_uint4(0, 0, 0, 0);
-                if (st * kSN + nl < n_sets)
-                    w = *reinterpret_cast<const uint4 *>(ring + ((slot * 2 + j) * kProd + p) * 16);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    *reinterpret_cast<uint4 *>(dst + sw128_off(nl, c)) =
-                        spread16(ws[c >> 1] >> (16 * (c & 1)));
+                for (int c = 0; c < 4; ++c)
+                    *reinterpret_cast<uint4 *>(dst + sw128_off(pr, 4 * ph + c)) =
+                        spread16((c < 2 ? w.x : w.y) >> (16 * (c & 1)));
+                fence_proxy_async();
+                mbar_arrive(&full[s]);
             }
-            fence_proxy_async();
-            mbar_arrive(&full[s]);
         }
         cp_async_wait<0>();
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // ---- MMA issue: one thread ------------------------------------------------
         if (lane == 0) {
             constexpr uint32_t idesc = umma_idesc_e4m3(kQM, kSN);
             const uint32_t aaddr = smem_u32(stA), baddr = smem_u32(stB);
             bool ok = true;
+            int u = 0;
             for (int it = 0; it < n_it && ok; ++it) {
                 const int buf = it & 1;
                 ok = wait_or_abort(&tempty[buf], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * kSN);
-                for (int kb = 0; kb < KB && ok; ++kb) {
-                    const int64_t u = (int64_t)it * KB + kb;
-                    const int s = (int)(u % kNS);
+                const uint32_t dt = tmem + (uint32_t)(buf * 2 * kSN);
+                for (int kb = 0; kb < KB && ok; ++kb, ++u) {
+                    const int s = u % kNS;
                     ok = wait_or_abort(&full[s], (uint32_t)((u / kNS) & 1), abort_flag, err);
                     if (!ok) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        umma_f8(dt, umma_desc_sw128(aaddr + s * kAStage + 32 * k),
-                                umma_desc_sw128(baddr + s * kBStage + 32 * k), idesc,
-                                (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t db = umma_desc_sw128(baddr + s * kBStage + 32 * k);
+                        const uint32_t acc = (kb | k) != 0 ? 1u : 0u;
+                        umma_f8(dt, umma_desc_sw128(aaddr + s * kAStage + 32 * k), db, idesc, acc);
+                        umma_f8(dt + kSN, umma_desc_sw128(aaddr + s * kAStage + kQBlk + 32 * k), db,
+                                idesc, acc);
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&tfull[buf]);
             }
         }
     } else {
-        // ---- epilogue: warps 0-3, lane = query row 32w + lane ------------------------
+        // ---- epilogue: warps 0-3, lane = query row 32w + lane of each block -------
         const int r = warp * 32 + lane;
         const uint32_t g_const = gate_mode == 0 ? 0xffffffffu : 0u;
         bool ok = true;
         for (int it = 0; it < n_it; ++it) {
             // all four warps leave together if one of them gave up
             if (!named_barrier_and(1, kEpi, ok)) break;
-            const int64_t tau = blockIdx.x + (int64_t)it * gridDim.x;
-            const int64_t st = tau / QBK;
-            const int qb = (int)(tau - st * QBK);
-            const int64_t s0 = st * kSN;
-            for (int i = r; i < kSN; i += kEpi) sp_s[i] = s0 + i < n_sets ? spop[s0 + i] : 0;
+            const int tau = (int)blockIdx.x + it * (int)gridDim.x;
+            const int st = tau / QP, qp = tau - st * QP;
+            const int64_t s0 = (int64_t)st * kSN;
+            if (r < kSN) sp_s[r] = s0 + r < n_sets ? spop[s0 + r] : 0;
             named_barrier_sync(2, kEpi);
-            const int q = qb * kQM + r;
-            const bool qv = q < n_q;
-            const int qp = qv ? qpop[q] : 0;
+            // layer-1 words of the tile's 4 groups of 32 sets for both queries, before the wait
+            int qh[2], qpc[2];
+            uint32_t gw[2][kSN / 32];
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2) {
+                const int q = (2 * qp + b2) * kQM + r;
+                const bool qv = q < n_q;
+                qh[b2] = qv ? q : -1;
+                qpc[b2] = qv ? qpop[q] : 0;
+#pragma unroll
+                for (int c = 0; c < kSN / 32; ++c)
+                    gw[b2][c] = gate_mode == 1
+                                    ? (qv && s0 + 32 * c < n_sets ? gate[(int64_t)q * NW + (s0 >> 5) + c] : 0u)
+                                    : g_const;
+            }
             const int buf = it & 1;
             ok = __all_sync(0xffffffffu,
                             wait_or_abort(&tfull[buf], (uint32_t)((it >> 1) & 1), abort_flag, err));
             if (!ok) continue;
             tc_fence_after();
-#pragma unroll 1
-            for (int c = 0; c < kSN / 32; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kSN + c * 32), v);
-                const int64_t sb = s0 + 32 * c;
-                if (qv && sb < n_sets) {
-                    const uint32_t g = gate_mode == 1 ? gate[(int64_t)q * NW + sb / 32] : g_const;
-                    uint32_t pk[16];
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const int d0 = __float2int_rn(__uint_as_float(v[j]) * kDotScale);
-                        const int d1 = __float2int_rn(__uint_as_float(v[j + 1]) * kDotScale);
-                        const uint32_t h0 = ((g >> j) & 1) ? (uint32_t)(qp + sp_s[32 * c + j] - 2 * d0)
-                                                           : (uint32_t)kGatedOut;
-                        const uint32_t h1 = ((g >> (j + 1)) & 1)
-                                                ? (uint32_t)(qp + sp_s[32 * c + j + 1] - 2 * d1)
-                                                : (uint32_t)kGatedOut;
-                        pk[j >> 1] = (h0 & 0xffffu) | (h1 << 16);
+            for (int b2 = 0; b2 < 2; ++b2) {
+#pragma unroll
+                for (int c = 0; c < kSN / 32; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) +
+                                  (uint32_t)(buf * 2 * kSN + b2 * kSN + c * 32),
+                              v);
+                    const int64_t sb = s0 + 32 * c;
+                    if (qh[b2] >= 0 && sb < n_sets) {
+                        const uint32_t g = gw[b2][c];
+                        const int qp_b = qpc[b2];
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
+                            const int d0 = __float2int_rn(__uint_as_float(v[j]) * kDotScale);
+                            const int d1 = __float2int_rn(__uint_as_float(v[j + 1]) * kDotScale);
+                            const uint32_t h0 = ((g >> j) & 1)
+                                                    ? (uint32_t)(qp_b + sp_s[32 * c + j] - 2 * d0)
+                                                    : (uint32_t)kGatedOut;
+                            const uint32_t h1 = ((g >> (j + 1)) & 1)
+                                                    ? (uint32_t)(qp_b + sp_s[32 * c + j + 1] - 2 * d1)
+                                                    : (uint32_t)kGatedOut;
+                            pk[j >> 1] = (h0 & 0xffffu) | (h1 << 16);
+                        }
+                        uint16_t *dst = h + (int64_t)qh[b2] * hs + sb;
+                        if (sb + 32 <= n_sets) {
+                            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                        } else {
+                            const int nv = (int)(n_sets - sb);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (j < nv) dst[j] = (uint16_t)(pk[j >> 1] >> (16 * (j & 1)));
+                        }
                     }
-                    uint16_t *dst = h + (int64_t)q * hs + sb;
-                    if (sb + 32 <= n_sets) {
-                        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            d4[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
-                    } else {
-                        const int nv = (int)(n_sets - sb);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < nv) dst[j] = (uint16_t)(pk[j >> 1] >> (16 * (j & 1)));
-                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -332,7 +351,7 @@ int sm_count_mma() {
 }  // namespace
 
 size_t scan_mma_q8_bytes(int64_t n_q, int m) {
-    return (size_t)((n_q + kQM - 1) / kQM) * kQM * (size_t)m;
+    return (size_t)((n_q + 2 * kQM - 1) / (2 * kQM)) * 2 * kQM * (size_t)m;
 }
 
 cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int32_t *spop,
@@ -349,24 +368,25 @@ cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t
                             int n_q, uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs,
                             int *err, cudaStream_t st) {
     if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
-    const int QBK = (n_q + kQM - 1) / kQM;
+    const int QP = (n_q + 2 * kQM - 1) / (2 * kQM);
     const int KB = W / 4;
     {
-        const int64_t total = (int64_t)QBK * kQM * KB;
+        const int64_t total = (int64_t)QP * 2 * kQM * KB;
         int64_t g = (total + 255) / 256;
         if (g > 4096) g = 4096;
-        k_expand_q<<<(unsigned)g, 256, 0, st>>>(sq, n_q, W, QBK, q8, qpop);
+        k_expand_q<<<(unsigned)g, 256, 0, st>>>(sq, n_q, W, QP, q8, qpop);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaFuncSetAttribute(k_scan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
     if (e != cudaSuccess) return e;
-    const int64_t n_tiles = ((n_sets + kSN - 1) / kSN) * QBK;
+    const int64_t n_tiles = ((n_sets + kSN - 1) / kSN) * QP;
+    if (n_tiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     int64_t grid = sm_count_mma();
     if (grid > n_tiles) grid = n_tiles;
     k_scan_mma<<<(unsigned)grid, kThreads, kSmemBytes, st>>>(sketch, spop, n_sets, W, gate, NW,
-                                                             gate_mode, q8, qpop, n_q, QBK, h,
+                                                             gate_mode, q8, qpop, n_q, QP, h,
                                                              hs, err);
     return cudaGetLastError();
 }
