@@ -1,7 +1,7 @@
 // refine_mma.cu -- exact re-rank of Alg. 6 (lines 19-22) of arXiv 2412.03301 on
 // the 5th-generation tensor cores (tcgen05), from BF16 copies of the vectors.
 //
-// One CTA takes one query set (at most 32 vectors) and up to 128 of its
+// One CTA takes one query set (at most 32 vectors) and up to 512 of its
 // candidates, whose rows, concatenated in candidate order, are cut into tiles
 // of 128 rows.  For every tile the dot products of all (row, query vector)
 // pairs are one 128 x 32 x d GEMM: the tile rows are the A operand (M = 128),
@@ -10,10 +10,11 @@
 // column = query vector).
 //
 // Warp roles (no block-wide barrier between set-up and tear-down):
-//   warps 4-7  producers: each thread gathers one row of every tile, one
-//              64-dimension block at a time, with 16-byte cp.async copies
-//              straight into the swizzled stage (a ring of 6-8 stages, 5 kept
-//              in flight per thread), then signals the stage's mbarrier;
+//   warps 4-7  producers: gather the tile rows one 64-dimension block at a
+//              time with 16-byte cp.async copies straight into the swizzled
+//              stage (8 lanes per 128-byte row segment, so copies coalesce; a
+//              ring of 5-8 stages, 4 or 5 kept in flight), then signal the
+//              stage's mbarrier;
 //   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
 //              one of two TMEM accumulators;
@@ -26,9 +27,11 @@
 //              rows and the maximum of the rows' minima, merged into
 //              per-candidate slots with shared-memory atomics (a candidate's
 //              rows may span warps and tiles).
-// After the last tile, each candidate's Hausdorff value (Def. 4) is the larger
-// of max over query vectors of the slot minima and the slot maximum; the pair
-// attaining it is recorded, and k_rescore computes that pair's distance
+// After each tile, every candidate whose last row has been seen is finished:
+// its Hausdorff value (Def. 4) is the larger of max over query vectors of the
+// slot minima and the slot maximum, the pair attaining it is recorded and the
+// slot is cleared.  Slots form a ring of 160 (candidates open at one time have
+// rows in one tile, so at most 128 of them), and k_rescore computes each pair's distance
 // directly in FP32 from the original vectors (one warp per candidate) and writes
 // the square root as the candidate's distance.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
@@ -45,8 +48,8 @@ namespace {
 constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
 constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
 constexpr int kMaxNS = 8;            // stages in the ring, at most
-constexpr int kLag = 5;              // stages a producer thread keeps in flight
-constexpr int kCandCTA = 128;        // candidates per CTA
+constexpr int kCandCTA = 512;        // candidates per CTA
+constexpr int kSlots = 160;          // per-candidate accumulator ring
 constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
 constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
 constexpr int kProd = 128;
@@ -82,8 +85,8 @@ __host__ __device__ inline Layout make_layout(int d, int ns) {
     L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
     L.dist = o;    o += kRowsN * 128;              // row-phase distances, 32 per row
-    L.cmin = o;    o += kCandCTA * kMaxQ * 8;      // per (candidate, query vector) minimum
-    L.ckey = o;    o += kCandCTA * 8;              // per candidate maximum of row minima
+    L.cmin = o;    o += kSlots * kMaxQ * 8;        // per (open candidate, query vector) minimum
+    L.ckey = o;    o += kSlots * 8;                // per open candidate maximum of row minima
     L.rkey = o;    o += kRowsN * 8;                // per row minimum, this tile
     L.bars = o;    o += (2 * kMaxNS + 4 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
@@ -94,9 +97,12 @@ __host__ __device__ inline Layout make_layout(int d, int ns) {
     return L;
 }
 
-// most stages that fit, at least kLag + 1 (a producer holds kLag arrivals back)
+// stages a producer keeps in flight for a ring of ns (it holds that many arrivals back)
+inline int lag_for(int ns) { return ns >= 6 ? 5 : 4; }
+
+// most stages that fit, at least 5
 inline int pick_stages(int d) {
-    for (int ns = kMaxNS; ns > kLag; --ns)
+    for (int ns = kMaxNS; ns >= 5; --ns)
         if (make_layout(d, ns).total <= kSmemMax && meta_ring(d / kKB, ns) <= kMaxMeta) return ns;
     return 0;
 }
@@ -121,6 +127,7 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | low;
 }
 
+template <int LAG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
@@ -158,38 +165,21 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lo.misc + 4);
 
     // ---- set-up -------------------------------------------------------------
-    if (warp == 0) {
-        // candidate table: sizes, exclusive prefix of the rows, first global rows
-        int n4[4], s = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int c = lane * 4 + i;
-            n4[i] = 0;
-            if (c < ncand) {
-                const int64_t id = cand[(int64_t)q * C + c0 + c];
-                const int64_t g = set_off[id];
-                grow0[c] = g;
-                n4[i] = (int)(set_off[id + 1] - g);
-            }
-            s += n4[i];
+    // candidate table: first global row and size of each candidate (sizes are
+    // turned into an exclusive prefix of the rows below)
+    for (int c = tid; c < kCandCTA; c += kThreads) {
+        int n = 0;
+        if (c < ncand) {
+            const int64_t id = cand[(int64_t)q * C + c0 + c];
+            const int64_t g = set_off[id];
+            grow0[c] = g;
+            n = (int)(set_off[id + 1] - g);
         }
-        int incl = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int run = incl - s;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            vrow0[lane * 4 + i] = run;
-            run += n4[i];
-        }
-        if (lane == 31) vrow0[kCandCTA] = incl;    // rows of the CTA
-        tmem_alloc(tmem_slot, kTmemCols);
+        vrow0[c] = n;
     }
-    for (int e = tid; e < kCandCTA * kMaxQ; e += kThreads) cmin[e] = ~0ull;
-    for (int e = tid; e < kCandCTA; e += kThreads) ckey[e] = 0ull;
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    for (int e = tid; e < kSlots * kMaxQ; e += kThreads) cmin[e] = ~0ull;
+    for (int e = tid; e < kSlots; e += kThreads) ckey[e] = 0ull;
     // query rows 0..31 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
     const int nch = d / 8;                         // 16-byte chunks per row
     for (int e = tid; e < kMaxQ * nch; e += kThreads) {
@@ -228,8 +218,31 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         fence_mbar_init();
     }
     __syncthreads();
-    // squared norms of the staged BF16 query rows, one warp per row
-    for (int a = warp; a < kMaxQ; a += kThreads / 32) {
+    if (warp == 0) {
+        // exclusive prefix of the candidate sizes, 16 per lane
+        constexpr int kPer = kCandCTA / 32;
+        int n[kPer], sum = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            n[i] = vrow0[lane * kPer + i];
+            sum += n[i];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            vrow0[lane * kPer + i] = run;
+            run += n[i];
+        }
+        if (lane == 31) vrow0[kCandCTA] = incl;
+    }
+    // squared norms of the staged BF16 query rows, one warp per row (warps 1-8)
+    for (int a = warp - 1; warp > 0 && a < kMaxQ; a += kThreads / 32 - 1) {
         float sq = 0.0f;
         for (int ch = lane; ch < nch; ch += 32) {
             const uint4 pk =
@@ -250,16 +263,19 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int R = vrow0[kCandCTA];
+    const int R = vrow0[ncand];
     const int n_tiles = (R + kRowsN - 1) / kRowsN;
     const int total = n_tiles * KB;
 
     if (warp >= 4 && warp <= 7) {
-        // ---- producers: thread p fills row p of every tile ----------------------
+        // ---- producers ----------------------------------------------------------
+        // Thread p locates row p of every tile (its candidate, row and norm, for
+        // the row metadata); the copies are coalesced instead: lane group p / 8
+        // copies rows p / 8 + 16 k (k = 0..7), lane p % 8 one 16-byte chunk of
+        // each, so a warp instruction moves four whole 128-byte row segments.
         const int p = tid - 128;
-        // where row p of tile t lives; its norm is loaded one tile ahead of use
+        const int pc = p & 7, pg = p >> 3;
         int n_slot = -1, n_row = 0;
-        int64_t n_grow = 0;
         float n_vn = 0.0f;
         auto locate = [&](int t) {
             const int v = t * kRowsN + p;
@@ -269,51 +285,55 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             if (v < R) {
                 int c = 0;
 #pragma unroll
-                for (int b = 64; b > 0; b >>= 1)
+                for (int b = kCandCTA / 2; b > 0; b >>= 1)
                     if (c + b < ncand && vrow0[c + b] <= v) c += b;
                 n_slot = c;
                 n_row = v - vrow0[c];
-                n_grow = grow0[c] + n_row;
-                n_vn = vnorm16[n_grow];
+                n_vn = vnorm16[grow0[c] + n_row];
             }
         };
         locate(0);
-        int64_t grow = 0;
-        bool rv = false;
         bool ok = true;
-        for (int u = 0; u < total && ok; ++u) {
-            const int t = u / KB, kb = u - t * KB, s = u % ns;
-            if (kb == 0) {
-                Meta m;
-                m.slot = n_slot;
-                m.row_in = n_row;
-                m.vn = n_vn;
-                m.pad = 0;
-                rv = n_slot >= 0;
-                grow = n_grow;
-                meta[(t % MR) * kRowsN + p] = m;
-                mbar_arrive(&mfull[t % MR]);
-                if (t + 1 < n_tiles) locate(t + 1);
+        int u = 0;
+        for (int t = 0; t < n_tiles; ++t) {
+            Meta m;
+            m.slot = n_slot;
+            m.row_in = n_row;
+            m.vn = n_vn;
+            m.pad = 0;
+            Meta *mt = meta + (t % MR) * kRowsN;
+            mt[p] = m;
+            mbar_arrive(&mfull[t % MR]);
+            // every producer's row metadata of this tile is visible after this barrier,
+            // which all producers also leave together if one of them gave up
+            if (!named_barrier_and(4, kProd, ok)) break;
+            const __nv_bfloat16 *src[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const Meta mk = mt[pg + 16 * k];
+                src[k] = mk.slot >= 0 ? vec16 + (grow0[mk.slot] + mk.row_in) * d + pc * 8 : nullptr;
             }
-            ok = wait_or_abort(&empty[s], (uint32_t)(((u / ns) & 1) ^ 1), abort_flag, err);
-            if (ok && rv) {
-                const unsigned char *src =
-                    reinterpret_cast<const unsigned char *>(vec16 + grow * d + kb * kKB);
+            if (t + 1 < n_tiles) locate(t + 1);
+            for (int kb = 0; kb < KB; ++kb, ++u) {
+                const int s = u % ns;
+                ok = wait_or_abort(&empty[s], (uint32_t)(((u / ns) & 1) ^ 1), abort_flag, err);
+                if (!ok) break;
                 unsigned char *dst = stages + s * kStageBytes;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) cp_async16(dst + sw128_off(p, c), src + c * 16);
-            }
-            cp_async_commit();
-            if (u >= kLag) {
-                cp_async_wait<kLag>();
-                fence_proxy_async();
-                mbar_arrive(&full[(u - kLag) % ns]);
+                for (int k = 0; k < 8; ++k)
+                    if (src[k]) cp_async16(dst + sw128_off(pg + 16 * k, pc), src[k] + kb * kKB);
+                cp_async_commit();
+                if (u >= LAG) {
+                    cp_async_wait<LAG>();
+                    fence_proxy_async();
+                    mbar_arrive(&full[(u - LAG) % ns]);
+                }
             }
         }
         cp_async_wait<0>();
         fence_proxy_async();
         if (ok)
-            for (int u = total > kLag ? total - kLag : 0; u < total; ++u) mbar_arrive(&full[u % ns]);
+            for (int v = total > LAG ? total - LAG : 0; v < total; ++v) mbar_arrive(&full[v % ns]);
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
@@ -349,101 +369,116 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         for (int a = 0; a < kMaxQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
         unsigned char *dw = dist + warp * 32 * 128;
         const int r = warp * 32 + lane;
+        int fin = 0;   // candidates finished so far (the same in every epilogue thread)
         bool ok = true;
-        for (int t = 0; t < n_tiles && ok; ++t) {
+        for (int t = 0; t < n_tiles; ++t) {
+            // all four warps leave together if one of them gave up
+            if (!named_barrier_and(1, kEpi, ok)) break;
             const int buf = t & 1;
             ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
                  wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
             ok = __all_sync(0xffffffffu, ok);   // the tensor-memory load below is warp-wide
-            if (!ok) break;
-            tc_fence_after();
-            const Meta *mt = meta + (t % MR) * kRowsN;
-            const int rows_w = min(32, R - t * kRowsN - warp * 32);
-            if (rows_w <= 0) {
+            if (ok) {
+                tc_fence_after();
+                const Meta *mt = meta + (t % MR) * kRowsN;
+                const int rows_w = min(32, R - t * kRowsN - warp * 32);
+                uint32_t v[32];
+                if (rows_w > 0)
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kMaxQ), v);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
-                continue;
-            }
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kMaxQ), v);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-            // row phase: lane = row r
-            {
-                const Meta m = mt[r];
-                float best = INF;
-                int ba = 0;
+                if (rows_w > 0) {
+                    // row phase: lane = row r
+                    {
+                        const Meta m = mt[r];
+                        float best = INF;
+                        int ba = 0;
 #pragma unroll
-                for (int c4 = 0; c4 < 8; ++c4) {
-                    float x[4];
+                        for (int c4 = 0; c4 < 8; ++c4) {
+                            float x[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int a = c4 * 4 + i;
-                        // qreg is +inf past the query, which keeps those entries out
-                        const float d2 = fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
-                        x[i] = d2;
-                        if (d2 < best) {
-                            best = d2;
-                            ba = a;
+                            for (int i = 0; i < 4; ++i) {
+                                const int a = c4 * 4 + i;
+                                // qreg is +inf past the query, which keeps those entries out
+                                const float d2 =
+                                    fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
+                                x[i] = d2;
+                                if (d2 < best) {
+                                    best = d2;
+                                    ba = a;
+                                }
+                            }
+                            *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                                make_float4(x[0], x[1], x[2], x[3]);
                         }
+                        rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
                     }
-                    *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
-                        make_float4(x[0], x[1], x[2], x[3]);
-                }
-                rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
-            }
-            __syncwarp();
-            // column phase: lane = query vector a, rows of this warp in order
-            {
-                const int a = lane;
-                int cur = -1;
-                float bmin = INF;
-                int brow = 0;
-                unsigned long long kmax = 0;
-                const int coff = ((a >> 2) << 4) + (a & 3) * 4;
-                for (int j = 0; j < rows_w; ++j) {
-                    const Meta mj = mt[warp * 32 + j];
-                    if (mj.slot != cur) {
-                        if (cur >= 0) {
-                            if (a < mq) atomicMin(&cmin[cur * kMaxQ + a], dkey(bmin, (uint32_t)brow));
-                            if (a == 0) atomicMax(&ckey[cur], kmax);
+                    __syncwarp();
+                    // column phase: lane = query vector a, rows of this warp in order
+                    {
+                        const int a = lane;
+                        int cur = -1;
+                        float bmin = INF;
+                        int brow = 0;
+                        unsigned long long kmax = 0;
+                        const int coff = ((a >> 2) << 4) + (a & 3) * 4;
+                        for (int j = 0; j < rows_w; ++j) {
+                            const Meta mj = mt[warp * 32 + j];
+                            if (mj.slot != cur) {
+                                if (cur >= 0) {
+                                    const int sl = cur % kSlots;
+                                    if (a < mq) atomicMin(&cmin[sl * kMaxQ + a], dkey(bmin, (uint32_t)brow));
+                                    if (a == 0) atomicMax(&ckey[sl], kmax);
+                                }
+                                cur = mj.slot;
+                                bmin = INF;
+                                brow = 0;
+                                kmax = 0;
+                            }
+                            const float x =
+                                *reinterpret_cast<const float *>(dw + j * 128 + (coff ^ ((j & 7) << 4)));
+                            if (x < bmin) {
+                                bmin = x;
+                                brow = mj.row_in;
+                            }
+                            const unsigned long long kj = rkey[warp * 32 + j];
+                            kmax = kj > kmax ? kj : kmax;
                         }
-                        cur = mj.slot;
-                        bmin = INF;
-                        brow = 0;
-                        kmax = 0;
+                        const int sl = cur % kSlots;
+                        if (a < mq) atomicMin(&cmin[sl * kMaxQ + a], dkey(bmin, (uint32_t)brow));
+                        if (a == 0) atomicMax(&ckey[sl], kmax);
                     }
-                    const float x = *reinterpret_cast<const float *>(dw + j * 128 + (coff ^ ((j & 7) << 4)));
-                    if (x < bmin) {
-                        bmin = x;
-                        brow = mj.row_in;
+                    __syncwarp();
+                }
+            }
+            named_barrier_sync(2, kEpi);   // every atomic of this tile is done
+            // candidates whose last row lies in tiles 0..t are complete
+            const int rows_done = min(R, (t + 1) * kRowsN);
+            int fend = fin;
+            while (fend < ncand && vrow0[fend + 1] <= rows_done) ++fend;
+            if (ok) {
+                for (int c = fin + warp; c < fend; c += kEpi / 32) {
+                    const int sl = c % kSlots;
+                    const unsigned long long kc = lane < mq ? cmin[sl * kMaxQ + lane] : 0ull;
+                    const uint32_t bits = (uint32_t)(kc >> 32);
+                    const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
+                    const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
+                    const int src = __ffs(who) - 1;
+                    int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)kc, src);
+                    const unsigned long long kr = ckey[sl];
+                    if (mx < (uint32_t)(kr >> 32)) {
+                        pa = (int)(kr & 0xff);
+                        pr = (int)((kr >> 8) & 0xffffff);
                     }
-                    const unsigned long long kj = rkey[warp * 32 + j];
-                    kmax = kj > kmax ? kj : kmax;
+                    if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
+                    __syncwarp();
+                    cmin[sl * kMaxQ + lane] = ~0ull;   // the slot is free for a later candidate
+                    if (lane == 0) ckey[sl] = 0ull;
                 }
-                if (a < mq) atomicMin(&cmin[cur * kMaxQ + a], dkey(bmin, (uint32_t)brow));
-                if (a == 0) atomicMax(&ckey[cur], kmax);
             }
-            __syncwarp();
-        }
-        // every epilogue warp is done with the per-candidate slots
-        if (named_barrier_and(1, kEpi, ok)) {
-            for (int c = warp; c < ncand; c += kEpi / 32) {
-                const unsigned long long kc = lane < mq ? cmin[c * kMaxQ + lane] : 0ull;
-                const uint32_t bits = (uint32_t)(kc >> 32);
-                const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-                const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
-                const int src = __ffs(who) - 1;
-                int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)kc, src);
-                const unsigned long long kr = ckey[c];
-                if (mx < (uint32_t)(kr >> 32)) {
-                    pa = (int)(kr & 0xff);
-                    pr = (int)((kr >> 8) & 0xffffff);
-                }
-                if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
-            }
+            fin = fend;
+            named_barrier_sync(3, kEpi);   // cleared slots are visible to the next tile
         }
     }
 
@@ -542,12 +577,12 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
     const int ns = pick_stages(d);
     if (ns == 0) return cudaErrorInvalidValue;
     const Layout Lo = make_layout(d, ns);
-    cudaError_t e = cudaFuncSetAttribute(k_refine_mma,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
-    if (e != cudaSuccess) return e;
     const int gx = (C + kCandCTA - 1) / kCandCTA;
-    k_refine_mma<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off,
-                                                            d, ns, cand, thr, C, pair, err);
+    auto kern = lag_for(ns) == 5 ? k_refine_mma<5> : k_refine_mma<4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,
+                                                    cand, thr, C, pair, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, set_off, cand, thr, pair,

@@ -253,6 +253,8 @@ def test_longest_codes(bv, orc, m):
     (3000, 8, 32, 384, 8, 32, 1000, 13),   # the large workload's shapes, 8 CTAs per query
     (300, 1, 3, 64, 1, 5, 300, 14),        # one 64-dim block, tiny sets, C > |F1|
     (500, 20, 140, 192, 2, 32, 150, 15),   # sets longer than one 128-row tile
+    (3000, 1, 1, 64, 1, 3, 1500, 21),      # one-row sets: 128 candidates finish per tile
+    (400, 2, 6, 1024, 2, 8, 300, 22),      # d = 1024: the shallowest stage ring
 ])
 def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
