@@ -205,6 +205,11 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
             }
         }
         cp_async_wait<0>();
+        if (p == 0 && !ok) {
+            // after giving up, let the query-block copies already issued land before the CTA exits
+            for (int v = u > kNS ? u - kNS : 0; v < u; ++v)
+                mbar_wait_bounded(&full[v % kNS], (uint32_t)((v / kNS) & 1), kWaitNs / 10);
+        }
     } else if (warp == 12) {
         // ---- MMA issue: one thread ------------------------------------------------
         if (lane == 0) {
