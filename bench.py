@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "query sets/s at recall@10≥0.95 (1M sets); fast vs plain form, same GB300"
 UNIT = "query sets/s"
-LAUNCHES_PER_BATCH = 10   # encode, prep, scan, hist, thresh, count, offsets, write, refine, topk
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 POPC_PER_CLK_PER_SM = 16   # 32-bit population count throughput per SM per clock
@@ -266,41 +265,53 @@ def traffic_per_unit(kernel):
 def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=False):
     """Roofline of the dominant kernel (scan or refine) of the timed region.
 
-    Each kernel has an ALU roof and an HBM roof; the one with the longer time at
-    peak binds.  scan: 32-bit popcounts = (query, gated set) pairs x m/32 at
-    152 SMs x 16/clk x 2070 MHz; bytes = sketch matrix once + A gate-plane words
-    per (query, 32 sets) + the h scores written.  refine: FLOPs = 2 x (query
-    vector, candidate vector) pairs x d at 152 x 128 FP32 lanes x 2 x 2070 MHz;
-    bytes = candidate rows x d x 4."""
+    Each kernel has a compute roof and an HBM roof; the one with the longer time
+    at peak binds.  Times are the kernel's own CUDA-event stage (the gate words
+    and the FP8 query operand are a stage of their own, so is the re-score).
+
+    k_scan_mma (tensor cores, FP8): FLOPs = 2 x query sets x N x m (every pair,
+    the algorithmic GEMM) against the FP8 peak (measured sustained BF16 x 2, the
+    nominal FP8/BF16 ratio); bytes = sketch matrix once + gate words read + h
+    written.  k_scan (CUDA cores): 32-bit popcounts = gated pairs x m/32 at
+    152 SMs x 16/clk x 2070 MHz.  k_refine_mma: bytes = candidate rows x d x 2
+    (BF16 gather); tensor FLOPs = 2 x (query vector, candidate vector) pairs x d
+    against sustained BF16.  k_refine_tma / k_refine: the same pairs on FP32
+    lanes (152 x 128 x 2 x 2070 MHz), bytes = rows x d x 4."""
     hbm, hbm_basis = measured_peaks()
     per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
     clock = SM_MAX_MHZ * 1e6
-    # the refine kernel the library runs for this workload
-    if fast and c["d"] % 64 == 0 and c["q_hi"] <= 32:
-        refine_name, vbytes = "k_refine_mma", 2
-    else:
-        refine_name = "k_refine_tma" if c["d"] % 4 == 0 and c["q_hi"] <= 64 else "k_refine"
-        vbytes = 4
     try:
         mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        bf16_peak, bf16_basis = float(mp["bf16_tflops_sustained"]) * 1e12, "of measured (sustained bf16)"
+        bf16_peak, bf16_basis = float(mp["bf16_tflops_sustained"]) * 1e12, "of measured"
     except Exception:
-        bf16_peak, bf16_basis = 1.7e15, "of fallback (sustained bf16)"
-    if refine_name == "k_refine_mma":
-        refine_alu = (2.0 * pair_elems * c["d"], bf16_peak, "TFLOP/s", bf16_basis, "tensor")
+        bf16_peak, bf16_basis = 1.7e15, "of fallback"
+    nw = (c["n_sets"] + 31) // 32
+    scan_bytes = c["n_sets"] * c["m"] / 8 + nq * nw * 4 + nq * c["n_sets"] * 2
+    tensor_scan = True          # the library default (BVSS_SEARCH_POPC_SCAN off)
+    if tensor_scan:
+        scan = dict(name="k_scan_mma", t=per["scan"],
+                    alu=(2.0 * nq * c["n_sets"] * c["m"], 2 * bf16_peak, "TFLOP/s",
+                         bf16_basis + " sustained bf16 x 2 (FP8 nominal ratio)", "tensor"),
+                    hbm_bytes=scan_bytes, units=None)
     else:
-        refine_alu = (2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock,
-                      "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)", "alu")
-    kern = {
-        "scan": dict(
-            name="k_scan", t=per["scan"],
-            alu=(gated_pairs * (c["m"] // 32), SM_COUNT * POPC_PER_CLK_PER_SM * clock, "Tpopc/s",
-                 "152 SMs x 16 popc/clk x 2070 MHz (nominal, measured 15.1)", "alu"),
-            hbm_bytes=c["n_sets"] * c["m"] / 8 + nq * c["A"] * c["n_sets"] / 8
-            + nq * c["n_sets"] * 2, units=None),
-        "refine": dict(name=refine_name, t=per["refine"], alu=refine_alu,
-                       hbm_bytes=cand_rows * c["d"] * float(vbytes), units=cand_rows),
-    }
+        scan = dict(name="k_scan", t=per["scan"],
+                    alu=(gated_pairs * (c["m"] // 32), SM_COUNT * POPC_PER_CLK_PER_SM * clock,
+                         "Tpopc/s", "152 SMs x 16 popc/clk x 2070 MHz (nominal, measured 15.1)",
+                         "alu"),
+                    hbm_bytes=scan_bytes, units=None)
+    if fast and c["d"] % 64 == 0 and c["q_hi"] <= 32:
+        refine = dict(name="k_refine_mma", t=per["refine"],
+                      alu=(2.0 * pair_elems * c["d"], bf16_peak, "TFLOP/s",
+                           bf16_basis + " sustained bf16", "tensor"),
+                      hbm_bytes=cand_rows * c["d"] * 2.0, units=cand_rows)
+    else:
+        refine = dict(name="k_refine_tma" if c["d"] % 4 == 0 and c["q_hi"] <= 64 else "k_refine",
+                      t=per["refine"],
+                      alu=(2.0 * pair_elems * c["d"], SM_COUNT * FP32_LANES_PER_SM * 2 * clock,
+                           "TFLOP/s", "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal FMA)",
+                           "alu"),
+                      hbm_bytes=cand_rows * c["d"] * 4.0, units=cand_rows)
+    kern = {"scan": scan, "refine": refine}
     dom = max(kern, key=lambda k: kern[k]["t"])
     k = kern[dom]
     t = k["t"] / 1e3
@@ -312,13 +323,15 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=F
         ach = k["hbm_bytes"] / t / 1e9
         return {"kernel": k["name"], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": traffic, "algorithmic_bytes": k["hbm_bytes"],
+                "launch_ms": k["t"],
                 "peak_basis": hbm_basis + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_basis ==
                 "of measured" else hbm_basis,
-                "alu_roof": {"achieved": ops / t / 1e12, "peak": peak_ops / 1e12, "unit": unit}}
+                "compute_roof": {"achieved": ops / t / 1e12, "peak": peak_ops / 1e12, "unit": unit,
+                                 "basis": basis}}
     ach = ops / t / 1e12
     return {"kernel": k["name"], "bound": alu_bound, "achieved": ach, "peak": peak_ops / 1e12,
             "unit": unit, "frac": ach / (peak_ops / 1e12), "traffic": traffic,
-            "peak_basis": basis, "algorithmic_bytes": k["hbm_bytes"],
+            "peak_basis": basis, "algorithmic_bytes": k["hbm_bytes"], "launch_ms": k["t"],
             "hbm_roof": {"achieved": k["hbm_bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s"}}
 
 
@@ -462,17 +475,17 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         clk = clocks.stop() if clocks else None
         t_ms = e0.elapsed_time(e1) / args.steps
-        st_ms, nb = bvss.bvss_profile_read(ix, reset=True)
+        st_ms, nb, nl = bvss.bvss_profile_read(ix, reset=True)
         bvss.bvss_profile_enable(ix, False)
         bvss.bvss_sync(ix, stream)
         if world > 1:
             t = torch.tensor([t_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             t_ms = float(t.item())
-        return t_ms, st_ms, nb, clk
+        return t_ms, st_ms, nb, nl, clk
 
-    ms_plain, stage_plain, _, _ = timed(kw, False)
-    ms, stage_ms, nbatch, clk = timed(kw_fast, True)
+    ms_plain, stage_plain, _, _, _ = timed(kw, False)
+    ms, stage_ms, nbatch, launches, clk = timed(kw_fast, True)
     value = world * nq / (ms / 1e3)
 
     # end to end through the same API: pinned host query vectors in, host results out
@@ -534,7 +547,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": LAUNCHES_PER_BATCH * nbatch,
+        "gpu_launches": launches,
         "clocks": clk,
         "build_s": build_s,
         "work": {"gated_pairs_per_step": gated_pairs, "candidates_per_step": sum_cand,

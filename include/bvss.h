@@ -204,20 +204,26 @@ int bvss_selftest_wait_timeout(int64_t limit_ns);
 
 /* Stages of bvss_query timed by the profiler (CUDA events on the query
  * stream, recorded between the kernels of every batch). */
-#define BVSS_STAGE_ENCODE 0   /* FlyHash of the query vectors + C_Q, S_Q, P */
-#define BVSS_STAGE_SCAN 1     /* first-layer gate + sketch Hamming over all sets */
-#define BVSS_STAGE_SELECT 2   /* the C smallest (Hamming, id) */
-#define BVSS_STAGE_REFINE 3   /* exact Hausdorff of the candidates */
-#define BVSS_STAGE_TOPK 4     /* k smallest (distance, id) and result copies */
-#define BVSS_N_STAGES 5
+#define BVSS_STAGE_ENCODE 0   /* FlyHash of the query vectors + C_Q, S_Q, P (Alg. 6 lines 1-4) */
+#define BVSS_STAGE_GATE 1     /* layer-1 words per 32 sets (lines 5-9), plus the FP8 query
+                                 sketches of the tensor-core scan */
+#define BVSS_STAGE_SCAN 2     /* sketch Hamming over all sets (line 12) */
+#define BVSS_STAGE_SELECT 3   /* the C smallest (Hamming, id) (lines 10-18) */
+#define BVSS_STAGE_REFINE 4   /* Hausdorff of the candidates (lines 19-22) */
+#define BVSS_STAGE_RESCORE 5  /* FP32 distance of each candidate's critical pair
+                                 (BVSS_SEARCH_FAST only; 0 otherwise) */
+#define BVSS_STAGE_TOPK 6     /* k smallest (distance, id) and result copies (line 23) */
+#define BVSS_N_STAGES 7
 
 /* Turn per-stage timing of later bvss_query calls on (on != 0) or off. */
 int bvss_profile_enable(bvss_index *ix, int on);
 
-/* Sum of the stage times (ms, host array of BVSS_N_STAGES) and the number of
- * timed query batches since the last reset.  Waits for the recorded events;
- * reset != 0 clears the sums afterwards. */
-int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int reset);
+/* Sum of the stage times (ms, host array of BVSS_N_STAGES), the number of timed
+ * query batches and the number of kernels those batches launched, since the
+ * last reset.  Waits for the recorded events; reset != 0 clears the sums
+ * afterwards.  n_batches and n_launches may be NULL. */
+int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int64_t *n_launches,
+                      int reset);
 
 /*
  * bvss_select_noalloc -- the candidate select of bvss_query (the min(C, |F1|)

@@ -63,7 +63,8 @@ SYMBOLS = {
     "bvss_get_counts": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "bvss_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bvss_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
-                                         ctypes.POINTER(_c_i64), ctypes.c_int]),
+                                         ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64),
+                                         ctypes.c_int]),
     "bvss_select_noalloc": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i32, _c_i32, _c_i32, _vp,
                                            _vp, _vp]),
     "bvss_sync": (ctypes.c_int, [_vp, _vp]),
@@ -303,7 +304,7 @@ def bvss_selftest_wait_timeout(limit_ns: int = 10_000_000) -> int:
     return load().bvss_selftest_wait_timeout(limit_ns)
 
 
-STAGES = ("encode", "scan", "select", "refine", "topk")
+STAGES = ("encode", "gate", "scan", "select", "refine", "rescore", "topk")
 
 
 def bvss_profile_enable(ix: Index, on: bool = True):
@@ -311,11 +312,12 @@ def bvss_profile_enable(ix: Index, on: bool = True):
 
 
 def bvss_profile_read(ix: Index, reset: bool = True):
-    """({stage: summed ms}, number of timed batches) since the last reset."""
+    """({stage: summed ms}, timed batches, kernels they launched) since the last reset."""
     ms = (ctypes.c_double * len(STAGES))()
-    nb = _c_i64()
-    _check(load().bvss_profile_read(ix.handle, ms, ctypes.byref(nb), 1 if reset else 0))
-    return dict(zip(STAGES, list(ms))), nb.value
+    nb, nl = _c_i64(), _c_i64()
+    _check(load().bvss_profile_read(ix.handle, ms, ctypes.byref(nb), ctypes.byref(nl),
+                                    1 if reset else 0))
+    return dict(zip(STAGES, list(ms))), nb.value, nl.value
 
 
 def bvss_free(ix: Index):

@@ -357,35 +357,61 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
         BVSS_CU(launch_query_prep(w.qpos, w.qoff, nb, m, L, A, w.sq, w.plist,
                                   tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
-        // lines 5-12
-        BVSS_CU(launch_scan(ix->sketch, ix->spop, ix->n_sets, W, plane, ix->NW, gate_mode, w.sq,
-                            w.plist, A, nb, w.gate, tensor_scan, w.q8, w.qpop, w.h, hs, ix->err,
-                            st));
+        int64_t launches = 2;
+        // lines 5-9: layer-1 words per 32 sets (and the FP8 query operand)
+        if (gate_mode == 1) {
+            BVSS_CU(launch_gate(plane, ix->NW, w.plist, A, nb, w.gate, st));
+            ++launches;
+        }
+        if (tensor_scan) {
+            BVSS_CU(launch_expand_q(w.sq, nb, W, w.q8, w.qpop, st));
+            ++launches;
+        }
         if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
+        // line 12
+        if (tensor_scan)
+            BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
+                                    w.q8, w.qpop, nb, w.h, hs, ix->err, st));
+        else
+            BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, w.gate, ix->NW, gate_mode, w.sq, nb, w.h,
+                                hs, st));
+        ++launches;
+        if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
         // lines 10-18
         BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
-        if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
+        launches += kSelectKernels;
+        if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
         // lines 19-23
-        if (fast && refine_mma_supported(d, max_mq))
-            BVSS_CU(launch_refine_mma(qv, w.qoff, nb, ix->vec, ix->vec16, ix->vnorm16, ix->set_off,
-                                      d, w.cand, w.thr, C, w.pair, w.cand_dist, ix->err, st));
+        const bool mma = fast && refine_mma_supported(d, max_mq);
+        if (mma)
+            BVSS_CU(launch_refine_mma(qv, w.qoff, nb, ix->vec16, ix->vnorm16, ix->set_off, d, w.cand,
+                                      w.thr, C, w.pair, ix->err, st));
         else if (refine_tma_supported(d, max_mq))
             BVSS_CU(launch_refine_tma(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off,
                                       d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
         else
             BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, st));
-        if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
+        ++launches;
+        if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
+        if (mma) {
+            BVSS_CU(launch_rescore(qv, w.qoff, nb, ix->vec, ix->set_off, d, w.cand, w.thr, C, w.pair,
+                                   w.cand_dist, st));
+            ++launches;
+        }
+        if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
         int64_t *ids = ids_dev ? out_ids + b0 * k : w.out_ids;
         float *dist = dist_dev ? out_dist + b0 * k : w.out_dist;
         BVSS_CU(launch_topk(w.cand, w.cand_dist, w.thr, nb, C, k, ids, dist, st));
+        ++launches;
+        if (ev) ix->prof_launches += launches;
         if (!ids_dev)
             BVSS_CU(cudaMemcpyAsync(out_ids + b0 * k, ids, sizeof(int64_t) * (size_t)nb * k,
                                     cudaMemcpyDeviceToHost, st));
         if (!dist_dev)
             BVSS_CU(cudaMemcpyAsync(out_dist + b0 * k, dist, sizeof(float) * (size_t)nb * k,
                                     cudaMemcpyDeviceToHost, st));
-        if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
+        if (ev) BVSS_CU(cudaEventRecord(ev[7], st));
         if (tr) {
             const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
             if (tr->qpos)
@@ -615,7 +641,8 @@ int bvss_profile_enable(bvss_index *ix, int on) {
     return BVSS_OK;
 }
 
-int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int reset) {
+int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int64_t *n_launches,
+                      int reset) {
     if (!ix) return fail(BVSS_EINVAL, "index is NULL");
     for (int64_t b = 0; b + kProfEvents <= ix->prof_used; b += kProfEvents) {
         BVSS_CU(cudaEventSynchronize(ix->prof_ev[b + kProfEvents - 1]));
@@ -630,9 +657,11 @@ int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int 
     if (stage_ms)
         for (int sidx = 0; sidx < BVSS_N_STAGES; ++sidx) stage_ms[sidx] = ix->prof_ms[sidx];
     if (n_batches) *n_batches = ix->prof_batches;
+    if (n_launches) *n_launches = ix->prof_launches;
     if (reset) {
         for (int sidx = 0; sidx < BVSS_N_STAGES; ++sidx) ix->prof_ms[sidx] = 0.0;
         ix->prof_batches = 0;
+        ix->prof_launches = 0;
     }
     return BVSS_OK;
 }

@@ -82,6 +82,7 @@ struct bvss_index {
     int64_t prof_cap = 0, prof_used = 0;
     double prof_ms[BVSS_N_STAGES] = {};
     int64_t prof_batches = 0;
+    int64_t prof_launches = 0;     // kernels launched by the profiled batches
 };
 
 namespace bvss {
@@ -113,28 +114,32 @@ cudaError_t launch_gather_counts(const uint8_t *count, int m, int64_t n_sets,
                                  cudaStream_t st);
 
 // ---- scan.cu ----------------------------------------------------------------
-// Alg. 6 lines 5-12: h[q][i] = popc(S_Q ^ S_i) for sets passing the gate.
-// gate_mode: 0 = every set passes (M = 0), 1 = gate planes, 2 = no set passes.
-// h rows have stride hs (a multiple of 64 elements).  gate: n_q x NW words of
-// scratch for the per-tile layer-1 masks (gate_mode 1 only).  tensor: score on
-// the tensor cores (scan_mma.cu; needs spop, q8 of scan_mma_q8_bytes(n_q, m)
-// bytes and qpop of n_q rounded up to 256 ints), else with CUDA-core popcounts.
-cudaError_t launch_scan(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
-                        const uint32_t *plane, int64_t NW, int gate_mode, const uint32_t *sq,
-                        const uint16_t *plist, int A, int n_q, uint32_t *gate, bool tensor,
-                        uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs, int *err,
-                        cudaStream_t st);
+// Alg. 6 lines 5-9: gate[q][t] = OR over the A positions of plane word t, i.e.
+// the first-layer mask of sets 32t .. 32t + 31 (n_q x NW words).
+cudaError_t launch_gate(const uint32_t *plane, int64_t NW, const uint16_t *plist, int A, int n_q,
+                        uint32_t *gate, cudaStream_t st);
+// Alg. 6 line 12 with CUDA-core popcounts: h[q][i] = popc(S_Q ^ S_i) for sets
+// passing the gate.  gate_mode: 0 = every set passes (M = 0), 1 = gate words,
+// 2 = no set passes.  h rows have stride hs (a multiple of 64 elements).
+cudaError_t launch_scan(const uint32_t *sketch, int64_t n_sets, int W, const uint32_t *gate,
+                        int64_t NW, int gate_mode, const uint32_t *sq, int n_q, uint16_t *h,
+                        int64_t hs, cudaStream_t st);
 
-// ---- scan_mma.cu ------------------------------------------------------------
+// ---- scan_mma.cu: the same h on the tensor cores ----------------------------
 size_t scan_mma_q8_bytes(int64_t n_q, int m);
 cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int32_t *spop,
                               cudaStream_t st);
+// query sketches -> FP8 MMA operand (q8 of scan_mma_q8_bytes(n_q, m) bytes) and
+// |S_Q| (qpop, n_q rounded up to 256 ints)
+cudaError_t launch_expand_q(const uint32_t *sq, int n_q, int W, uint8_t *q8, int32_t *qpop,
+                            cudaStream_t st);
 cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
-                            const uint32_t *gate, int64_t NW, int gate_mode, const uint32_t *sq,
-                            int n_q, uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs,
-                            int *err, cudaStream_t st);
+                            const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
+                            const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
+                            cudaStream_t st);
 
-// ---- select.cu --------------------------------------------------------------
+// ---- select.cu
+constexpr int kSelectKernels = 5;   // kernels launch_select runs --------------------------------------------------------------
 // Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.
 cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, int n_q,
                           int C, uint32_t *hist, int32_t *thr, int32_t *chunk,
@@ -157,11 +162,15 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
 bool refine_mma_supported(int d, int max_mq);
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st);
+// records each candidate's critical (query vector, row) pair; launch_rescore then
+// writes its FP32 distance as the candidate's distance
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
-                              const float *vec, const __nv_bfloat16 *vec16,
-                              const float *vnorm16, const int64_t *set_off, int d,
-                              const int32_t *cand, const int32_t *thr, int C, int2 *pair,
-                              float *cand_dist, int *err, cudaStream_t st);
+                              const __nv_bfloat16 *vec16, const float *vnorm16,
+                              const int64_t *set_off, int d, const int32_t *cand,
+                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st);
+cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
+                           const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
+                           int C, const int2 *pair, float *cand_dist, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf

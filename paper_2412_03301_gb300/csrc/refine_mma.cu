@@ -569,10 +569,9 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
 }
 
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
-                              const float *vec, const __nv_bfloat16 *vec16,
-                              const float *vnorm16, const int64_t *set_off, int d,
-                              const int32_t *cand, const int32_t *thr, int C, int2 *pair,
-                              float *cand_dist, int *err, cudaStream_t st) {
+                              const __nv_bfloat16 *vec16, const float *vnorm16,
+                              const int64_t *set_off, int d, const int32_t *cand,
+                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
     const int ns = pick_stages(d);
     if (ns == 0) return cudaErrorInvalidValue;
@@ -583,8 +582,13 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,
                                                     cand, thr, C, pair, err);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
+                           const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
+                           int C, const int2 *pair, float *cand_dist, cudaStream_t st) {
+    if (n_q <= 0) return cudaSuccess;
     k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, set_off, cand, thr, pair,
                                                        C, d, cand_dist);
     return cudaGetLastError();

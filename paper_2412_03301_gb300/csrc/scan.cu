@@ -142,23 +142,20 @@ cudaError_t launch_scan_t(const uint32_t *sketch, int64_t n_sets, int W, const u
 
 }  // namespace
 
-cudaError_t launch_scan(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
-                        const uint32_t *plane, int64_t NW, int gate_mode, const uint32_t *sq,
-                        const uint16_t *plist, int A, int n_q, uint32_t *gate, bool tensor,
-                        uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs, int *err,
-                        cudaStream_t st) {
+cudaError_t launch_gate(const uint32_t *plane, int64_t NW, const uint16_t *plist, int A, int n_q,
+                        uint32_t *gate, cudaStream_t st) {
+    if (n_q <= 0 || NW <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)n_q * NW;
+    int64_t g = (total + 255) / 256;
+    if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
+    k_gate<<<(unsigned)g, 256, 0, st>>>(plane, NW, plist, A, n_q, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t *sketch, int64_t n_sets, int W, const uint32_t *gate,
+                        int64_t NW, int gate_mode, const uint32_t *sq, int n_q, uint16_t *h,
+                        int64_t hs, cudaStream_t st) {
     if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
-    if (gate_mode == 1) {
-        const int64_t total = (int64_t)n_q * NW;
-        int64_t g = (total + 255) / 256;
-        if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
-        k_gate<<<(unsigned)g, 256, 0, st>>>(plane, NW, plist, A, n_q, gate);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (tensor)
-        return launch_scan_mma(sketch, spop, n_sets, W, gate, NW, gate_mode, sq, n_q, q8, qpop, h,
-                               hs, err, st);
     const int G = W / 4;
     const int CH = (G + 31) / 32;
     const bool full = G == 32 * CH;

@@ -368,21 +368,23 @@ cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_expand_q(const uint32_t *sq, int n_q, int W, uint8_t *q8, int32_t *qpop,
+                            cudaStream_t st) {
+    if (n_q <= 0) return cudaSuccess;
+    const int QP = (n_q + 2 * kQM - 1) / (2 * kQM);
+    const int64_t total = (int64_t)QP * 2 * kQM * (W / 4);
+    int64_t g = (total + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_expand_q<<<(unsigned)g, 256, 0, st>>>(sq, n_q, W, QP, q8, qpop);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
-                            const uint32_t *gate, int64_t NW, int gate_mode, const uint32_t *sq,
-                            int n_q, uint8_t *q8, int32_t *qpop, uint16_t *h, int64_t hs,
-                            int *err, cudaStream_t st) {
+                            const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
+                            const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
+                            cudaStream_t st) {
     if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
     const int QP = (n_q + 2 * kQM - 1) / (2 * kQM);
-    const int KB = W / 4;
-    {
-        const int64_t total = (int64_t)QP * 2 * kQM * KB;
-        int64_t g = (total + 255) / 256;
-        if (g > 4096) g = 4096;
-        k_expand_q<<<(unsigned)g, 256, 0, st>>>(sq, n_q, W, QP, q8, qpop);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     cudaError_t e = cudaFuncSetAttribute(k_scan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
     if (e != cudaSuccess) return e;

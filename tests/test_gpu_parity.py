@@ -145,6 +145,23 @@ def test_scan_forms_agree(bv, orc, n_sets, nq, m, L, A, M):
         assert np.array_equal(ha[q].astype(np.int64), want.astype(np.int64)), q
 
 
+def test_profile_stages_and_launch_count(bv, small):
+    """The profiler sees every stage and counts the kernels each form launches:
+    encode, prep, gate, [FP8 query operand], scan, 5 select kernels, refine,
+    [re-score], top-k."""
+    w = small.w
+    qv = small.qv_cuda
+    for popc, want in ((False, 12), (True, 11)):
+        bv.bvss_profile_enable(small.ix, True)
+        bv.bvss_profile_read(small.ix, reset=True)
+        bv.bvss_query(small.ix, qv, w["q_offsets"], k=10, C=200, A=3, M=1, popc_scan=popc)
+        ms, nb, nl = bv.bvss_profile_read(small.ix, reset=True)
+        bv.bvss_profile_enable(small.ix, False)
+        assert nb == 1 and nl == want
+        assert set(ms) == set(bv.STAGES) and ms["scan"] > 0 and ms["refine"] > 0
+        assert ms["rescore"] == pytest.approx(0.0, abs=0.05)
+
+
 def test_query_results_without_trace_match(bv, small):
     s = datagen.SMALL
     w = small.w
