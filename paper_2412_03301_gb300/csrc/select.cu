@@ -32,6 +32,7 @@ k_hist(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs, int m,
     for (int b = threadIdx.x; b <= m; b += kSelThreads) sh[b] = 0;
     __syncthreads();
     const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+#pragma unroll 4
     for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
         const uint4 v = row4[i8];
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -99,6 +100,7 @@ k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
     int lt = 0, eq = 0;
     if (H >= 0) {
         const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+#pragma unroll 4
         for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
             const uint4 v = row4[i8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -150,61 +152,111 @@ k_offsets(const int32_t *__restrict__ thr, int n_chunks, int32_t *__restrict__ c
     }
 }
 
+// inclusive prefix sum over the warp
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Stable compaction of one chunk: warp w owns sets [c0 + w S, c0 + (w + 1) S),
+// S = kSelChunk / 8.  Pass 1 counts each warp's h < H* and h == H*; a prefix
+// over the 8 warps gives each warp its first output slot and the id-order rank
+// of its first tie; pass 2 re-reads the warp's range (from L1/L2) 256 sets at a
+// time, with warp-shuffle scans only where the warp's ballot shows a candidate.
 __global__ void __launch_bounds__(kSelThreads)
 k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
         const int32_t *__restrict__ thr, const int32_t *__restrict__ chunk, int C,
         int32_t *__restrict__ cand) {
-    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    constexpr int kWarps = kSelThreads / 32;
+    constexpr int kSpan = kSelChunk / kWarps;       // sets per warp
+    __shared__ int w_lt[kWarps], w_eq[kWarps], w_rank[kWarps], w_pos[kWarps];
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
     const int H = thr[q * 4];
     if (H < 0) return;   // uniform over the CTA
     const int take = thr[q * 4 + 2];
     const int32_t *o = chunk + ((int64_t)q * n_chunks + blockIdx.x) * 4;
-    const int eqb = o[2];
-    const int off = o[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
-    const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    const int64_t w0 = c0 + (int64_t)warp * kSpan;
+    const int64_t chunk_end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    const int64_t w1 = w0 + kSpan < chunk_end ? w0 + kSpan : chunk_end;
     const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
-    int32_t *out = cand + (int64_t)q * C;
-    int run_eq = 0, run_sel = 0;
-    for (int64_t r0 = c0; r0 < end; r0 += kSelThreads * 8) {
-        const int64_t i0 = r0 + threadIdx.x * 8;
-        int val[8];
-        if (i0 < end) {
+    auto load8 = [&](int64_t i0, int (&val)[8]) {
+        if (i0 < w1) {
             const uint4 v = row4[i0 / 8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                val[e] = i0 + e < end ? (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu) : 0xFFFF;
+                val[e] = i0 + e < w1 ? (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu) : 0xFFFF;
         } else {
 #pragma unroll
             for (int e = 0; e < 8; ++e) val[e] = 0xFFFF;
         }
+    };
+    // pass 1: this warp's counts
+    int lt = 0, eq = 0;
+#pragma unroll 4
+    for (int64_t i0 = w0 + lane * 8; i0 < w1; i0 += 256) {
+        int val[8];
+        load8(i0, val);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            lt += val[e] < H;
+            eq += val[e] == H;
+        }
+    }
+    lt = __reduce_add_sync(0xffffffffu, (uint32_t)lt);
+    eq = __reduce_add_sync(0xffffffffu, (uint32_t)eq);
+    if (lane == 0) {
+        w_lt[warp] = lt;
+        w_eq[warp] = eq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int rank = o[2], pos = o[3];
+        for (int w = 0; w < kWarps; ++w) {
+            w_rank[w] = rank;
+            w_pos[w] = pos;
+            pos += w_lt[w] + max(0, min(take - rank, w_eq[w]));
+            rank += w_eq[w];
+        }
+    }
+    __syncthreads();
+    int rank = w_rank[warp], pos = w_pos[warp];
+    int32_t *out = cand + (int64_t)q * C;
+    // pass 2: write this warp's candidates in id order
+    for (int64_t i0 = w0 + lane * 8; i0 - lane * 8 < w1; i0 += 256) {
+        int val[8];
+        load8(i0, val);
         int n_lt = 0, n_eq = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             n_lt += val[e] < H;
             n_eq += val[e] == H;
         }
-        int te;
-        const int ex_eq = block_excl_scan<kSelThreads>(n_eq, scan_sh, &te);
-        int rank = eqb + run_eq + ex_eq;   // id-order rank of my first tie
-        const int n_sel = n_lt + max(0, min(take - rank, n_eq));
-        int ts;
-        const int ex_sel = block_excl_scan<kSelThreads>(n_sel, scan_sh, &ts);
-        int pos = off + run_sel + ex_sel;
+        if (!__any_sync(0xffffffffu, (n_lt | n_eq) != 0)) continue;
+        const int inc_eq = warp_incl_scan(n_eq);
+        int r = rank + inc_eq - n_eq;   // id-order rank of my first tie
+        const int n_sel = n_lt + max(0, min(take - r, n_eq));
+        const int inc_sel = warp_incl_scan(n_sel);
+        int p = pos + inc_sel - n_sel;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            bool s = val[e] < H;
+            bool sel = val[e] < H;
             if (val[e] == H) {
-                s = rank < take;
-                ++rank;
+                sel = r < take;
+                ++r;
             }
-            if (s && pos < C) out[pos++] = (int32_t)(i0 + e);
+            if (sel && p < C) out[p++] = (int32_t)(i0 + e);
         }
-        run_eq += te;
-        run_sel += ts;
+        rank += __shfl_sync(0xffffffffu, inc_eq, 31);
+        pos += __shfl_sync(0xffffffffu, inc_sel, 31);
     }
 }
 
