@@ -18,22 +18,22 @@
 //   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
 //              one of two TMEM accumulators;
-//   warps 0-3  epilogue; warp w owns rows 32w..32w+31 of every tile.  Row
-//              phase (lane = row): squared distances |q|^2 + |v|^2 - 2 q.v to
-//              all query vectors from one tensor-memory load, their minimum
-//              (with its arg-min), and the distances written to a swizzled
-//              shared-memory block.  Column phase (lane = query vector): walk
-//              the 32 rows in order, keeping per candidate the minimum over its
-//              rows and the maximum of the rows' minima, merged into
-//              per-candidate slots with shared-memory atomics (a candidate's
-//              rows may span warps and tiles).
-// After each tile, every candidate whose last row has been seen is finished:
-// its Hausdorff value (Def. 4) is the larger of max over query vectors of the
-// slot minima and the slot maximum, the pair attaining it is recorded and the
-// slot is cleared.  Slots form a ring of 160 (candidates open at one time have
-// rows in one tile, so at most 128 of them), and k_rescore computes each pair's distance
-// directly in FP32 from the original vectors (one warp per candidate) and writes
-// the square root as the candidate's distance.
+//   warps 0-3  epilogue.  Row phase (lane = row 32w + lane): squared
+//              distances |q|^2 + |v|^2 - 2 q.v to all query vectors from one
+//              tensor-memory load, their minimum with its arg-min (the row's
+//              key), the distances written to a swizzled shared-memory block.
+//              After a barrier over the four warps, column phase (lane = query
+//              vector): warp w walks, whole, the candidates whose first row in
+//              the tile lies in rows 32w..32w+31, keeping per query vector the
+//              minimum over the candidate's rows (with the row) and the maximum
+//              of the rows' keys; when a candidate ends, the larger of the two
+//              directed values (Def. 4) gives the pair that attains its
+//              Hausdorff value, which is recorded.  The one candidate that runs
+//              past the end of a tile carries its state in shared memory to the
+//              next tile (double-buffered), so no atomics are needed.
+// k_rescore then computes each pair's distance directly in FP32 from the
+// original vectors (one warp per candidate) and writes the square root as the
+// candidate's distance.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include <cuda_bf16.h>
@@ -49,7 +49,6 @@ constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
 constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
 constexpr int kMaxNS = 8;            // stages in the ring, at most
 constexpr int kCandCTA = 512;        // candidates per CTA
-constexpr int kSlots = 160;          // per-candidate accumulator ring
 constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
 constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
 constexpr int kProd = 128;
@@ -69,7 +68,7 @@ struct Meta {
 };
 
 struct Layout {
-    int q, stages, meta, dist, cmin, ckey, rkey, bars, grow0, vrow0, qn, misc, total;
+    int q, stages, meta, dist, rkey, carry, bars, grow0, vrow0, qn, misc, total;
 };
 
 // Tiles of row metadata the ring must hold: producers run at most ns stages
@@ -85,9 +84,8 @@ __host__ __device__ inline Layout make_layout(int d, int ns) {
     L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
     L.dist = o;    o += kRowsN * 128;              // row-phase distances, 32 per row
-    L.cmin = o;    o += kSlots * kMaxQ * 8;        // per (open candidate, query vector) minimum
-    L.ckey = o;    o += kSlots * 8;                // per open candidate maximum of row minima
-    L.rkey = o;    o += kRowsN * 8;                // per row minimum, this tile
+    L.rkey = o;    o += kRowsN * 8;                // per row minimum (the row's key), this tile
+    L.carry = o;   o += 2 * (kMaxQ + 1) * 8;       // state of a candidate continuing into the next tile
     L.bars = o;    o += (2 * kMaxNS + 4 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
@@ -152,8 +150,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     unsigned char *stages = smem + Lo.stages;
     Meta *meta = reinterpret_cast<Meta *>(smem + Lo.meta);
     unsigned char *dist = smem + Lo.dist;
-    unsigned long long *cmin = reinterpret_cast<unsigned long long *>(smem + Lo.cmin);
-    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem + Lo.ckey);
+    unsigned long long *carry = reinterpret_cast<unsigned long long *>(smem + Lo.carry);
     unsigned long long *rkey = reinterpret_cast<unsigned long long *>(smem + Lo.rkey);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bars);
     uint64_t *full = bars, *empty = bars + kMaxNS, *tfull = bars + 2 * kMaxNS,
@@ -178,8 +175,6 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         vrow0[c] = n;
     }
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
-    for (int e = tid; e < kSlots * kMaxQ; e += kThreads) cmin[e] = ~0ull;
-    for (int e = tid; e < kSlots; e += kThreads) ckey[e] = 0ull;
     // query rows 0..31 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
     const int nch = d / 8;                         // 16-byte chunks per row
     for (int e = tid; e < kMaxQ * nch; e += kThreads) {
@@ -362,14 +357,14 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             }
         }
     } else {
-        // ---- epilogue: warps 0-3, warp w owns rows 32w..32w+31 ---------------------
+        // ---- epilogue: warps 0-3 ----------------------------------------------------
         const float INF = __int_as_float(0x7f800000);
         float qreg[kMaxQ];
 #pragma unroll
         for (int a = 0; a < kMaxQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
         unsigned char *dw = dist + warp * 32 * 128;
         const int r = warp * 32 + lane;
-        int fin = 0;   // candidates finished so far (the same in every epilogue thread)
+        const int coff = ((lane >> 2) << 4) + (lane & 3) * 4;   // column phase: my query vector's word
         bool ok = true;
         for (int t = 0; t < n_tiles; ++t) {
             // all four warps leave together if one of them gave up
@@ -378,10 +373,12 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
                  wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
             ok = __all_sync(0xffffffffu, ok);   // the tensor-memory load below is warp-wide
+            const Meta *mt = meta + (t % MR) * kRowsN;
+            const int t0 = t * kRowsN;
+            const int rows_t = min(kRowsN, R - t0);
             if (ok) {
                 tc_fence_after();
-                const Meta *mt = meta + (t % MR) * kRowsN;
-                const int rows_w = min(32, R - t * kRowsN - warp * 32);
+                const int rows_w = min(32, rows_t - warp * 32);
                 uint32_t v[32];
                 if (rows_w > 0)
                     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kMaxQ), v);
@@ -390,95 +387,95 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 if (lane == 0) mbar_arrive(&tempty[buf]);
                 if (rows_w > 0) {
                     // row phase: lane = row r
-                    {
-                        const Meta m = mt[r];
-                        float best = INF;
-                        int ba = 0;
+                    const Meta m = mt[r];
+                    float best = INF;
+                    int ba = 0;
 #pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4) {
-                            float x[4];
+                    for (int c4 = 0; c4 < 8; ++c4) {
+                        float x[4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int a = c4 * 4 + i;
-                                // qreg is +inf past the query, which keeps those entries out
-                                const float d2 =
-                                    fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
-                                x[i] = d2;
-                                if (d2 < best) {
-                                    best = d2;
-                                    ba = a;
-                                }
+                        for (int i = 0; i < 4; ++i) {
+                            const int a = c4 * 4 + i;
+                            // qreg is +inf past the query, which keeps those entries out
+                            const float d2 = fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
+                            x[i] = d2;
+                            if (d2 < best) {
+                                best = d2;
+                                ba = a;
                             }
-                            *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
-                                make_float4(x[0], x[1], x[2], x[3]);
                         }
-                        rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
+                        *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                            make_float4(x[0], x[1], x[2], x[3]);
                     }
-                    __syncwarp();
-                    // column phase: lane = query vector a, rows of this warp in order
-                    {
-                        const int a = lane;
-                        int cur = -1;
-                        float bmin = INF;
-                        int brow = 0;
-                        unsigned long long kmax = 0;
-                        const int coff = ((a >> 2) << 4) + (a & 3) * 4;
-                        for (int j = 0; j < rows_w; ++j) {
-                            const Meta mj = mt[warp * 32 + j];
-                            if (mj.slot != cur) {
-                                if (cur >= 0) {
-                                    const int sl = cur % kSlots;
-                                    if (a < mq) atomicMin(&cmin[sl * kMaxQ + a], dkey(bmin, (uint32_t)brow));
-                                    if (a == 0) atomicMax(&ckey[sl], kmax);
-                                }
-                                cur = mj.slot;
-                                bmin = INF;
-                                brow = 0;
-                                kmax = 0;
-                            }
-                            const float x =
-                                *reinterpret_cast<const float *>(dw + j * 128 + (coff ^ ((j & 7) << 4)));
-                            if (x < bmin) {
-                                bmin = x;
-                                brow = mj.row_in;
-                            }
-                            const unsigned long long kj = rkey[warp * 32 + j];
-                            kmax = kj > kmax ? kj : kmax;
-                        }
-                        const int sl = cur % kSlots;
-                        if (a < mq) atomicMin(&cmin[sl * kMaxQ + a], dkey(bmin, (uint32_t)brow));
-                        if (a == 0) atomicMax(&ckey[sl], kmax);
-                    }
-                    __syncwarp();
+                    rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
                 }
             }
-            named_barrier_sync(2, kEpi);   // every atomic of this tile is done
-            // candidates whose last row lies in tiles 0..t are complete
-            const int rows_done = min(R, (t + 1) * kRowsN);
-            int fend = fin;
-            while (fend < ncand && vrow0[fend + 1] <= rows_done) ++fend;
-            if (ok) {
-                for (int c = fin + warp; c < fend; c += kEpi / 32) {
-                    const int sl = c % kSlots;
-                    const unsigned long long kc = lane < mq ? cmin[sl * kMaxQ + lane] : 0ull;
-                    const uint32_t bits = (uint32_t)(kc >> 32);
-                    const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-                    const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
-                    const int src = __ffs(who) - 1;
-                    int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)kc, src);
-                    const unsigned long long kr = ckey[sl];
-                    if (mx < (uint32_t)(kr >> 32)) {
-                        pa = (int)(kr & 0xff);
-                        pr = (int)((kr >> 8) & 0xffffff);
+            named_barrier_sync(2, kEpi);   // the tile's distances and row keys are visible
+            if (ok && warp * 32 < rows_t) {
+                // column phase: lane = query vector; candidates whose first row in this
+                // tile lies in rows lo..hi-1 belong to this warp
+                const int lo = warp * 32, hi = min(lo + 32, rows_t);
+                int c = mt[lo].slot;
+                int j = lo;
+                if (lo > 0 && vrow0[c] - t0 < lo) {   // begun in an earlier warp's rows
+                    j = vrow0[c + 1] - t0;
+                    ++c;
+                }
+                const unsigned long long *cin = carry + ((t + 1) & 1) * (kMaxQ + 1);
+                unsigned long long *cout = carry + (t & 1) * (kMaxQ + 1);
+                while (j < hi) {
+                    const int cs = vrow0[c] - t0;                 // < 0: continues from the last tile
+                    const int je = min(vrow0[c + 1] - t0, rows_t);
+                    float bmin = INF;
+                    int brow = 0;
+                    unsigned long long kmax = 0;
+                    if (cs < 0) {
+                        const unsigned long long k0 = cin[lane];
+                        bmin = __uint_as_float((uint32_t)(k0 >> 32));
+                        brow = (int)(uint32_t)k0;
+                        kmax = cin[kMaxQ];
                     }
-                    if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
-                    __syncwarp();
-                    cmin[sl * kMaxQ + lane] = ~0ull;   // the slot is free for a later candidate
-                    if (lane == 0) ckey[sl] = 0ull;
+                    for (int j0 = j; j0 < je; j0 += 4) {
+                        float x[4];
+                        unsigned long long kk[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
+                            x[i] = *reinterpret_cast<const float *>(dist + jr * 128 +
+                                                                    (coff ^ ((jr & 7) << 4)));
+                            kk[i] = rkey[jr];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (x[i] < bmin) {
+                                bmin = x[i];
+                                brow = j0 + i - cs;   // row inside the candidate's set
+                            }
+                            kmax = kk[i] > kmax ? kk[i] : kmax;
+                        }
+                    }
+                    if (vrow0[c + 1] - t0 <= rows_t) {
+                        // complete: max over query vectors of the row minima vs max over rows
+                        const unsigned long long key = dkey(bmin, (uint32_t)brow);
+                        const uint32_t bits = lane < mq ? __float_as_uint(bmin) : 0u;
+                        const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
+                        const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
+                        const int src = __ffs(who) - 1;
+                        int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)key, src);
+                        if (mx < (uint32_t)(kmax >> 32)) {
+                            pa = (int)(kmax & 0xff);
+                            pr = (int)((kmax >> 8) & 0xffffff);
+                        }
+                        if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
+                    } else {
+                        // continues into the next tile
+                        cout[lane] = dkey(bmin, (uint32_t)brow);
+                        if (lane == 0) cout[kMaxQ] = kmax;
+                    }
+                    j = je;
+                    ++c;
                 }
             }
-            fin = fend;
-            named_barrier_sync(3, kEpi);   // cleared slots are visible to the next tile
         }
     }
 
