@@ -195,14 +195,23 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
                 }
                 uint2 w = make_uint2(0, 0);
                 if (row_ok) w = *reinterpret_cast<const uint2 *>(ring + ((u % kPR) * kProd + p) * 8);
+                // The previous stage is signalled here, one step late: its stores were
+                // issued an iteration ago, so the proxy fence does not wait on the
+                // stores this iteration is about to make.
+                if (u > 0) {
+                    fence_proxy_async();
+                    mbar_arrive(&full[(u - 1) % kNS]);
+                }
                 unsigned char *dst = stB + s * kBStage;
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
                     *reinterpret_cast<uint4 *>(dst + sw128_off(pr, 4 * ph + c)) =
                         spread16((c < 2 ? w.x : w.y) >> (16 * (c & 1)));
-                fence_proxy_async();
-                mbar_arrive(&full[s]);
             }
+        }
+        if (ok && u > 0) {
+            fence_proxy_async();
+            mbar_arrive(&full[(u - 1) % kNS]);
         }
         cp_async_wait<0>();
         if (p == 0 && !ok) {
