@@ -486,7 +486,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// distance of each candidate's recorded pair, directly in FP32; one warp per candidate
+// distance of each candidate's recorded pair, directly in FP32; one warp per
+// candidate, all of the row's loads issued before the first use
 __global__ void __launch_bounds__(256)
 k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
           const float *__restrict__ vec, const int64_t *__restrict__ set_off,
@@ -504,17 +505,27 @@ k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     pr.y = min(max(pr.y, 0), (int)(set_off[id + 1] - set_off[id]) - 1);
     const float4 *x4 = reinterpret_cast<const float4 *>(qvec + (qoff[q] + pr.x) * d);
     const float4 *y4 = reinterpret_cast<const float4 *>(vec + (set_off[id] + pr.y) * d);
+    const int n4 = d / 4;
     float s = 0.0f;
-    for (int k = lane; k < d / 4; k += 32) {
-        const float4 x = x4[k], y = y4[k];
-        float u = x.x - y.x;
-        s = fmaf(u, u, s);
-        u = x.y - y.y;
-        s = fmaf(u, u, s);
-        u = x.z - y.z;
-        s = fmaf(u, u, s);
-        u = x.w - y.w;
-        s = fmaf(u, u, s);
+    for (int k0 = 0; k0 < n4; k0 += 32 * 4) {
+        float4 x[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + 32 * i + lane;
+            x[i] = k < n4 ? x4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            y[i] = k < n4 ? y4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float u = x[i].x - y[i].x;
+            s = fmaf(u, u, s);
+            u = x[i].y - y[i].y;
+            s = fmaf(u, u, s);
+            u = x[i].z - y[i].z;
+            s = fmaf(u, u, s);
+            u = x[i].w - y[i].w;
+            s = fmaf(u, u, s);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
