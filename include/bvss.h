@@ -234,7 +234,7 @@ int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int6
  * caching allocator, or a latency-bound serving loop that must not call
  * cudaMalloc / cudaFree (which can synchronise the whole device).  It calls
  * neither, nor any allocating library routine: its scratch memory is one
- * fixed array of about 1.6 MB compiled into the library, which every GPU that
+ * fixed array of about 5.2 MB compiled into the library, which every GPU that
  * loads the library holds until the process exits.
  *   h          device, n_queries rows of h_stride uint16 Hamming scores
  *              (0xFFFF = set outside F1), 16-byte aligned; the layout of

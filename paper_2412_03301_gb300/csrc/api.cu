@@ -206,7 +206,7 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 256)));
         BVSS_CU(dalloc(&w.hist, (size_t)cq * (m + 1)));
         BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
-        BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * 4));
+        BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * kSelRangeWords));
         BVSS_CU(dalloc(&w.cand, (size_t)cq * cC));
         BVSS_CU(dalloc(&w.cand_dist, (size_t)cq * cC));
         BVSS_CU(dalloc(&w.pair, (size_t)cq * cC));

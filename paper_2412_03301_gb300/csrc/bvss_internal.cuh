@@ -13,6 +13,7 @@ namespace bvss {
 constexpr int kMaxPlanes = 8;          // cached first-layer gate planes (one per M)
 constexpr uint16_t kGatedOut = 0xFFFF; // h of a set outside F1
 constexpr int kSelChunk = 16384;       // sets per CTA in the candidate select
+constexpr int kSelRangeWords = 32;     // per chunk: 8 warp ranges x (lt, eq, tie rank, slot)
 constexpr int kOffRing = 4;            // pinned staging slots for query offsets
 constexpr int kProfEvents = BVSS_N_STAGES + 1;  // events per profiled batch
 

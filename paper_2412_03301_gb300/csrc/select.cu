@@ -7,7 +7,7 @@
 //   2. H* = smallest value whose cumulative count reaches
 //      C' = min(C, |F1|); sets with h < H* all qualify, and the
 //      first (C' - #{h < H*}) sets with h == H* in id order      (k_thresh)
-//   3. per chunk of sets: counts of h < H* and h == H*          (k_count)
+//   3. per warp range of sets: counts of h < H* and h == H*     (k_count)
 //   4. per query: exclusive scans over chunks                     (k_offsets)
 //   5. stable compaction in id order                              (k_write)
 // The result lists the C' candidate ids in ascending id order, -1 padded.
@@ -88,52 +88,66 @@ k_thresh(const uint32_t *__restrict__ hist, int m, int C, int32_t *__restrict__ 
     for (int j = cp + tid; j < C; j += kSelThreads) cand[(int64_t)q * C + j] = -1;
 }
 
+// Each chunk of kSelChunk sets is split into kSelWarps ranges of kSelSpan
+// sets, one per warp; counts and output slots are kept per range.
+constexpr int kSelWarps = kSelThreads / 32;
+constexpr int kSelSpan = kSelChunk / kSelWarps;
+static_assert(kSelRangeWords == kSelWarps * 4, "per-chunk record size");
+
+__device__ __forceinline__ void sel_range(int64_t n_sets, int warp, int64_t &w0, int64_t &w1) {
+    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
+    const int64_t chunk_end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    w0 = c0 + (int64_t)warp * kSelSpan;
+    w1 = w0 + kSelSpan < chunk_end ? w0 + kSelSpan : chunk_end;
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
-        const int32_t *__restrict__ thr, int32_t *__restrict__ chunk) {
-    __shared__ int scan_sh[kSelThreads / 32 + 1];
+        const int32_t *__restrict__ thr, int32_t *__restrict__ ranges) {
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int H = thr[q * 4];
-    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
-    const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
+    int64_t w0, w1;
+    sel_range(n_sets, warp, w0, w1);
     int lt = 0, eq = 0;
     if (H >= 0) {
         const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
 #pragma unroll 4
-        for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
-            const uint4 v = row4[i8];
+        for (int64_t i0 = w0 + lane * 8; i0 < w1; i0 += 256) {
+            const uint4 v = row4[i0 / 8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int val = (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
-                const bool in = i8 * 8 + e < end;
+                const bool in = i0 + e < w1;
                 lt += in && val < H;
                 eq += in && val == H;
             }
         }
     }
-    int tl, te;
-    block_excl_scan<kSelThreads>(lt, scan_sh, &tl);
-    block_excl_scan<kSelThreads>(eq, scan_sh, &te);
-    if (threadIdx.x == 0) {
-        int32_t *o = chunk + ((int64_t)q * n_chunks + blockIdx.x) * 4;
-        o[0] = tl;
-        o[1] = te;
+    lt = (int)__reduce_add_sync(0xffffffffu, (uint32_t)lt);
+    eq = (int)__reduce_add_sync(0xffffffffu, (uint32_t)eq);
+    if (lane == 0) {
+        int32_t *o = ranges + (((int64_t)q * n_chunks + blockIdx.x) * kSelWarps + warp) * 4;
+        o[0] = lt;
+        o[1] = eq;
     }
 }
 
+// per query: in id order over all ranges, the rank of each range's first tie
+// and its first output slot (the first `take` ties by id are selected)
 __global__ void __launch_bounds__(kSelThreads)
-k_offsets(const int32_t *__restrict__ thr, int n_chunks, int32_t *__restrict__ chunk) {
+k_offsets(const int32_t *__restrict__ thr, int n_ranges, int32_t *__restrict__ ranges) {
     __shared__ int scan_sh[kSelThreads / 32 + 1];
     const int q = blockIdx.x;
     const int take = thr[q * 4 + 2];
     int run_eq = 0, run_sel = 0;
-    for (int base = 0; base < n_chunks; base += kSelThreads) {
-        const int c = base + threadIdx.x;
-        int32_t *o = chunk + ((int64_t)q * n_chunks + c) * 4;
+    for (int base = 0; base < n_ranges; base += kSelThreads) {
+        const int r = base + threadIdx.x;
+        int32_t *o = ranges + ((int64_t)q * n_ranges + r) * 4;
         int lt = 0, eq = 0;
-        if (c < n_chunks) {
+        if (r < n_ranges) {
             lt = o[0];
             eq = o[1];
         }
@@ -143,7 +157,7 @@ k_offsets(const int32_t *__restrict__ thr, int n_chunks, int32_t *__restrict__ c
         const int sel = lt + max(0, min(take - eqb, eq));
         int ts;
         const int ex_sel = block_excl_scan<kSelThreads>(sel, scan_sh, &ts);
-        if (c < n_chunks) {
+        if (r < n_ranges) {
             o[2] = eqb;
             o[3] = run_sel + ex_sel;
         }
@@ -163,31 +177,28 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
     return x;
 }
 
-// Stable compaction of one chunk: warp w owns sets [c0 + w S, c0 + (w + 1) S),
-// S = kSelChunk / 8.  Pass 1 counts each warp's h < H* and h == H*; a prefix
-// over the 8 warps gives each warp its first output slot and the id-order rank
-// of its first tie; pass 2 re-reads the warp's range (from L1/L2) 256 sets at a
-// time, with warp-shuffle scans only where the warp's ballot shows a candidate.
+// Stable compaction: warp w of a chunk walks its range 256 sets at a time and
+// writes the selected ids from the range's first output slot on, with
+// warp-shuffle scans only where the warp's ballot shows a candidate.
 __global__ void __launch_bounds__(kSelThreads)
 k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
-        const int32_t *__restrict__ thr, const int32_t *__restrict__ chunk, int C,
+        const int32_t *__restrict__ thr, const int32_t *__restrict__ ranges, int C,
         int32_t *__restrict__ cand) {
-    constexpr int kWarps = kSelThreads / 32;
-    constexpr int kSpan = kSelChunk / kWarps;       // sets per warp
-    __shared__ int w_lt[kWarps], w_eq[kWarps], w_rank[kWarps], w_pos[kWarps];
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
     const int H = thr[q * 4];
     if (H < 0) return;   // uniform over the CTA
     const int take = thr[q * 4 + 2];
-    const int32_t *o = chunk + ((int64_t)q * n_chunks + blockIdx.x) * 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
-    const int64_t w0 = c0 + (int64_t)warp * kSpan;
-    const int64_t chunk_end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
-    const int64_t w1 = w0 + kSpan < chunk_end ? w0 + kSpan : chunk_end;
+    int64_t w0, w1;
+    sel_range(n_sets, warp, w0, w1);
+    const int32_t *o = ranges + (((int64_t)q * n_chunks + blockIdx.x) * kSelWarps + warp) * 4;
+    if (o[0] == 0 && (o[1] == 0 || o[2] >= take)) return;   // nothing selected in this range
+    int rank = o[2], pos = o[3];
     const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
-    auto load8 = [&](int64_t i0, int (&val)[8]) {
+    int32_t *out = cand + (int64_t)q * C;
+    for (int64_t i0 = w0 + lane * 8; i0 - lane * 8 < w1; i0 += 256) {
+        int val[8];
         if (i0 < w1) {
             const uint4 v = row4[i0 / 8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -198,42 +209,6 @@ k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
 #pragma unroll
             for (int e = 0; e < 8; ++e) val[e] = 0xFFFF;
         }
-    };
-    // pass 1: this warp's counts
-    int lt = 0, eq = 0;
-#pragma unroll 4
-    for (int64_t i0 = w0 + lane * 8; i0 < w1; i0 += 256) {
-        int val[8];
-        load8(i0, val);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            lt += val[e] < H;
-            eq += val[e] == H;
-        }
-    }
-    lt = __reduce_add_sync(0xffffffffu, (uint32_t)lt);
-    eq = __reduce_add_sync(0xffffffffu, (uint32_t)eq);
-    if (lane == 0) {
-        w_lt[warp] = lt;
-        w_eq[warp] = eq;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int rank = o[2], pos = o[3];
-        for (int w = 0; w < kWarps; ++w) {
-            w_rank[w] = rank;
-            w_pos[w] = pos;
-            pos += w_lt[w] + max(0, min(take - rank, w_eq[w]));
-            rank += w_eq[w];
-        }
-    }
-    __syncthreads();
-    int rank = w_rank[warp], pos = w_pos[warp];
-    int32_t *out = cand + (int64_t)q * C;
-    // pass 2: write this warp's candidates in id order
-    for (int64_t i0 = w0 + lane * 8; i0 - lane * 8 < w1; i0 += 256) {
-        int val[8];
-        load8(i0, val);
         int n_lt = 0, n_eq = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -276,7 +251,7 @@ cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, 
     k_hist<<<g2, kSelThreads, smem, st>>>(h, n_sets, hs, m, hist);
     k_thresh<<<n_q, kSelThreads, 0, st>>>(hist, m, C, thr, cand);
     k_count<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk);
-    k_offsets<<<n_q, kSelThreads, 0, st>>>(thr, n_chunks, chunk);
+    k_offsets<<<n_q, kSelThreads, 0, st>>>(thr, n_chunks * kSelWarps, chunk);
     k_write<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk, C, cand);
     return cudaGetLastError();
 }
@@ -298,7 +273,7 @@ constexpr int kNoAllocMaxM = 8192;
 constexpr int kNoAllocMaxChunks = 1024;
 constexpr size_t kNoAllocHistWords = (size_t)kNoAllocMaxQ * (kNoAllocMaxM + 1);
 constexpr size_t kNoAllocThrWords = (size_t)kNoAllocMaxQ * 4;
-constexpr size_t kNoAllocChunkWords = (size_t)kNoAllocMaxQ * kNoAllocMaxChunks * 4;
+constexpr size_t kNoAllocChunkWords = (size_t)kNoAllocMaxQ * kNoAllocMaxChunks * kSelRangeWords;
 constexpr size_t kNoAllocWords = kNoAllocHistWords + kNoAllocThrWords + kNoAllocChunkWords;
 constexpr int kNoAllocMaxDevices = 64;
 
