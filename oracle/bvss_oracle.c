@@ -22,6 +22,10 @@
  *   orc_heap_select     Alg. 6 lines 10-18 (bounded max-heap of T entries)
  *   orc_haus*           Def. 4 (Hausdorff distance), in FP64
  *   orc_refine_topk     Alg. 6 lines 19-23 (exact re-rank, top-k)
+ *   orc_haus_h          Haus^H of Alg. 2: Def. 4 with the Hamming distance
+ *                       between per-vector codes in place of the norm
+ *   orc_alg2_scores     Alg. 2 lines 6-8 (Haus^H against every set)
+ *   orc_alg2_select     Alg. 2 line 9 (the c smallest d_H)
  *
  * Readings where the paper is silent (the same readings the GPU path uses):
  *   - activations a_j are FP32 sums taken in the order of W's row, starting
@@ -32,7 +36,8 @@
  *   - counts saturate at 255 (uint8 storage);
  *   - the heap orders entries by the pair (d, i) and the sets of F1 are
  *     visited in ascending id, so it keeps the T smallest pairs (d, i);
- *   - top-k orders by (distance, id) and pads with (-1, +inf).
+ *   - top-k orders by (distance, id) and pads with (-1, +inf);
+ *   - Alg. 2 line 9 keeps exactly c sets, the c smallest pairs (d_H, id).
  * Non-finite inputs are outside the method's domain; results are undefined.
  */
 #include <math.h>
@@ -453,4 +458,75 @@ int orc_bruteforce_topk(const float *Q, int64_t mq, const float *vectors,
                              out_dist, NULL);
     free(all);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 2: Haus^H, the Hausdorff distance of Def. 4 with the Hamming   */
+/* distance between per-vector codes (m-bit masks, counted bit by     */
+/* bit) in place of the norm:                                          */
+/*   max( max_a min_r ham(a, r), max_r min_a ham(a, r) )              */
+/* ------------------------------------------------------------------ */
+static int32_t orc_ham_codes(const uint32_t *x, const uint32_t *y, int32_t m) {
+    int32_t d = 0;
+    for (int32_t p = 0; p < m; ++p)
+        if (((x[p >> 5] >> (p & 31)) & 1u) != ((y[p >> 5] >> (p & 31)) & 1u)) ++d;
+    return d;
+}
+
+int32_t orc_haus_h(const uint32_t *qmask, int64_t mq, const uint32_t *vmask, int64_t mv,
+                   int32_t m) {
+    const int32_t words = (m + 31) / 32;
+    int32_t fwd = 0, bwd = 0;
+    for (int64_t a = 0; a < mq; ++a) {          /* max over query codes of the nearest row */
+        int32_t best = INT32_MAX;
+        for (int64_t r = 0; r < mv; ++r) {
+            const int32_t h = orc_ham_codes(qmask + a * words, vmask + r * words, m);
+            if (h < best) best = h;
+        }
+        if (best > fwd) fwd = best;
+    }
+    for (int64_t r = 0; r < mv; ++r) {          /* max over rows of the nearest query code */
+        int32_t best = INT32_MAX;
+        for (int64_t a = 0; a < mq; ++a) {
+            const int32_t h = orc_ham_codes(qmask + a * words, vmask + r * words, m);
+            if (h < best) best = h;
+        }
+        if (best > bwd) bwd = best;
+    }
+    return fwd > bwd ? fwd : bwd;
+}
+
+/* Alg. 2 lines 6-8: d_H for every set j of the database (mask holds the  */
+/* codes of all database vectors, set j is rows set_off[j]..set_off[j+1]) */
+int orc_alg2_scores(const uint32_t *qmask, int64_t mq, const uint32_t *mask,
+                    const int64_t *set_off, int64_t n_sets, int32_t m, int32_t *score) {
+    const int32_t words = (m + 31) / 32;
+    for (int64_t j = 0; j < n_sets; ++j)
+        score[j] = orc_haus_h(qmask, mq, mask + set_off[j] * words, set_off[j + 1] - set_off[j], m);
+    return ORC_OK;
+}
+
+/* Alg. 2 line 9: the c smallest pairs (d_H, j) by a full sort; out_ids    */
+/* receives them in ascending id order, *n_out = min(c, n_sets).          */
+static int orc_pair_cmp(const void *pa, const void *pb) {
+    const int64_t *a = (const int64_t *)pa, *b = (const int64_t *)pb;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    return a[1] < b[1] ? -1 : (a[1] > b[1]);
+}
+
+int orc_alg2_select(const int32_t *score, int64_t n_sets, int32_t c, int32_t *out_ids,
+                    int64_t *n_out) {
+    int64_t *pr = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(n_sets > 0 ? n_sets : 1));
+    if (!pr) return ORC_ENOMEM;
+    for (int64_t j = 0; j < n_sets; ++j) {
+        pr[2 * j] = score[j];
+        pr[2 * j + 1] = j;
+    }
+    qsort(pr, (size_t)n_sets, 2 * sizeof(int64_t), orc_pair_cmp);
+    const int64_t n = n_sets < c ? n_sets : c;
+    for (int64_t t = 0; t < n; ++t) out_ids[t] = (int32_t)pr[2 * t + 1];
+    qsort(out_ids, (size_t)n, sizeof(int32_t), orc_i32_cmp);
+    *n_out = n;
+    free(pr);
+    return ORC_OK;
 }

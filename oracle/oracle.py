@@ -76,6 +76,9 @@ def _load():
         "orc_haus_directed": (dbl, [P, i64, P, i64, i32]),
         "orc_refine_topk": (ctypes.c_int, [P, i64, P, P, i32, P, i64, i32, P, P, P]),
         "orc_bruteforce_topk": (ctypes.c_int, [P, i64, P, P, i64, i32, i32, P, P]),
+        "orc_haus_h": (i32, [P, i64, P, i64, i32]),
+        "orc_alg2_scores": (ctypes.c_int, [P, i64, P, P, i64, i32, P]),
+        "orc_alg2_select": (ctypes.c_int, [P, i64, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -284,6 +287,43 @@ def query(index: Index, Q, k, C, A, M):
     ids, dist, cand_dist = refine_topk(Q, index.vectors, index.set_off, cand, k)
     return dict(qpos=qpos, qmask=qmask, cq=cq, sq=sq, plist=plist, gate=gate,
                 h=h, cand=cand, cand_dist=cand_dist, ids=ids, dist=dist)
+
+
+def haus_h(qmask, vmask, m):
+    """Haus^H (Alg. 2) between two sets of m-bit codes, rows of uint32 words."""
+    qmask = _c(qmask, np.uint32)
+    vmask = _c(vmask, np.uint32)
+    return int(_load().orc_haus_h(_p(qmask), qmask.shape[0], _p(vmask), vmask.shape[0], m))
+
+
+def alg2_scores(qmask, mask, set_off, m):
+    qmask = _c(qmask, np.uint32)
+    mask = _c(mask, np.uint32)
+    set_off = _c(set_off, np.int64)
+    n = set_off.shape[0] - 1
+    score = np.empty(n, np.int32)
+    _check(_load().orc_alg2_scores(_p(qmask), qmask.shape[0], _p(mask), _p(set_off), n, m,
+                                   _p(score)), "alg2_scores")
+    return score
+
+
+def alg2_select(score, c):
+    score = _c(score, np.int32)
+    out = np.empty(max(1, min(c, score.shape[0])), np.int32)
+    n = ctypes.c_int64()
+    _check(_load().orc_alg2_select(_p(score), score.shape[0], c, _p(out), ctypes.byref(n)),
+           "alg2_select")
+    return out[:n.value]
+
+
+def query_alg2(index: Index, Q, k, C):
+    """Alg. 2 (plain BioVSS) for one query set; returns every intermediate."""
+    qpos, qmask = encode(Q, index.proj, index.L)
+    score = alg2_scores(qmask, index.mask, index.set_off, index.m)
+    cand = alg2_select(score, C)
+    ids, dist, cand_dist = refine_topk(Q, index.vectors, index.set_off, cand, k)
+    return dict(qpos=qpos, qmask=qmask, score=score, cand=cand, cand_dist=cand_dist, ids=ids,
+                dist=dist)
 
 
 if __name__ == "__main__":
