@@ -91,12 +91,19 @@ typedef struct bvss_params {
                                     form (one FP8 GEMM over all pairs, masked by layer 1); both
                                     give identical h */
 
+#define BVSS_SEARCH_ALG2 4  /* the plain BioVSS search (Alg. 2) instead of Alg. 6: candidates are
+                               the C sets of smallest Haus^H -- Def. 4 with the Hamming distance
+                               between per-vector codes in place of the norm -- over every set, by
+                               (Haus^H, id); A and M are not used and the trace's cq, sq and plist
+                               are not written (its h holds Haus^H).  Query sets of at most 32
+                               vectors.  Combines with BVSS_SEARCH_FAST */
+
 typedef struct bvss_search {
     int32_t k;      /* results per query set, >= 1 */
     int32_t C;      /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
-    int32_t flags;  /* 0, or BVSS_SEARCH_FAST and/or BVSS_SEARCH_POPC_SCAN */
+    int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2 */
     int32_t reserved;
 } bvss_search;
 

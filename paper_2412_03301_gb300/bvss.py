@@ -35,6 +35,7 @@ class bvss_search(ctypes.Structure):
 BVSS_BUILD_BF16 = 1
 BVSS_SEARCH_FAST = 1
 BVSS_SEARCH_POPC_SCAN = 2
+BVSS_SEARCH_ALG2 = 4
 
 
 class bvss_trace(ctypes.Structure):
@@ -171,13 +172,14 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
     return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
 
 
-def _search_flags(fast, popc_scan):
-    return (BVSS_SEARCH_FAST if fast else 0) | (BVSS_SEARCH_POPC_SCAN if popc_scan else 0)
+def _search_flags(fast, popc_scan, alg2=False):
+    return ((BVSS_SEARCH_FAST if fast else 0) | (BVSS_SEARCH_POPC_SCAN if popc_scan else 0)
+            | (BVSS_SEARCH_ALG2 if alg2 else 0))
 
 
 def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
-               M: int = 1, fast: bool = False, popc_scan: bool = False, out_ids=None,
-               out_dist=None, stream=None):
+               M: int = 1, fast: bool = False, popc_scan: bool = False, alg2: bool = False,
+               out_ids=None, out_dist=None, stream=None):
     """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
 
     q_vectors and the outputs may live on the host or on the index's GPU."""
@@ -189,7 +191,7 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
         out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan))
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -197,7 +199,7 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
 
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
                      A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
-                     stream=None):
+                     alg2: bool = False, stream=None):
     """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
 
     Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
@@ -220,7 +222,7 @@ def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C
     tr = bvss_trace(**{name: t[name].data_ptr() for name in t})
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan))
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
     _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                                 _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
     t["ids"] = ids

@@ -204,7 +204,7 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         BVSS_CU(dalloc(&w.gate, (size_t)cq * ix->NW));
         BVSS_CU(dalloc(&w.q8, scan_mma_q8_bytes(cq, m)));
         BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 256)));
-        BVSS_CU(dalloc(&w.hist, (size_t)cq * (m + 1)));
+        BVSS_CU(dalloc(&w.hist, (size_t)cq * ((m > 2 * L ? m : 2 * L) + 1)));
         BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
         BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * kSelRangeWords));
         BVSS_CU(dalloc(&w.cand, (size_t)cq * cC));
@@ -280,11 +280,12 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (s->k < 1) return fail(BVSS_EINVAL, "k = %d: need k >= 1", s->k);
     if (s->C < s->k || s->C > BVSS_MAX_C)
         return fail(BVSS_EINVAL, "C = %d: need k <= C <= %d", s->C, BVSS_MAX_C);
-    if (s->A < 1 || s->A > L || s->A > BVSS_MAX_A)
+    if ((s->flags & BVSS_SEARCH_ALG2) == 0 && (s->A < 1 || s->A > L || s->A > BVSS_MAX_A))
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
-    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN))
+    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2))
         return fail(BVSS_EINVAL, "unknown search flags");
+    const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
     const bool fast = (s->flags & BVSS_SEARCH_FAST) != 0;
     const bool tensor_scan = (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
     if (fast && !ix->vec16)
@@ -293,7 +294,8 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (n_queries == 0) return BVSS_OK;
     if (!q_vectors || !out_ids || !out_dist)
         return fail(BVSS_EINVAL, "query vectors or outputs are NULL");
-    int rc = check_offsets(q_offsets, n_queries, BVSS_MAX_QSET, "query");
+    // Alg. 2's scoring kernel holds one bit per query vector in a 32-bit word
+    int rc = check_offsets(q_offsets, n_queries, alg2 ? 32 : BVSS_MAX_QSET, "query");
     if (rc) return rc;
     rc = check_device(ix);
     if (rc) return rc;
@@ -352,24 +354,30 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
                                     cudaMemcpyHostToDevice, st));
             qv = w.qvec;
         }
-        // Alg. 6 lines 1-4
+        // Alg. 6 lines 1-4 (Alg. 2 lines 2-5: the codes only)
         BVSS_CU(launch_encode(qv, nv, d, ix->proj, m, ix->p.fanin, L, w.qpos, nullptr, st));
-        BVSS_CU(launch_query_prep(w.qpos, w.qoff, nb, m, L, A, w.sq, w.plist,
-                                  tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
+        int64_t launches = 1;
+        if (!alg2) {
+            BVSS_CU(launch_query_prep(w.qpos, w.qoff, nb, m, L, A, w.sq, w.plist,
+                                      tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
+            ++launches;
+        }
         if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
-        int64_t launches = 2;
         // lines 5-9: layer-1 words per 32 sets (and the FP8 query operand)
-        if (gate_mode == 1) {
+        if (!alg2 && gate_mode == 1) {
             BVSS_CU(launch_gate(plane, ix->NW, w.plist, A, nb, w.gate, st));
             ++launches;
         }
-        if (tensor_scan) {
+        if (!alg2 && tensor_scan) {
             BVSS_CU(launch_expand_q(w.sq, nb, W, w.q8, w.qpop, st));
             ++launches;
         }
         if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
-        // line 12
-        if (tensor_scan)
+        // line 12 (Alg. 2 lines 6-8: Haus^H against every set)
+        if (alg2)
+            BVSS_CU(launch_haus_h(w.qpos, w.qoff, nb, ix->codes, ix->set_off, ix->n_sets, m, L,
+                                  w.h, hs, st));
+        else if (tensor_scan)
             BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
                                     w.q8, w.qpop, nb, w.h, hs, ix->err, st));
         else
@@ -377,8 +385,9 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
                                 hs, st));
         ++launches;
         if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
-        // lines 10-18
-        BVSS_CU(launch_select(w.h, ix->n_sets, hs, m, nb, C, w.hist, w.thr, w.chunk, w.cand, st));
+        // lines 10-18 (Alg. 2 line 9); scores run up to m (Hamming of sketches) or 2L (Haus^H)
+        BVSS_CU(launch_select(w.h, ix->n_sets, hs, alg2 ? 2 * L : m, nb, C, w.hist, w.thr, w.chunk,
+                              w.cand, st));
         launches += kSelectKernels;
         if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
         // lines 19-23

@@ -139,6 +139,13 @@ cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t
                             const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
                             cudaStream_t st);
 
+// ---- alg2.cu: Haus^H scores of the plain BioVSS search (Alg. 2 lines 6-8) ----
+// h[q][j] = Haus^H between query set q's codes (qpos, L positions per vector,
+// at most 32 vectors per set) and set j's codes (codes, set_off)
+cudaError_t launch_haus_h(const uint16_t *qpos, const int64_t *qoff, int n_q,
+                          const uint16_t *codes, const int64_t *set_off, int64_t n_sets, int m,
+                          int L, uint16_t *h, int64_t hs, cudaStream_t st);
+
 // ---- select.cu
 constexpr int kSelectKernels = 5;   // kernels launch_select runs --------------------------------------------------------------
 // Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.

@@ -294,3 +294,58 @@ def test_fast_form_falls_back_and_validates(bv, orc):
     with pytest.raises(bv.BvssError) as e:
         bv.bvss_build(w2["vectors"].cuda(), w2["offsets"], w2["proj"], wta_l=8, bf16=True)
     assert e.value.code == bv.BVSS_EINVAL
+
+
+def _check_alg2(bv, orc, case, k, C, nq=None, fast=False):
+    """The plain BioVSS search (Alg. 2) against the oracle: Haus^H of every
+    set bit for bit, the candidates, their distances and the top-k."""
+    w = case.w
+    qo = w["q_offsets"] if nq is None else w["q_offsets"][:nq + 1]
+    nq = qo.shape[0] - 1
+    t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, fast=fast, alg2=True)
+    torch.cuda.synchronize()
+    qpos = _np(t["qpos"], np.uint16)
+    h = _np(t["h"], np.uint16)
+    cand, ncand, cdist = _np(t["cand"]), _np(t["n_cand"]), _np(t["cand_dist"])
+    ids, dist = _np(t["ids"]), _np(t["dist"])
+    for q in range(nq):
+        Q = case.qvec[qo[q]:qo[q + 1]]
+        r = orc.query_alg2(case.orc_ix, Q, k=k, C=C)
+        assert np.array_equal(qpos[qo[q]:qo[q + 1]], r["qpos"]), q
+        assert np.array_equal(h[q].astype(np.int64), r["score"].astype(np.int64)), q
+        n = int(ncand[q])
+        assert n == r["cand"].shape[0], q
+        assert np.array_equal(cand[q, :n], r["cand"]), q
+        np.testing.assert_allclose(cdist[q, :n], r["cand_dist"], rtol=RTOL, atol=0)
+        assert ids[q].tolist() == r["ids"].tolist(), q
+        fin = np.isfinite(r["dist"])
+        np.testing.assert_allclose(dist[q][fin], r["dist"][fin], rtol=RTOL, atol=0)
+
+
+def test_alg2_parity(bv, orc, small):
+    s = datagen.SMALL
+    _check_alg2(bv, orc, small, k=s["k"], C=s["C"], nq=40)
+    _check_alg2(bv, orc, small, k=10, C=small.ix.n_sets, nq=5)   # every set refined
+
+
+def test_alg2_edges_and_long_codes(bv, orc):
+    # one-vector sets and queries, m = 128, L = 5 (the smallest counter)
+    w = _workload(90, 1, 3, 16, 8, 7, 1, 4, 128, 3, seed=31)
+    case = Case(bv, orc, w, 5)
+    _check_alg2(bv, orc, case, k=5, C=30)
+    # L = 200 on m = 8192: eight counter planes
+    w = _workload(120, 2, 6, 64, 16, 5, 2, 9, 8192, 1, seed=32)
+    case = Case(bv, orc, w, 200)
+    _check_alg2(bv, orc, case, k=7, C=40)
+
+
+def test_alg2_with_fast_refine_and_limits(bv, orc):
+    w = _workload(800, 4, 20, 128, 32, 8, 3, 32, 1024, 8, seed=33)
+    case = Case(bv, orc, w, 24, bf16=True)
+    _check_alg2(bv, orc, case, k=10, C=300, fast=True)
+    # Alg. 2 scoring holds one bit per query vector: sets of 33 vectors are refused
+    w2 = _workload(50, 2, 4, 32, 8, 2, 33, 34, 256, 4, seed=34)
+    ix = bv.bvss_build(w2["vectors"].cuda(), w2["offsets"], w2["proj"], wta_l=8)
+    with pytest.raises(bv.BvssError) as e:
+        bv.bvss_query(ix, w2["q_vectors"].cuda(), w2["q_offsets"], k=3, C=10, alg2=True)
+    assert e.value.code == bv.BVSS_EINVAL
