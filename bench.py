@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=0,
                     help="override the number of query sets of the workload (profiling)")
     ap.add_argument("--recall-queries", type=int, default=200)
+    ap.add_argument("--alg2-queries", type=int, default=100,
+                    help="query sets for the plain BioVSS search (Alg. 2) line; 0 skips it")
     ap.add_argument("--cpu-sample-sets", type=int, default=2000)
     ap.add_argument("--cpu-sample-queries", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
@@ -434,6 +436,15 @@ def run_ours(args, rank, world, local_rank):
         got_d2 = true_d2_of(vec, vnorm, qv, qoff, off, qids, got)
         rs, rt = recall_at_k(got, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(), got_d2, c["k"])
         rec = {"recall_at_10": rs, "recall_at_10_ties": rt, "queries": len(qids)}
+        if args.alg2_queries > 0 and c["q_hi"] <= 32:
+            # the same query sets through the plain BioVSS search (Alg. 2)
+            nr = len(qids)
+            ids2, _ = bvss.bvss_query(ix, qv[:int(qoff[nr])], qoff[:nr + 1], alg2=True, **kw_fast)
+            got2 = ids2.cpu().numpy()
+            d2_2 = true_d2_of(vec, vnorm, qv, qoff, off, qids, got2)
+            rec["alg2"] = dict(zip(("recall_at_10", "recall_at_10_ties"),
+                                   recall_at_k(got2, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(),
+                                               d2_2, c["k"])))
         del vnorm, set_of_row
 
     # CPU baseline sample (rank 0): copy the sample before freeing the database
@@ -487,6 +498,37 @@ def run_ours(args, rank, world, local_rank):
     ms_plain, stage_plain, _, _, _ = timed(kw, False)
     ms, stage_ms, nbatch, launches, clk = timed(kw_fast, True)
     value = world * nq / (ms / 1e3)
+
+    # the plain BioVSS search (Alg. 2) on the same index: every set is scored with Haus^H over
+    # codes, so it is timed on the first --alg2-queries query sets only
+    alg2 = None
+    if rank == 0 and args.alg2_queries > 0 and c["q_hi"] <= 32:
+        na = min(args.alg2_queries, nq)
+        qo2, qv2 = qoff[:na + 1], qv[:int(qoff[na])]
+        oi2 = torch.empty((na, c["k"]), dtype=torch.int64, device=dev)
+        od2 = torch.empty((na, c["k"]), dtype=torch.float32, device=dev)
+        kw2 = dict(kw_fast, alg2=True)
+        bvss.bvss_query(ix, qv2, qo2, out_ids=oi2, out_dist=od2, stream=stream, **kw2)
+        torch.cuda.synchronize(dev)
+        bvss.bvss_profile_enable(ix, True)
+        bvss.bvss_profile_read(ix, reset=True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_rep = 3
+        a0.record(stream)
+        for _ in range(n_rep):
+            bvss.bvss_query(ix, qv2, qo2, out_ids=oi2, out_dist=od2, stream=stream, **kw2)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        st2, _, nl2 = bvss.bvss_profile_read(ix, reset=True)
+        bvss.bvss_profile_enable(ix, False)
+        t2 = a0.elapsed_time(a1) / n_rep
+        alg2 = {"value": na / (t2 / 1e3), "unit": UNIT, "query_sets": na, "ms_per_step": t2,
+                "stages_ms_per_step": {k: v / n_rep for k, v in st2.items()},
+                "gpu_launches_per_step": nl2 // n_rep,
+                "recall": rec.get("alg2") if rec else None,
+                "form": "plain BioVSS (Alg. 2): Haus^H over per-vector codes against every set, "
+                        "C smallest, BF16 tensor-core refine" if fast_ok else
+                        "plain BioVSS (Alg. 2), FP32 refine"}
 
     # end to end through the same API: pinned host query vectors in, host results out
     hq = qv.cpu().pin_memory()
@@ -548,6 +590,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": world * nq / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "alg2": alg2,
         "clocks": clk,
         "build_s": build_s,
         "work": {"gated_pairs_per_step": gated_pairs, "candidates_per_step": sum_cand,

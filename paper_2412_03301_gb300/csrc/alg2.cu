@@ -66,7 +66,21 @@ k_haus_h(const uint16_t *__restrict__ qpos, const int64_t *__restrict__ qoff,
             for (int b = 0; b < NB; ++b) c[b] = 0;
             if (rv) {
                 const uint16_t *pr = codes + (r0 + rc + lane) * L;
-                for (int t = 0; t < L; ++t) add_bits<NB>(c, qbits[pr[t]]);
+                if ((L & 7) == 0) {
+                    // rows are 16-byte aligned: eight positions per load
+                    const uint4 *pr4 = reinterpret_cast<const uint4 *>(pr);
+                    for (int t = 0; t < L / 8; ++t) {
+                        const uint4 v = pr4[t];
+                        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            add_bits<NB>(c, qbits[w[i] & 0xFFFFu]);
+                            add_bits<NB>(c, qbits[w[i] >> 16]);
+                        }
+                    }
+                } else {
+                    for (int t = 0; t < L; ++t) add_bits<NB>(c, qbits[pr[t]]);
+                }
             }
             uint32_t rmax = 0;
 #pragma unroll
