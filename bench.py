@@ -379,7 +379,7 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local_rank):
     from paper_2412_03301_gb300 import build as libbuild
     libbuild.build()
-    from paper_2412_03301_gb300 import bvss, datagen
+    from paper_2412_03301_gb300 import bvss, datagen, shard
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     c = workload_cfg(args.workload, args.queries)
@@ -387,12 +387,9 @@ def run_ours(args, rank, world, local_rank):
     w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
                          d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],
                          q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
-                         seed=args.seed + 0 * rank, device=dev)
-    if rank > 0:   # each rank answers its own query sets against the same database
-        qs = datagen.set_sizes(c["n_queries"], c["q_lo"], c["q_hi"], 1000 * (args.seed + rank) + 12)
-        mix = datagen.Mixture(c["d"], c["n_components"], args.seed, device=dev)
-        w["q_vectors"] = mix.draw_sets(qs, 1000 * (args.seed + rank) + 22)
-        w["q_offsets"] = datagen.offsets_from_sizes(qs)
+                         seed=args.seed, device=dev)
+    # each rank answers its own query sets against the same database
+    w["q_vectors"], w["q_offsets"] = shard.replica_queries(w, c, args.seed, rank, device=dev)
     off = w["offsets"]
     t0 = time.perf_counter()
     ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=c["d"] % 64 == 0)
@@ -489,10 +486,7 @@ def run_ours(args, rank, world, local_rank):
         st_ms, nb, nl = bvss.bvss_profile_read(ix, reset=True)
         bvss.bvss_profile_enable(ix, False)
         bvss.bvss_sync(ix, stream)
-        if world > 1:
-            t = torch.tensor([t_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_ms = float(t.item())
+        t_ms = shard.max_over_ranks(t_ms, device=dev)
         return t_ms, st_ms, nb, nl, clk
 
     ms_plain, stage_plain, _, _, _ = timed(kw, False)
@@ -544,10 +538,7 @@ def run_ours(args, rank, world, local_rank):
         bvss.bvss_query(ix, hq, qoff, out_ids=hi, out_dist=hd, stream=stream, **kw_fast)
     torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, device=dev)
     assert torch.equal(hi, ids_ref.cpu())
     h2d = hq.numel() * 4 + (nq + 1) * 8
     d2h = hi.numel() * 8 + hd.numel() * 4
