@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--alg2-queries", type=int, default=100,
                     help="query sets for the plain BioVSS search (Alg. 2) line; 0 skips it")
+    ap.add_argument("--serving-queries", type=int, default=4096,
+                    help="query sets per pass of the batched serving line (200k Zipf-sized "
+                         "sets, d=768, one graph launch per pass); 0 skips it")
     ap.add_argument("--cpu-sample-sets", type=int, default=2000)
     ap.add_argument("--cpu-sample-queries", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
@@ -194,6 +197,90 @@ def true_d2_of(vec, vnorm, qvec, qoff, offsets, qids, ids):
             D = qn[:, None] + vnorm[None, r0:r1] - 2 * Q @ vec[r0:r1].T
             D.clamp_(min=0)
             out[j, c] = float(torch.maximum(D.min(1).values.max(), D.min(0).values.max()))
+    return out
+
+
+# --------------------------------------------------------------------------
+# batched serving line: a query plan (one CUDA graph launch per pass)
+# --------------------------------------------------------------------------
+def serving_line(args, dev, stream):
+    """The serving load (datagen.SERVING): 200k sets of Zipf sizes 1-128, d = 768, a pass of
+    uneven query sets of 1-64 vectors run as one graph launch of a tuned plan."""
+    from paper_2412_03301_gb300 import bvss, datagen
+    c = dict(datagen.SERVING)
+    c["A"], c["M"] = 3, 1
+    nq = args.serving_queries
+    w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
+                         d=c["d"], n_components=c["n_components"], n_queries=nq,
+                         q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
+                         seed=args.seed + 7, device=dev, size_dist="zipf")
+    off, qv, qo = w["offsets"], w["q_vectors"], w["q_offsets"]
+    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=True)
+    kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"], fast=True)
+    plan = bvss.Plan(ix, nq, int(qo[-1]), c["q_hi"], stream=stream, **kw)
+    plan.set_queries(qv, qo, stream=stream)
+
+    def time_plan(steps):
+        for _ in range(args.warmup):
+            plan.launch(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    ms_default = time_plan(max(2, args.steps // 4))
+    knobs_default = plan.info()
+    t0 = time.perf_counter()
+    plan.tune(reps=2, stream=stream)
+    tune_s = time.perf_counter() - t0
+    ms = time_plan(args.steps)
+    bvss.bvss_sync(ix, stream)
+    ids_plan = plan.ids.clone()
+    # the same pass through bvss_query (host offsets, no graph), for comparison and parity
+    ids_q, _ = bvss.bvss_query(ix, qv, qo, stream=stream, **kw)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(max(2, args.steps // 4)):
+        bvss.bvss_query(ix, qv, qo, out_ids=ids_q, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_query = e0.elapsed_time(e1) / max(2, args.steps // 4)
+    rec = None
+    if args.recall_queries > 0:
+        vec = w["vectors"]
+        vnorm = (vec * vec).sum(1)
+        set_of_row = torch.repeat_interleave(torch.arange(c["n_sets"], device=dev),
+                                             torch.from_numpy(np.diff(off)).to(dev))
+        qids = list(range(min(50, nq)))
+        gt_ids, gt_d2 = exact_topk(vec, vnorm, set_of_row, c["n_sets"], qv, qo, qids, c["k"])
+        got = ids_plan[qids].cpu().numpy()
+        got_d2 = true_d2_of(vec, vnorm, qv, qo, off, qids, got)
+        rs, rt = recall_at_k(got, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(), got_d2, c["k"])
+        rec = {"recall_at_10": rs, "recall_at_10_ties": rt, "queries": len(qids)}
+    nv = int(off[-1])
+    out = {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "query_sets": nq,
+           "query_vectors": int(qo[-1]),
+           "workload": "N=%d sets, Zipf sizes %d-%d (%d vectors), d=%d (BF16-exact grid values), "
+                       "%d-component mixture; FlyHash m=%d F=%d L=%d; %d query sets of %d-%d "
+                       "vectors; A=%d M=%d C=%d k=%d"
+                       % (c["n_sets"], c["size_lo"], c["size_hi"], nv, c["d"],
+                          c["n_components"], c["m"], c["fanin"], c["L"], nq, c["q_lo"],
+                          c["q_hi"], c["A"], c["M"], c["C"], c["k"]),
+           "form": "one CUDA graph launch per pass (bvss_plan), tensor-core scan and BF16 "
+                   "tensor-core refine (64-wide), FP32 re-score of the critical pair",
+           "tuned": plan.info(), "untuned": dict(knobs_default, ms_per_step=ms_default),
+           "tune_s": tune_s,
+           "bvss_query_ms_per_step": ms_query, "same_ids_as_bvss_query": bool(torch.equal(ids_plan, ids_q)),
+           "recall": rec,
+           "l2": "vectors %.1f GB BF16 + %.1f GB FP32; the %.0f MB sketch matrix is evicted by "
+                 "each pass's refine traffic" % (nv * c["d"] * 2 / 1e9, nv * c["d"] * 4 / 1e9,
+                                                 c["n_sets"] * c["m"] / 8 / 1e6)}
+    plan.close()
+    ix.close()
     return out
 
 
@@ -559,6 +646,10 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
     roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok)
+    ix.close()
+    torch.cuda.empty_cache()
+    serving = (serving_line(args, dev, stream)
+               if args.serving_queries > 0 and args.workload == "large" else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -582,6 +673,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "alg2": alg2,
+        "serving": serving,
         "clocks": clk,
         "build_s": build_s,
         "work": {"gated_pairs_per_step": gated_pairs, "candidates_per_step": sum_cand,

@@ -209,6 +209,56 @@ int bvss_sync(bvss_index *ix, void *stream);
  * the CUDA context still usable.  Synchronises the device; allocates 4 bytes. */
 int bvss_selftest_wait_timeout(int64_t limit_ns);
 
+/*
+ * Query plans: the batched serving form.  A plan fixes the shape of a query
+ * pass -- n_queries query sets with at most max_vectors vectors in all and at
+ * most max_qset per set -- and binds it to the caller's device buffers:
+ *   q_vectors  max_vectors x d FP32 (query vectors, set-contiguous),
+ *   q_offsets  n_queries + 1 int64, q_offsets[0] = 0 (CSR over q_vectors),
+ *   out_ids    n_queries x k int64, out_dist n_queries x k FP32 (as bvss_query).
+ * The whole pass (an on-device check of the offsets, the FlyHash of every
+ * query vector, then Alg. 6 -- or Alg. 2 with BVSS_SEARCH_ALG2 -- for
+ * batches of query sets of uneven sizes) is captured once into a CUDA graph
+ * and replayed by bvss_plan_launch, one graph launch per pass, with no host
+ * work, no allocation and no synchronisation.  Between launches the caller
+ * may rewrite the buffers' contents (new query sets, other sizes within the
+ * bounds), but not move them.  Results equal bvss_query's on the same input.
+ *
+ * Offsets are read on the device.  When they break the bounds (a set empty or
+ * larger than max_qset, more than max_vectors vectors, q_offsets[0] != 0),
+ * the pass runs on one-vector placeholder sets instead, its results are not
+ * valid, and the next bvss_sync on the index returns BVSS_EINVAL.
+ *
+ * The plan owns its workspace (about that of a bvss_query call of the same
+ * shape).  It must be freed before its index, after the streams it was
+ * launched on have been synchronised.  bvss_plan_create synchronises
+ * `stream` and returns EINVAL for out-of-range shapes or search parameters
+ * (as bvss_query), or for host buffers.
+ */
+typedef struct bvss_plan bvss_plan;
+
+int bvss_plan_create(bvss_index *ix, const bvss_search *s, int64_t n_queries,
+                     int64_t max_vectors, int32_t max_qset, const float *q_vectors,
+                     const int64_t *q_offsets, int64_t *out_ids, float *out_dist, void *stream,
+                     bvss_plan **out);
+/* One pass: one graph launch on `stream` (asynchronous). */
+int bvss_plan_launch(bvss_plan *p, void *stream);
+/* Autotuner: times the pass on the buffers' current contents (reps launches
+ * after one warm-up per setting) while varying one choice at a time -- the
+ * sketch scan (tensor-core or popcount), the tensor-core refine's candidates
+ * per CTA (128, 256, 512) and its copy lag (4 or 5 stages, as the ring
+ * allows) -- keeps the fastest setting and re-captures the graph with it.
+ * Every setting gives the same results.  Synchronises `stream` first and
+ * runs on the plan's own stream; *best_ms (may be NULL) = the chosen pass's
+ * time in milliseconds. */
+int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms);
+/* knobs (host, 4 entries, may be NULL): {scan (1 tensor-core, 2 popcount, 0
+ * Alg. 2's own), refine candidates per CTA (0 if the FP32 refine runs),
+ * refine copy lag, refine query-set width (32 or 64)}; *launches = kernels per
+ * pass. */
+int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches);
+void bvss_plan_free(bvss_plan *p);
+
 /* Stages of bvss_query timed by the profiler (CUDA events on the query
  * stream, recorded between the kernels of every batch). */
 #define BVSS_STAGE_ENCODE 0   /* FlyHash of the query vectors + C_Q, S_Q, P (Alg. 6 lines 1-4) */

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 import torch
@@ -70,6 +71,12 @@ SYMBOLS = {
                                            _vp, _vp]),
     "bvss_sync": (ctypes.c_int, [_vp, _vp]),
     "bvss_selftest_wait_timeout": (ctypes.c_int, [_c_i64]),
+    "bvss_plan_create": (ctypes.c_int, [_vp, ctypes.POINTER(bvss_search), _c_i64, _c_i64,
+                                        _c_i32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "bvss_plan_launch": (ctypes.c_int, [_vp, _vp]),
+    "bvss_plan_tune": (ctypes.c_int, [_vp, _c_i32, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "bvss_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i64)]),
+    "bvss_plan_free": (None, [_vp]),
     "bvss_free": (None, [_vp]),
     "bvss_last_error": (ctypes.c_char_p, []),
 }
@@ -127,6 +134,7 @@ class Index:
         self.n_sets = n_sets
         self.n_vectors = n_vectors
         self.device = device
+        self._plans = weakref.WeakSet()   # plans are freed before their index
 
     @property
     def d(self):
@@ -142,6 +150,8 @@ class Index:
 
     def close(self):
         if self.handle:
+            for p in list(self._plans):
+                p.close()
             torch.cuda.synchronize(self.device)
             load().bvss_free(self.handle)
             self.handle = None
@@ -195,6 +205,79 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
+
+
+class Plan:
+    """A graph-captured query pass over fixed device buffers (bvss_plan_*).
+
+    The plan allocates its buffers: ``q_vectors`` (max_vectors, d) float32,
+    ``q_offsets`` (n_queries + 1,) int64, ``ids`` (n_queries, k) int64 and
+    ``dist`` (n_queries, k) float32, all on the index's GPU.  Write a batch
+    into the first two (``set_queries``), call ``launch`` and read the last two.
+    """
+
+    def __init__(self, ix: Index, n_queries: int, max_vectors: int, max_qset: int, *, k: int,
+                 C: int, A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
+                 alg2: bool = False, stream=None):
+        lib = load()
+        dev = ix.device
+        self.ix = ix
+        self.n_queries, self.max_vectors, self.max_qset = n_queries, max_vectors, max_qset
+        self.q_vectors = torch.zeros((max_vectors, ix.d), dtype=torch.float32, device=dev)
+        self.q_offsets = torch.arange(n_queries + 1, dtype=torch.int64, device=dev)
+        self.ids = torch.empty((n_queries, k), dtype=torch.int64, device=dev)
+        self.dist = torch.empty((n_queries, k), dtype=torch.float32, device=dev)
+        s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.bvss_plan_create(ix.handle, ctypes.byref(s), n_queries, max_vectors,
+                                        max_qset, _dptr(self.q_vectors), _dptr(self.q_offsets),
+                                        _dptr(self.ids), _dptr(self.dist), _stream(stream),
+                                        ctypes.byref(h)))
+        self.handle = h
+        ix._plans.add(self)
+
+    def set_queries(self, q_vectors: torch.Tensor, q_offsets, stream=None):
+        """Copy a batch (vectors on any device, offsets host or device) into the buffers."""
+        n = q_vectors.shape[0]
+        if n > self.max_vectors:
+            raise ValueError("batch has %d vectors, the plan holds %d" % (n, self.max_vectors))
+        off = torch.as_tensor(np.asarray(q_offsets) if not torch.is_tensor(q_offsets)
+                              else q_offsets, dtype=torch.int64)
+        if off.shape[0] != self.n_queries + 1:
+            raise ValueError("the plan takes %d query sets" % self.n_queries)
+        st = torch.cuda.current_stream(self.ix.device) if stream is None else stream
+        with torch.cuda.stream(st):
+            self.q_vectors[:n].copy_(q_vectors, non_blocking=True)
+            self.q_offsets.copy_(off, non_blocking=True)
+
+    def launch(self, stream=None):
+        _check(load().bvss_plan_launch(self.handle, _stream(stream)))
+        return self.ids, self.dist
+
+    def tune(self, reps: int = 3, stream=None) -> float:
+        ms = ctypes.c_float()
+        _check(load().bvss_plan_tune(self.handle, reps, _stream(stream), ctypes.byref(ms)))
+        return ms.value
+
+    def info(self):
+        kn = (_c_i32 * 4)()
+        nl = _c_i64()
+        _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
+        return dict(scan={1: "tensor", 2: "popcount", 0: "alg2"}[kn[0]], cand_cta=kn[1],
+                    lag=kn[2], mq=kn[3], launches=nl.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.ix.device)
+            load().bvss_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,

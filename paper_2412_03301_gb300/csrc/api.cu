@@ -58,6 +58,9 @@ void dfree(T *&p) {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// device status bit of a plan whose query offsets failed the on-device check
+constexpr int kErrPlanInput = 8;
+
 // h rows are padded to 64 entries so every row starts 128-byte aligned
 int64_t h_stride(const bvss_index *ix) { return round_up(ix->n_sets, 64); }
 
@@ -165,6 +168,9 @@ int get_plane(bvss_index *ix, int M, cudaStream_t st, const uint32_t **out) {
         }
     int slot = ix->n_planes;
     if (slot == kMaxPlanes) {
+        if (ix->n_plans > 0)
+            return fail(BVSS_EINVAL, "%d gate planes are cached and live plans use them; free "
+                                     "the plans to search with another M", kMaxPlanes);
         slot = kMaxPlanes - 1;   // replace the most recent extra plane
         BVSS_CU(cudaStreamSynchronize(st));
         dfree(ix->planes[slot].words);
@@ -180,12 +186,42 @@ int get_plane(bvss_index *ix, int M, cudaStream_t st, const uint32_t **out) {
     return BVSS_OK;
 }
 
-int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int k,
-                     bool need_qvec, bool need_out) {
-    Workspace &w = ix->ws;
+// allocate a workspace for batches of nq query sets with nvq vectors in all
+int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq, int C, int A,
+                    int k, bool need_qvec, bool need_out) {
     const int m = ix->p.m, W = ix->W, L = ix->p.wta_l, d = ix->p.d;
     const int64_t hs = h_stride(ix);
     const int n_chunks = (int)((ix->n_sets + kSelChunk - 1) / kSelChunk);
+    BVSS_CU(dalloc(&w.qoff, nq + 1));
+    BVSS_CU(dalloc(&w.qpos, (size_t)nvq * L));
+    BVSS_CU(dalloc(&w.sq, (size_t)nq * W));
+    BVSS_CU(dalloc(&w.plist, (size_t)nq * A));
+    BVSS_CU(dalloc(&w.h, (size_t)nq * hs));
+    BVSS_CU(dalloc(&w.gate, (size_t)nq * ix->NW));
+    BVSS_CU(dalloc(&w.q8, scan_mma_q8_bytes(nq, m)));
+    BVSS_CU(dalloc(&w.qpop, (size_t)round_up(nq, 256)));
+    BVSS_CU(dalloc(&w.hist, (size_t)nq * ((m > 2 * L ? m : 2 * L) + 1)));
+    BVSS_CU(dalloc(&w.thr, (size_t)nq * 4));
+    BVSS_CU(dalloc(&w.chunk, (size_t)nq * n_chunks * kSelRangeWords));
+    BVSS_CU(dalloc(&w.cand, (size_t)nq * C));
+    BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
+    BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
+    if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
+    if (need_out) {
+        BVSS_CU(dalloc(&w.out_ids, (size_t)nq * k));
+        BVSS_CU(dalloc(&w.out_dist, (size_t)nq * k));
+    }
+    w.cap_q = nq;
+    w.cap_vq = nvq;
+    w.cap_C = C;
+    w.cap_A = A;
+    w.cap_k = k;
+    return BVSS_OK;
+}
+
+int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int k,
+                     bool need_qvec, bool need_out) {
+    Workspace &w = ix->ws;
     if (nq > w.cap_q || nvq > w.cap_vq || C > w.cap_C || A > w.cap_A || k > w.cap_k ||
         (need_qvec && !w.qvec) || (need_out && !w.out_ids)) {
         const int64_t cq = nq > w.cap_q ? nq : w.cap_q;
@@ -196,30 +232,12 @@ int ensure_workspace(bvss_index *ix, int64_t nq, int64_t nvq, int C, int A, int 
         const bool had_qvec = w.qvec != nullptr, had_out = w.out_ids != nullptr;
         BVSS_CU(cudaDeviceSynchronize());
         free_workspace(w);
-        BVSS_CU(dalloc(&w.qoff, cq + 1));
-        BVSS_CU(dalloc(&w.qpos, (size_t)cvq * L));
-        BVSS_CU(dalloc(&w.sq, (size_t)cq * W));
-        BVSS_CU(dalloc(&w.plist, (size_t)cq * cA));
-        BVSS_CU(dalloc(&w.h, (size_t)cq * hs));
-        BVSS_CU(dalloc(&w.gate, (size_t)cq * ix->NW));
-        BVSS_CU(dalloc(&w.q8, scan_mma_q8_bytes(cq, m)));
-        BVSS_CU(dalloc(&w.qpop, (size_t)round_up(cq, 256)));
-        BVSS_CU(dalloc(&w.hist, (size_t)cq * ((m > 2 * L ? m : 2 * L) + 1)));
-        BVSS_CU(dalloc(&w.thr, (size_t)cq * 4));
-        BVSS_CU(dalloc(&w.chunk, (size_t)cq * n_chunks * kSelRangeWords));
-        BVSS_CU(dalloc(&w.cand, (size_t)cq * cC));
-        BVSS_CU(dalloc(&w.cand_dist, (size_t)cq * cC));
-        BVSS_CU(dalloc(&w.pair, (size_t)cq * cC));
-        if (need_qvec || had_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)cvq * d));
-        if (need_out || had_out) {
-            BVSS_CU(dalloc(&w.out_ids, (size_t)cq * ck));
-            BVSS_CU(dalloc(&w.out_dist, (size_t)cq * ck));
+        const int rc = alloc_workspace(ix, w, cq, cvq, cC, cA, ck, need_qvec || had_qvec,
+                                       need_out || had_out);
+        if (rc) {
+            free_workspace(w);
+            return rc;
         }
-        w.cap_q = cq;
-        w.cap_vq = cvq;
-        w.cap_C = cC;
-        w.cap_A = cA;
-        w.cap_k = ck;
     }
     // pinned staging ring for the per-batch query offsets
     for (int i = 0; i < kOffRing; ++i) {
@@ -244,6 +262,9 @@ int sync_and_check(bvss_index *ix, cudaStream_t st) {
     BVSS_CU(cudaMemcpy(&e, ix->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         BVSS_CU(cudaMemset(ix->err, 0, sizeof(int)));
+        if (e == kErrPlanInput)
+            return fail(BVSS_EINVAL, "a plan's query offsets were out of range; its results "
+                                     "are not valid");
         return fail(BVSS_ETIMEOUT, "a kernel's bounded wait gave up (device status %d)", e);
     }
     return BVSS_OK;
@@ -271,12 +292,17 @@ cudaEvent_t *prof_reserve(bvss_index *ix) {
     return base;
 }
 
-int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
-               int64_t n_queries, const bvss_search *s, int64_t *out_ids, float *out_dist,
-               const bvss_trace *tr, void *stream) {
-    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+// Kernel and tile choices of one query pass.  Zero fields take the built-in
+// heuristics; a plan's autotuner sets them to the fastest measured choice.
+struct Knobs {
+    int scan = 0;       // 1: tensor-core sketch scan, 2: popcount scan, 0: by the search flags
+    int cand_cta = 0;   // tensor-core refine: candidates per CTA (0: 512)
+    int lag = 0;        // tensor-core refine: stages of copies in flight (0: by the ring depth)
+};
+
+int check_search(const bvss_index *ix, const bvss_search *s) {
     if (!s) return fail(BVSS_EINVAL, "search parameters are NULL");
-    const int L = ix->p.wta_l, m = ix->p.m, d = ix->p.d, W = ix->W;
+    const int L = ix->p.wta_l;
     if (s->k < 1) return fail(BVSS_EINVAL, "k = %d: need k >= 1", s->k);
     if (s->C < s->k || s->C > BVSS_MAX_C)
         return fail(BVSS_EINVAL, "C = %d: need k <= C <= %d", s->C, BVSS_MAX_C);
@@ -285,17 +311,119 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
     if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2))
         return fail(BVSS_EINVAL, "unknown search flags");
+    if ((s->flags & BVSS_SEARCH_FAST) && !ix->vec16)
+        return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
+    return BVSS_OK;
+}
+
+// Everything a query batch needs besides the index, for enqueue_batch.
+struct Batch {
+    const float *qv = nullptr;       // query vectors (device)
+    const int64_t *qoff = nullptr;   // nb + 1 offsets into qv and qpos (device)
+    int nb = 0;                      // query sets
+    int max_mq = 0;                  // bound on the vectors of one query set
+    int64_t enc_n = 0;               // > 0: encode qv[0, enc_n) into w.qpos first
+    const int64_t *enc_n_dev = nullptr;   // with enc_n: the count, read on the device
+    const uint32_t *plane = nullptr;      // layer-1 plane for M (gate mode 1)
+    int64_t *ids = nullptr;          // nb x k results (device)
+    float *dist = nullptr;
+    int32_t *cq_trace = nullptr;
+    cudaEvent_t *ev = nullptr;       // kProfEvents stage events, or null
+};
+
+// Alg. 6 (or Alg. 2) for one batch, enqueued on st: no host synchronisation and no
+// allocation, so a stream capture of it is a valid CUDA graph.  Counts the launches.
+int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knobs &kn,
+                  const Batch &b, int64_t *launches, cudaStream_t st) {
+    const int L = ix->p.wta_l, m = ix->p.m, d = ix->p.d, W = ix->W;
+    const int k = s->k, C = s->C, A = s->A, M = s->M, nb = b.nb;
     const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
     const bool fast = (s->flags & BVSS_SEARCH_FAST) != 0;
-    const bool tensor_scan = (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
-    if (fast && !ix->vec16)
-        return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
+    const bool tensor_scan =
+        kn.scan ? kn.scan == 1 : (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
+    const int gate_mode = M == 0 ? 0 : (M > 255 ? 2 : 1);
+    const int64_t hs = h_stride(ix);
+    cudaEvent_t *ev = b.ev;
+    const float *qv = b.qv;
+    int64_t n = 0;
+    if (ev) BVSS_CU(cudaEventRecord(ev[0], st));
+    // Alg. 6 lines 1-4 (Alg. 2 lines 2-5: the codes only)
+    if (b.enc_n > 0) {
+        BVSS_CU(launch_encode(qv, b.enc_n, d, ix->proj, m, ix->p.fanin, L, w.qpos, nullptr, st,
+                              b.enc_n_dev));
+        ++n;
+    }
+    if (!alg2) {
+        BVSS_CU(launch_query_prep(w.qpos, b.qoff, nb, m, L, A, w.sq, w.plist, b.cq_trace, st));
+        ++n;
+    }
+    if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
+    // lines 5-9: layer-1 words per 32 sets (and the FP8 query operand)
+    if (!alg2 && gate_mode == 1) {
+        BVSS_CU(launch_gate(b.plane, ix->NW, w.plist, A, nb, w.gate, st));
+        ++n;
+    }
+    if (!alg2 && tensor_scan) {
+        BVSS_CU(launch_expand_q(w.sq, nb, W, w.q8, w.qpop, st));
+        ++n;
+    }
+    if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
+    // line 12 (Alg. 2 lines 6-8: Haus^H against every set)
+    if (alg2)
+        BVSS_CU(launch_haus_h(w.qpos, b.qoff, nb, ix->codes, ix->set_off, ix->n_sets, m, L, w.h,
+                              hs, st));
+    else if (tensor_scan)
+        BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
+                                w.q8, w.qpop, nb, w.h, hs, ix->err, st));
+    else
+        BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, w.gate, ix->NW, gate_mode, w.sq, nb, w.h,
+                            hs, st));
+    ++n;
+    if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
+    // lines 10-18 (Alg. 2 line 9); scores run up to m (Hamming of sketches) or 2L (Haus^H)
+    BVSS_CU(launch_select(w.h, ix->n_sets, hs, alg2 ? 2 * L : m, nb, C, w.hist, w.thr, w.chunk,
+                          w.cand, st));
+    n += kSelectKernels;
+    if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
+    // lines 19-23
+    const bool mma = fast && refine_mma_supported(d, b.max_mq);
+    if (mma)
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, ix->vec16, ix->vnorm16, ix->set_off,
+                                  d, w.cand, w.thr, C, w.pair, ix->err, st, kn.cand_cta, kn.lag));
+    else if (refine_tma_supported(d, b.max_mq))
+        BVSS_CU(launch_refine_tma(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
+                                  w.cand, w.thr, C, w.cand_dist, ix->err, st));
+    else
+        BVSS_CU(launch_refine(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
+                              w.cand, w.thr, C, w.cand_dist, st));
+    ++n;
+    if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
+    if (mma) {
+        BVSS_CU(launch_rescore(qv, b.qoff, nb, ix->vec, ix->set_off, d, w.cand, w.thr, C, w.pair,
+                               w.cand_dist, st));
+        ++n;
+    }
+    if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
+    BVSS_CU(launch_topk(w.cand, w.cand_dist, w.thr, nb, C, k, b.ids, b.dist, st));
+    ++n;
+    *launches += n;
+    return BVSS_OK;
+}
+
+int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+               int64_t n_queries, const bvss_search *s, int64_t *out_ids, float *out_dist,
+               const bvss_trace *tr, void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    int rc = check_search(ix, s);
+    if (rc) return rc;
+    const int L = ix->p.wta_l, d = ix->p.d, W = ix->W;
+    const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
     if (n_queries < 0) return fail(BVSS_EINVAL, "n_queries < 0");
     if (n_queries == 0) return BVSS_OK;
     if (!q_vectors || !out_ids || !out_dist)
         return fail(BVSS_EINVAL, "query vectors or outputs are NULL");
     // Alg. 2's scoring kernel holds one bit per query vector in a 32-bit word
-    int rc = check_offsets(q_offsets, n_queries, alg2 ? 32 : BVSS_MAX_QSET, "query");
+    rc = check_offsets(q_offsets, n_queries, alg2 ? 32 : BVSS_MAX_QSET, "query");
     if (rc) return rc;
     rc = check_device(ix);
     if (rc) return rc;
@@ -321,9 +449,8 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     if (rc) return rc;
     Workspace &w = ix->ws;
 
-    const int gate_mode = M == 0 ? 0 : (M > 255 ? 2 : 1);
     const uint32_t *plane = nullptr;
-    if (gate_mode == 1) {
+    if (M >= 1 && M <= 255) {
         rc = get_plane(ix, M, st, &plane);
         if (rc) return rc;
     }
@@ -347,78 +474,32 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
                                 cudaMemcpyHostToDevice, st));
         BVSS_CU(cudaEventRecord(ix->off_event[slot], st));
         cudaEvent_t *ev = ix->prof_on ? prof_reserve(ix) : nullptr;
-        if (ev) BVSS_CU(cudaEventRecord(ev[0], st));
         const float *qv = q_vectors + v0 * d;
         if (!qv_dev) {
             BVSS_CU(cudaMemcpyAsync(w.qvec, qv, sizeof(float) * (size_t)nv * d,
                                     cudaMemcpyHostToDevice, st));
             qv = w.qvec;
         }
-        // Alg. 6 lines 1-4 (Alg. 2 lines 2-5: the codes only)
-        BVSS_CU(launch_encode(qv, nv, d, ix->proj, m, ix->p.fanin, L, w.qpos, nullptr, st));
-        int64_t launches = 1;
-        if (!alg2) {
-            BVSS_CU(launch_query_prep(w.qpos, w.qoff, nb, m, L, A, w.sq, w.plist,
-                                      tr && tr->cq ? tr->cq + b0 * m : nullptr, st));
-            ++launches;
-        }
-        if (ev) BVSS_CU(cudaEventRecord(ev[1], st));
-        // lines 5-9: layer-1 words per 32 sets (and the FP8 query operand)
-        if (!alg2 && gate_mode == 1) {
-            BVSS_CU(launch_gate(plane, ix->NW, w.plist, A, nb, w.gate, st));
-            ++launches;
-        }
-        if (!alg2 && tensor_scan) {
-            BVSS_CU(launch_expand_q(w.sq, nb, W, w.q8, w.qpop, st));
-            ++launches;
-        }
-        if (ev) BVSS_CU(cudaEventRecord(ev[2], st));
-        // line 12 (Alg. 2 lines 6-8: Haus^H against every set)
-        if (alg2)
-            BVSS_CU(launch_haus_h(w.qpos, w.qoff, nb, ix->codes, ix->set_off, ix->n_sets, m, L,
-                                  w.h, hs, st));
-        else if (tensor_scan)
-            BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
-                                    w.q8, w.qpop, nb, w.h, hs, ix->err, st));
-        else
-            BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, w.gate, ix->NW, gate_mode, w.sq, nb, w.h,
-                                hs, st));
-        ++launches;
-        if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
-        // lines 10-18 (Alg. 2 line 9); scores run up to m (Hamming of sketches) or 2L (Haus^H)
-        BVSS_CU(launch_select(w.h, ix->n_sets, hs, alg2 ? 2 * L : m, nb, C, w.hist, w.thr, w.chunk,
-                              w.cand, st));
-        launches += kSelectKernels;
-        if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
-        // lines 19-23
-        const bool mma = fast && refine_mma_supported(d, max_mq);
-        if (mma)
-            BVSS_CU(launch_refine_mma(qv, w.qoff, nb, ix->vec16, ix->vnorm16, ix->set_off, d, w.cand,
-                                      w.thr, C, w.pair, ix->err, st));
-        else if (refine_tma_supported(d, max_mq))
-            BVSS_CU(launch_refine_tma(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off,
-                                      d, w.cand, w.thr, C, w.cand_dist, ix->err, st));
-        else
-            BVSS_CU(launch_refine(qv, w.qoff, nb, max_mq, ix->vec, ix->vnorm, ix->set_off, d,
-                                  w.cand, w.thr, C, w.cand_dist, st));
-        ++launches;
-        if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
-        if (mma) {
-            BVSS_CU(launch_rescore(qv, w.qoff, nb, ix->vec, ix->set_off, d, w.cand, w.thr, C, w.pair,
-                                   w.cand_dist, st));
-            ++launches;
-        }
-        if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
-        int64_t *ids = ids_dev ? out_ids + b0 * k : w.out_ids;
-        float *dist = dist_dev ? out_dist + b0 * k : w.out_dist;
-        BVSS_CU(launch_topk(w.cand, w.cand_dist, w.thr, nb, C, k, ids, dist, st));
-        ++launches;
+        Batch b;
+        b.qv = qv;
+        b.qoff = w.qoff;
+        b.nb = nb;
+        b.max_mq = max_mq;
+        b.enc_n = nv;
+        b.plane = plane;
+        b.ids = ids_dev ? out_ids + b0 * k : w.out_ids;
+        b.dist = dist_dev ? out_dist + b0 * k : w.out_dist;
+        b.cq_trace = tr && tr->cq ? tr->cq + b0 * ix->p.m : nullptr;
+        b.ev = ev;
+        int64_t launches = 0;
+        rc = enqueue_batch(ix, w, s, Knobs(), b, &launches, st);
+        if (rc) return rc;
         if (ev) ix->prof_launches += launches;
         if (!ids_dev)
-            BVSS_CU(cudaMemcpyAsync(out_ids + b0 * k, ids, sizeof(int64_t) * (size_t)nb * k,
+            BVSS_CU(cudaMemcpyAsync(out_ids + b0 * k, b.ids, sizeof(int64_t) * (size_t)nb * k,
                                     cudaMemcpyDeviceToHost, st));
         if (!dist_dev)
-            BVSS_CU(cudaMemcpyAsync(out_dist + b0 * k, dist, sizeof(float) * (size_t)nb * k,
+            BVSS_CU(cudaMemcpyAsync(out_dist + b0 * k, b.dist, sizeof(float) * (size_t)nb * k,
                                     cudaMemcpyDeviceToHost, st));
         if (ev) BVSS_CU(cudaEventRecord(ev[7], st));
         if (tr) {
@@ -445,6 +526,127 @@ int query_impl(bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
     }
     if (!ids_dev || !dist_dev) return sync_and_check(ix, st);
     return BVSS_OK;
+}
+
+// The query offsets of a plan live on the device, so they are checked there: offsets
+// from 0, every set 1..max_qset vectors, at most max_v vectors in all.  Valid offsets
+// are copied into the plan's array; otherwise status bit kErrPlanInput is set and the
+// array is filled with one-vector sets (j), which keeps every kernel of the pass inside
+// the plan's buffers (n_q <= max_v).
+__global__ void __launch_bounds__(1024)
+k_plan_offsets(const int64_t *__restrict__ in, int64_t n_q, int max_qset, int64_t max_v,
+               int64_t *__restrict__ out, int *__restrict__ err) {
+    bool bad = false;
+    for (int64_t j = threadIdx.x; j < n_q; j += blockDim.x) {
+        const int64_t sz = in[j + 1] - in[j];
+        bad |= sz < 1 || sz > max_qset;
+    }
+    if (threadIdx.x == 0) bad |= in[0] != 0 || in[n_q] > max_v;
+    bad = __syncthreads_or(bad);
+    for (int64_t j = threadIdx.x; j <= n_q; j += blockDim.x) out[j] = bad ? j : in[j];
+    if (bad && threadIdx.x == 0) atomicOr(err, kErrPlanInput);
+}
+
+}  // namespace
+
+// A fixed-shape query pass bound to the caller's device buffers and captured into one
+// CUDA graph: the offsets check, the FlyHash of every query vector, then Alg. 6 (or
+// Alg. 2) batch by batch, with its own workspace so the graph's pointers stay valid.
+struct bvss_plan {
+    bvss_index *ix = nullptr;
+    bvss_search s{};
+    int64_t n_q = 0, max_v = 0;
+    int max_qset = 0;
+    const float *qv = nullptr;
+    const int64_t *qoff_in = nullptr;
+    int64_t *ids = nullptr;
+    float *dist = nullptr;
+    Workspace w;
+    int64_t *qoff = nullptr;   // checked offsets, n_q + 1
+    const uint32_t *plane = nullptr;
+    Knobs kn;
+    cudaStream_t cs = nullptr;   // capture and tuning stream
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;        // kernels per pass
+};
+
+namespace {
+
+void free_plan(bvss_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->cs) cudaStreamDestroy(p->cs);
+    free_workspace(p->w);
+    dfree(p->qoff);
+    delete p;
+}
+
+int plan_enqueue(bvss_plan *p, cudaStream_t st, int64_t *launches) {
+    bvss_index *ix = p->ix;
+    const int k = p->s.k;
+    k_plan_offsets<<<1, 1024, 0, st>>>(p->qoff_in, p->n_q, p->max_qset, p->max_v, p->qoff,
+                                       ix->err);
+    BVSS_CU(cudaGetLastError());
+    BVSS_CU(launch_encode(p->qv, p->max_v, ix->p.d, ix->proj, ix->p.m, ix->p.fanin,
+                          ix->p.wta_l, p->w.qpos, nullptr, st, p->qoff + p->n_q));
+    *launches = 2;
+    const int64_t QB = p->w.cap_q;
+    for (int64_t b0 = 0; b0 < p->n_q; b0 += QB) {
+        Batch b;
+        b.qv = p->qv;
+        b.qoff = p->qoff + b0;
+        b.nb = (int)(b0 + QB < p->n_q ? QB : p->n_q - b0);
+        b.max_mq = p->max_qset;
+        b.plane = p->plane;
+        b.ids = p->ids + b0 * k;
+        b.dist = p->dist + b0 * k;
+        const int rc = enqueue_batch(ix, p->w, &p->s, p->kn, b, launches, st);
+        if (rc) return rc;
+    }
+    return BVSS_OK;
+}
+
+// (re)capture the pass with the current knobs into the plan's graph
+int plan_capture(bvss_plan *p) {
+    BVSS_CU(cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeThreadLocal));
+    int64_t launches = 0;
+    const int rc = plan_enqueue(p, p->cs, &launches);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cs, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    BVSS_CU(e);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    BVSS_CU(ei);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    p->exec = ex;
+    p->launches = launches;
+    return BVSS_OK;
+}
+
+// mean time of one graph launch (ms) with the given knobs, after one warm-up launch
+int plan_time(bvss_plan *p, const Knobs &kn, int reps, float *ms) {
+    p->kn = kn;
+    int rc = plan_capture(p);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BVSS_CU(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, p->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, p->cs);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(p->exec, p->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, p->cs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    BVSS_CU(e);
+    *ms /= (float)reps;
+    return sync_and_check(p->ix, p->cs);
 }
 
 }  // namespace
@@ -678,5 +880,147 @@ int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int6
 void bvss_free(bvss_index *ix) { free_index(ix); }
 
 const char *bvss_last_error(void) { return g_err; }
+
+int bvss_plan_create(bvss_index *ix, const bvss_search *s, int64_t n_queries,
+                     int64_t max_vectors, int32_t max_qset, const float *q_vectors,
+                     const int64_t *q_offsets, int64_t *out_ids, float *out_dist, void *stream,
+                     bvss_plan **out) {
+    if (!out) return fail(BVSS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    int rc = check_search(ix, s);
+    if (rc) return rc;
+    const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
+    const int qmax = alg2 ? 32 : BVSS_MAX_QSET;
+    if (n_queries < 1) return fail(BVSS_EINVAL, "n_queries = %lld: need >= 1", (long long)n_queries);
+    if (max_qset < 1 || max_qset > qmax)
+        return fail(BVSS_EINVAL, "max_qset = %d: need 1 <= max_qset <= %d", max_qset, qmax);
+    if (max_vectors < n_queries || max_vectors > n_queries * (int64_t)max_qset)
+        return fail(BVSS_EINVAL, "max_vectors = %lld: need n_queries <= max_vectors <= "
+                                 "n_queries * max_qset", (long long)max_vectors);
+    if (!q_vectors || !q_offsets || !out_ids || !out_dist)
+        return fail(BVSS_EINVAL, "plan buffers are NULL");
+    if (!is_device_ptr(q_vectors) || !is_device_ptr(q_offsets) || !is_device_ptr(out_ids) ||
+        !is_device_ptr(out_dist))
+        return fail(BVSS_EINVAL, "plan buffers must be device memory");
+    rc = check_device(ix);
+    if (rc) return rc;
+    bvss_plan *p = new (std::nothrow) bvss_plan();
+    if (!p) return fail(BVSS_ENOMEM, "plan allocation failed");
+    p->ix = ix;
+    p->s = *s;
+    p->n_q = n_queries;
+    p->max_v = max_vectors;
+    p->max_qset = max_qset;
+    p->qv = q_vectors;
+    p->qoff_in = q_offsets;
+    p->ids = out_ids;
+    p->dist = out_dist;
+    const int64_t QB = batch_cap(ix);
+    rc = alloc_workspace(ix, p->w, n_queries < QB ? n_queries : QB, max_vectors, s->C, s->A,
+                         s->k, false, false);
+    if (!rc && dalloc(&p->qoff, n_queries + 1) != cudaSuccess)
+        rc = fail(BVSS_ENOMEM, "plan offsets allocation failed");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!rc && s->M >= 1 && s->M <= 255) rc = get_plane(ix, s->M, st, &p->plane);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess)
+        rc = fail(BVSS_ECUDA, "stream synchronisation failed");
+    if (!rc && cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking) != cudaSuccess)
+        rc = fail(BVSS_ECUDA, "stream creation failed");
+    if (!rc) rc = plan_capture(p);
+    if (rc) {
+        free_plan(p);
+        return rc;
+    }
+    ++ix->n_plans;
+    *out = p;
+    return BVSS_OK;
+}
+
+int bvss_plan_launch(bvss_plan *p, void *stream) {
+    if (!p || !p->exec) return fail(BVSS_EINVAL, "plan is NULL");
+    BVSS_CU(cudaGraphLaunch(p->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return BVSS_OK;
+}
+
+int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
+    if (!p || !p->exec) return fail(BVSS_EINVAL, "plan is NULL");
+    if (reps < 1) return fail(BVSS_EINVAL, "reps = %d: need >= 1", reps);
+    BVSS_CU(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    const int d = p->ix->p.d;
+    const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
+    const bool mma = (p->s.flags & BVSS_SEARCH_FAST) && refine_mma_supported(d, p->max_qset);
+    const int ns = mma ? refine_mma_stages(d, p->max_qset) : 0;
+    Knobs best = p->kn;
+    float best_t = 0.0f;
+    int rc = plan_time(p, best, reps, &best_t);
+    if (rc) return rc;
+    // one knob at a time, each over its values, keeping the fastest pass
+    auto sweep = [&](int Knobs::*field, const int *vals, int nv) -> int {
+        for (int i = 0; i < nv; ++i) {
+            Knobs kn = best;
+            if (kn.*field == vals[i]) continue;
+            kn.*field = vals[i];
+            float t = 0.0f;
+            const int r = plan_time(p, kn, reps, &t);
+            if (r) return r;
+            if (t < best_t) {
+                best_t = t;
+                best = kn;
+            }
+        }
+        return BVSS_OK;
+    };
+    if (!alg2) {
+        const int scans[] = {1, 2};
+        rc = sweep(&Knobs::scan, scans, 2);
+    }
+    if (!rc && mma) {
+        const int ctas[] = {128, 256, 512};
+        rc = sweep(&Knobs::cand_cta, ctas, 3);
+    }
+    if (!rc && mma) {
+        int lags[2], nl = 0;
+        for (int l = 4; l <= 5; ++l)
+            if (l < ns) lags[nl++] = l;
+        rc = sweep(&Knobs::lag, lags, nl);
+    }
+    p->kn = best;
+    const int rc2 = plan_capture(p);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (best_ms) *best_ms = best_t;
+    return BVSS_OK;
+}
+
+int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
+    if (!p) return fail(BVSS_EINVAL, "plan is NULL");
+    const int d = p->ix->p.d;
+    const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
+    const bool mma = (p->s.flags & BVSS_SEARCH_FAST) && refine_mma_supported(d, p->max_qset);
+    if (knobs) {
+        knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
+                                          : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
+        knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
+        int lag = 0;
+        if (mma) {
+            const int ns = refine_mma_stages(d, p->max_qset);
+            lag = (p->kn.lag == 4 || p->kn.lag == 5) && p->kn.lag < ns
+                      ? p->kn.lag
+                      : refine_mma_default_lag(d, p->max_qset);
+        }
+        knobs[2] = lag;
+        knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
+    }
+    if (launches) *launches = p->launches;
+    return BVSS_OK;
+}
+
+void bvss_plan_free(bvss_plan *p) {
+    if (!p) return;
+    if (p->cs) cudaStreamSynchronize(p->cs);
+    --p->ix->n_plans;
+    free_plan(p);
+}
 
 }  // extern "C"

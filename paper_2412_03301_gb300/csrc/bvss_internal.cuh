@@ -72,6 +72,7 @@ struct bvss_index {
     int64_t max_set = 0;         // largest set size (vectors)
     bvss::GatePlane planes[bvss::kMaxPlanes];
     int n_planes = 0;
+    int n_plans = 0;             // live plans (their graphs hold plane pointers)
     bvss::Workspace ws;
     int64_t *off_host[bvss::kOffRing] = {};     // pinned, batch-relative offsets
     cudaEvent_t off_event[bvss::kOffRing] = {}; // last copy out of each slot
@@ -89,10 +90,11 @@ struct bvss_index {
 namespace bvss {
 
 // ---- encode.cu --------------------------------------------------------------
-// FlyHash (Def. 7): pos[v] = ascending L winners, mask[v] = code bits.
+// FlyHash (Def. 7): pos[v] = ascending L winners, mask[v] = code bits.  With n_dev,
+// the count is min(n, *n_dev) read on the device (n is then the capacity).
 cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj,
                           int m, int F, int L, uint16_t *pos, uint32_t *mask,
-                          cudaStream_t st);
+                          cudaStream_t st, const int64_t *n_dev = nullptr);
 // Alg. 6 lines 1-4 for n_q query sets (codes qpos, offsets qoff relative to qpos).
 cudaError_t launch_query_prep(const uint16_t *qpos, const int64_t *qoff, int n_q,
                               int m, int L, int A, uint32_t *sq, uint16_t *plist,
@@ -166,16 +168,23 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
                               const float *vec, const float *vnorm, const int64_t *set_off,
                               int d, const int32_t *cand, const int32_t *thr, int C,
                               float *cand_dist, int *err, cudaStream_t st);
-// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 32)
+// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 64)
 bool refine_mma_supported(int d, int max_mq);
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st);
 // records each candidate's critical (query vector, row) pair; launch_rescore then
 // writes its FP32 distance as the candidate's distance
-cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
+// cand_cta: candidates per CTA (1..512, 0 = 512); lag: stages of copies a producer keeps in
+// flight (0 = by the ring depth; a lag that the ring cannot hold falls back to that).
+cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
-                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st);
+                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
+                              int cand_cta = 0, int lag = 0);
+// stages of the refine's ring for this dimension and batch (0 if the kernel cannot run),
+// and the copy lag used when none is asked for
+int refine_mma_stages(int d, int max_mq);
+int refine_mma_default_lag(int d, int max_mq);
 cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
                            const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
                            int C, const int2 *pair, float *cand_dist, cudaStream_t st);

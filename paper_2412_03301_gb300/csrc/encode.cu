@@ -19,8 +19,8 @@ constexpr int kEncThreads = 128;   // divides every valid m (m % 128 == 0)
 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_encode(const float *__restrict__ x, int64_t n, int d, int dpad,
-         const uint16_t *__restrict__ proj, int m, int F, int L,
+k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_dev, int d,
+         int dpad, const uint16_t *__restrict__ proj, int m, int F, int L,
          uint16_t *__restrict__ pos, uint32_t *__restrict__ mask) {
     extern __shared__ uint32_t sm[];
     float *xs = reinterpret_cast<float *>(sm);       // dpad floats
@@ -33,6 +33,7 @@ k_encode(const float *__restrict__ x, int64_t n, int d, int dpad,
 
     const int tid = threadIdx.x;
     const int W = m >> 5;
+    if (n_dev && *n_dev < n) n = *n_dev;   // the vector count, when it lives on the device
     for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
         const float *xv = x + v * (int64_t)d;
         for (int k = tid; k < d; k += THREADS) xs[k] = xv[k];
@@ -206,7 +207,8 @@ k_query_prep(const uint16_t *__restrict__ qpos, const int64_t *__restrict__ qoff
 }  // namespace
 
 cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj, int m,
-                          int F, int L, uint16_t *pos, uint32_t *mask, cudaStream_t st) {
+                          int F, int L, uint16_t *pos, uint32_t *mask, cudaStream_t st,
+                          const int64_t *n_dev) {
     if (n <= 0) return cudaSuccess;
     const int dpad = (d + 3) & ~3;
     const size_t smem = sizeof(uint32_t) * ((size_t)dpad + m + 2048 + m / 32);
@@ -215,7 +217,8 @@ cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = n < (int64_t)1 << 30 ? n : (int64_t)1 << 30;
-    kern<<<(unsigned)grid, kEncThreads, smem, st>>>(x, n, d, dpad, proj, m, F, L, pos, mask);
+    kern<<<(unsigned)grid, kEncThreads, smem, st>>>(x, n, n_dev, d, dpad, proj, m, F, L, pos,
+                                                     mask);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,12 @@
 // refine_mma.cu -- exact re-rank of Alg. 6 (lines 19-22) of arXiv 2412.03301 on
 // the 5th-generation tensor cores (tcgen05), from BF16 copies of the vectors.
 //
-// One CTA takes one query set (at most 32 vectors) and up to 512 of its
-// candidates, whose rows, concatenated in candidate order, are cut into tiles
-// of 128 rows.  For every tile the dot products of all (row, query vector)
-// pairs are one 128 x 32 x d GEMM: the tile rows are the A operand (M = 128),
-// the query vectors the B operand (N = 32), both K-major in the 128-byte
+// One CTA takes one query set (at most MQ = 32 or 64 vectors, one kernel
+// instance each) and up to 512 of its candidates, whose rows, concatenated in
+// candidate order, are cut into tiles of 128 rows.  For every tile the dot
+// products of all (row, query vector) pairs are one 128 x MQ x d GEMM: the tile
+// rows are the A operand (M = 128), the query vectors the B operand (N = MQ),
+// both K-major in the 128-byte
 // swizzle layout, accumulated in FP32 in tensor memory (TMEM lane = row,
 // column = query vector).
 //
@@ -19,11 +20,11 @@
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
 //              one of two TMEM accumulators;
 //   warps 0-3  epilogue.  Row phase (lane = row 32w + lane): squared
-//              distances |q|^2 + |v|^2 - 2 q.v to all query vectors from one
-//              tensor-memory load, their minimum with its arg-min (the row's
+//              distances |q|^2 + |v|^2 - 2 q.v to all query vectors from
+//              MQ / 32 tensor-memory loads, their minimum with its arg-min (the row's
 //              key), the distances written to a swizzled shared-memory block.
 //              After a barrier over the four warps, column phase (lane = query
-//              vector): warp w walks, whole, the candidates whose first row in
+//              vector, and lane + 32 when MQ = 64): warp w walks, whole, the candidates whose first row in
 //              the tile lies in rows 32w..32w+31, keeping per query vector the
 //              minimum over the candidate's rows (with the row) and the maximum
 //              of the rows' keys; when a candidate ends, the larger of the two
@@ -53,11 +54,9 @@ constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
 constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
 constexpr int kProd = 128;
 constexpr int kEpi = 128;
-constexpr int kMaxQ = 32;
-constexpr uint32_t kTmemCols = 64;   // two accumulators of 32 columns
+constexpr int kMaxQ = 64;            // query vectors per query set, at most
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kStageBytes = kRowsN * 128;
-constexpr int kQBlock = kMaxQ * 128; // 32 query rows x 128 bytes per K-block
 constexpr int kSmemMax = 232448;
 
 struct Meta {
@@ -75,21 +74,22 @@ struct Layout {
 // ahead of the MMA, which runs at most two tiles ahead of the epilogue.
 __host__ __device__ inline int meta_ring(int KB, int ns) { return (ns + KB) / KB + 3; }
 
-__host__ __device__ inline Layout make_layout(int d, int ns) {
+// MQ query rows x 128 bytes per K-block
+__host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
     Layout L;
     const int KB = d / kKB;
     const int MR = meta_ring(KB, ns);
     int o = 0;
-    L.q = o;       o += KB * kQBlock;
+    L.q = o;       o += KB * MQ * 128;
     L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
-    L.dist = o;    o += kRowsN * 128;              // row-phase distances, 32 per row
+    L.dist = o;    o += kRowsN * MQ * 4;           // row-phase distances, MQ per row
     L.rkey = o;    o += kRowsN * 8;                // per row minimum (the row's key), this tile
-    L.carry = o;   o += 2 * (kMaxQ + 1) * 8;       // state of a candidate continuing into the next tile
+    L.carry = o;   o += 2 * (MQ + 1) * 8;          // state of a candidate continuing into the next tile
     L.bars = o;    o += (2 * kMaxNS + 4 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
-    L.qn = o;      o += kMaxQ * 4;
+    L.qn = o;      o += MQ * 4;
     L.misc = o;    o += 16;                        // TMEM address, abort flag
     L.total = o + 1024;                            // slack to align the base to 1024 bytes
     return L;
@@ -99,9 +99,10 @@ __host__ __device__ inline Layout make_layout(int d, int ns) {
 inline int lag_for(int ns) { return ns >= 6 ? 5 : 4; }
 
 // most stages that fit, at least 5
-inline int pick_stages(int d) {
+inline int pick_stages(int d, int MQ) {
     for (int ns = kMaxNS; ns >= 5; --ns)
-        if (make_layout(d, ns).total <= kSmemMax && meta_ring(d / kKB, ns) <= kMaxMeta) return ns;
+        if (make_layout(d, ns, MQ).total <= kSmemMax && meta_ring(d / kKB, ns) <= kMaxMeta)
+            return ns;
     return 0;
 }
 
@@ -125,25 +126,28 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | low;
 }
 
-template <int LAG>
+template <int MQ, int LAG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
              const int64_t *__restrict__ set_off, int d, int ns,
-             const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C,
+             const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int cpc,
              int2 *__restrict__ pair, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     const int q = blockIdx.y;
     const int n_sel = thr[q * 4 + 3];
-    const int c0 = blockIdx.x * kCandCTA;
+    const int c0 = blockIdx.x * cpc;               // cpc <= kCandCTA candidates per CTA
     if (c0 >= n_sel) return;                       // uniform over the CTA
-    const int ncand = min(kCandCTA, n_sel - c0);
+    const int ncand = min(cpc, n_sel - c0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t a0 = qoff[q];
     const int mq = (int)(qoff[q + 1] - a0);
+    constexpr int kQBlock = MQ * 128;               // query rows x 128 bytes per K-block
+    constexpr int kRowB = MQ * 4;                    // bytes of one row's distances
+    constexpr uint32_t kTmemCols = 2 * MQ;           // two accumulators of MQ columns
     const int KB = d / kKB;
     const int MR = meta_ring(KB, ns);
-    const Layout Lo = make_layout(d, ns);
+    const Layout Lo = make_layout(d, ns, MQ);
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *Qs = smem + Lo.q;
@@ -175,9 +179,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         vrow0[c] = n;
     }
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
-    // query rows 0..31 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
+    // query rows 0..MQ-1 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
     const int nch = d / 8;                         // 16-byte chunks per row
-    for (int e = tid; e < kMaxQ * nch; e += kThreads) {
+    for (int e = tid; e < MQ * nch; e += kThreads) {
         const int a = e / nch, ch = e - (e / nch) * nch;
         float x[8];
         if (a < mq) {
@@ -237,7 +241,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         if (lane == 31) vrow0[kCandCTA] = incl;
     }
     // squared norms of the staged BF16 query rows, one warp per row (warps 1-8)
-    for (int a = warp - 1; warp > 0 && a < kMaxQ; a += kThreads / 32 - 1) {
+    for (int a = warp - 1; warp > 0 && a < MQ; a += kThreads / 32 - 1) {
         float sq = 0.0f;
         for (int ch = lane; ch < nch; ch += 32) {
             const uint4 pk =
@@ -332,7 +336,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(kRowsN, kMaxQ);
+            constexpr uint32_t idesc = umma_idesc_bf16(kRowsN, MQ);
             const uint32_t qaddr = smem_u32(Qs), saddr = smem_u32(stages);
             bool ok = true;
             for (int t = 0; t < n_tiles && ok; ++t) {
@@ -340,7 +344,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 ok = wait_or_abort(&tempty[buf], (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag, err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * kMaxQ);
+                const uint32_t dt = tmem + (uint32_t)(buf * MQ);
                 for (int kb = 0; kb < KB && ok; ++kb) {
                     const int u = t * KB + kb, s = u % ns;
                     ok = wait_or_abort(&full[s], (uint32_t)((u / ns) & 1), abort_flag, err);
@@ -359,10 +363,11 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     } else {
         // ---- epilogue: warps 0-3 ----------------------------------------------------
         const float INF = __int_as_float(0x7f800000);
-        float qreg[kMaxQ];
+        constexpr int H = MQ / 32;                   // query vectors per lane in the column phase
+        float qreg[MQ];
 #pragma unroll
-        for (int a = 0; a < kMaxQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
-        unsigned char *dw = dist + warp * 32 * 128;
+        for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
+        unsigned char *dw = dist + warp * 32 * kRowB;
         const int r = warp * 32 + lane;
         const int coff = ((lane >> 2) << 4) + (lane & 3) * 4;   // column phase: my query vector's word
         bool ok = true;
@@ -379,9 +384,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             if (ok) {
                 tc_fence_after();
                 const int rows_w = min(32, rows_t - warp * 32);
-                uint32_t v[32];
-                if (rows_w > 0)
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kMaxQ), v);
+                uint32_t v[MQ];
+                if (rows_w > 0) {
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * MQ + 32 * h),
+                                  *reinterpret_cast<uint32_t(*)[32]>(v + 32 * h));
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -391,7 +400,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     float best = INF;
                     int ba = 0;
 #pragma unroll
-                    for (int c4 = 0; c4 < 8; ++c4) {
+                    for (int c4 = 0; c4 < MQ / 4; ++c4) {
                         float x[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
@@ -404,7 +413,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                                 ba = a;
                             }
                         }
-                        *reinterpret_cast<float4 *>(dw + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                        // 128-byte halves of the row, 16-byte chunks swizzled by the row
+                        *reinterpret_cast<float4 *>(dw + lane * kRowB + (c4 >> 3) * 128 +
+                                                    (((c4 & 7) ^ (lane & 7)) << 4)) =
                             make_float4(x[0], x[1], x[2], x[3]);
                     }
                     rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
@@ -421,47 +432,75 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     j = vrow0[c + 1] - t0;
                     ++c;
                 }
-                const unsigned long long *cin = carry + ((t + 1) & 1) * (kMaxQ + 1);
-                unsigned long long *cout = carry + (t & 1) * (kMaxQ + 1);
+                const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
+                unsigned long long *cout = carry + (t & 1) * (MQ + 1);
                 while (j < hi) {
                     const int cs = vrow0[c] - t0;                 // < 0: continues from the last tile
                     const int je = min(vrow0[c + 1] - t0, rows_t);
-                    float bmin = INF;
-                    int brow = 0;
+                    // per query vector lane + 32 h: minimum over the candidate's rows, with the row
+                    float bmin[H];
+                    int brow[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        bmin[h] = INF;
+                        brow[h] = 0;
+                    }
                     unsigned long long kmax = 0;
                     if (cs < 0) {
-                        const unsigned long long k0 = cin[lane];
-                        bmin = __uint_as_float((uint32_t)(k0 >> 32));
-                        brow = (int)(uint32_t)k0;
-                        kmax = cin[kMaxQ];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const unsigned long long k0 = cin[32 * h + lane];
+                            bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
+                            brow[h] = (int)(uint32_t)k0;
+                        }
+                        kmax = cin[MQ];
                     }
                     for (int j0 = j; j0 < je; j0 += 4) {
-                        float x[4];
+                        float x[4][H];
                         unsigned long long kk[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
-                            x[i] = *reinterpret_cast<const float *>(dist + jr * 128 +
-                                                                    (coff ^ ((jr & 7) << 4)));
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                x[i][h] = *reinterpret_cast<const float *>(
+                                    dist + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
                             kk[i] = rkey[jr];
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            if (x[i] < bmin) {
-                                bmin = x[i];
-                                brow = j0 + i - cs;   // row inside the candidate's set
-                            }
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                if (x[i][h] < bmin[h]) {
+                                    bmin[h] = x[i][h];
+                                    brow[h] = j0 + i - cs;   // row inside the candidate's set
+                                }
                             kmax = kk[i] > kmax ? kk[i] : kmax;
                         }
                     }
                     if (vrow0[c + 1] - t0 <= rows_t) {
-                        // complete: max over query vectors of the row minima vs max over rows
-                        const unsigned long long key = dkey(bmin, (uint32_t)brow);
-                        const uint32_t bits = lane < mq ? __float_as_uint(bmin) : 0u;
-                        const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-                        const uint32_t who = __ballot_sync(0xffffffffu, lane < mq && bits == mx);
-                        const int src = __ffs(who) - 1;
-                        int pa = src, pr = (int)__shfl_sync(0xffffffffu, (uint32_t)key, src);
+                        // complete: max over query vectors of the row minima vs max over rows;
+                        // the query side's pair is the lowest query vector attaining it
+                        uint32_t bits[H], lmx = 0;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            bits[h] = 32 * h + lane < mq ? __float_as_uint(bmin[h]) : 0u;
+                            lmx = bits[h] > lmx ? bits[h] : lmx;
+                        }
+                        const uint32_t mx = __reduce_max_sync(0xffffffffu, lmx);
+                        int pa = -1, pr = 0;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const uint32_t who =
+                                __ballot_sync(0xffffffffu, 32 * h + lane < mq && bits[h] == mx);
+                            const int src = __ffs(who) - 1;
+                            const int rsrc = (int)__shfl_sync(0xffffffffu, (uint32_t)brow[h],
+                                                              src < 0 ? 0 : src);
+                            if (pa < 0 && who != 0u) {
+                                pa = 32 * h + src;
+                                pr = rsrc;
+                            }
+                        }
                         if (mx < (uint32_t)(kmax >> 32)) {
                             pa = (int)(kmax & 0xff);
                             pr = (int)((kmax >> 8) & 0xffffff);
@@ -469,8 +508,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                         if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
                     } else {
                         // continues into the next tile
-                        cout[lane] = dkey(bmin, (uint32_t)brow);
-                        if (lane == 0) cout[kMaxQ] = kmax;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
+                        if (lane == 0) cout[MQ] = kmax;
                     }
                     j = je;
                     ++c;
@@ -562,9 +602,12 @@ __global__ void k_to_bf16(const float *__restrict__ x, int64_t n, int d,
 
 }  // namespace
 
+// query-set width of the kernel instance for the batch's largest query set
+inline int mq_for(int max_mq) { return max_mq <= 32 ? 32 : 64; }
+
 bool refine_mma_supported(int d, int max_mq) {
     if (d % kKB != 0 || d < kKB || max_mq < 1 || max_mq > kMaxQ) return false;
-    return pick_stages(d) > 0;
+    return pick_stages(d, mq_for(max_mq)) > 0;
 }
 
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
@@ -576,20 +619,36 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q,
+int refine_mma_stages(int d, int max_mq) {
+    return refine_mma_supported(d, max_mq) ? pick_stages(d, mq_for(max_mq)) : 0;
+}
+
+int refine_mma_default_lag(int d, int max_mq) {
+    const int ns = refine_mma_stages(d, max_mq);
+    return ns ? lag_for(ns) : 0;
+}
+
+cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
-                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st) {
+                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
+                              int cand_cta, int lag) {
     if (n_q <= 0) return cudaSuccess;
-    const int ns = pick_stages(d);
-    if (ns == 0) return cudaErrorInvalidValue;
-    const Layout Lo = make_layout(d, ns);
-    const int gx = (C + kCandCTA - 1) / kCandCTA;
-    auto kern = lag_for(ns) == 5 ? k_refine_mma<5> : k_refine_mma<4>;
+    if (!refine_mma_supported(d, max_mq)) return cudaErrorInvalidValue;
+    const int MQ = mq_for(max_mq);
+    const int ns = pick_stages(d, MQ);
+    const Layout Lo = make_layout(d, ns, MQ);
+    const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
+    const int gx = (C + cpc - 1) / cpc;
+    // a producer holds `lag` arrivals back, so the ring needs more stages than that
+    if (!((lag == 4 || lag == 5) && lag < ns)) lag = lag_for(ns);
+    const bool l5 = lag == 5;
+    auto kern = MQ == 32 ? (l5 ? k_refine_mma<32, 5> : k_refine_mma<32, 4>)
+                         : (l5 ? k_refine_mma<64, 5> : k_refine_mma<64, 4>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,
-                                                    cand, thr, C, pair, err);
+                                                    cand, thr, C, cpc, pair, err);
     return cudaGetLastError();
 }
 

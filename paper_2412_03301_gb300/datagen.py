@@ -58,6 +58,15 @@ def set_sizes(n_sets: int, lo: int, hi: int, seed: int) -> np.ndarray:
     return rng.integers(lo, hi + 1, size=n_sets, dtype=np.int64)
 
 
+def zipf_sizes(n_sets: int, lo: int, hi: int, seed: int, s: float = 1.0) -> np.ndarray:
+    """Set sizes with P(size = k) proportional to k^-s on [lo, hi] (a truncated Zipf
+    law; s = 1 is the classic one)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = np.arange(lo, hi + 1, dtype=np.float64)
+    p = k ** -s
+    return rng.choice(np.arange(lo, hi + 1, dtype=np.int64), size=n_sets, p=p / p.sum())
+
+
 def offsets_from_sizes(sizes: np.ndarray) -> np.ndarray:
     off = np.zeros(sizes.shape[0] + 1, np.int64)
     np.cumsum(sizes, out=off[1:])
@@ -115,15 +124,22 @@ class Mixture:
 def workload(n_sets: int, size_lo: int, size_hi: int, d: int, n_components: int,
              n_queries: int, q_lo: int, q_hi: int, m: int, fanin: int,
              seed: int = 0, device="cpu", sigma: float = 0.5, tau: float = 0.5,
-             group: int = 16, grid: bool = True):
+             group: int = 16, grid: bool = True, size_dist: str = "uniform"):
     """A database, its query sets and the FlyHash projection, all seeded.
 
-    seed -> database, seed + 1 -> queries, seed + 2 -> projection.
+    seed -> database, seed + 1 -> queries, seed + 2 -> projection.  Database set
+    sizes are uniform or (size_dist="zipf") truncated Zipf with exponent 1 on
+    [size_lo, size_hi]; query set sizes are uniform on [q_lo, q_hi].
     Returns a dict of vectors / offsets (torch on ``device``; offsets also
     as numpy) and the projection (numpy uint16).
     """
     mix = Mixture(d, n_components, seed, group=group, tau=tau, device=device)
-    sizes = set_sizes(n_sets, size_lo, size_hi, seed * 1000 + 11)
+    if size_dist == "zipf":
+        sizes = zipf_sizes(n_sets, size_lo, size_hi, seed * 1000 + 11)
+    elif size_dist == "uniform":
+        sizes = set_sizes(n_sets, size_lo, size_hi, seed * 1000 + 11)
+    else:
+        raise ValueError("size_dist must be 'uniform' or 'zipf'")
     qsizes = set_sizes(n_queries, q_lo, q_hi, seed * 1000 + 12)
     vec = mix.draw_sets(sizes, seed * 1000 + 21, sigma=sigma, grid=grid)
     qvec = mix.draw_sets(qsizes, seed * 1000 + 22, sigma=sigma, grid=grid)
@@ -137,3 +153,9 @@ SMALL = dict(n_sets=2000, size_lo=4, size_hi=16, d=128, n_components=64,
              n_queries=100, q_lo=4, q_hi=16, m=2048, fanin=8, L=32, C=200, k=10)
 LARGE = dict(n_sets=1_000_000, size_lo=8, size_hi=32, d=384, n_components=4096,
              n_queries=1000, q_lo=8, q_hi=32, m=4096, fanin=8, L=64, C=2000, k=10)
+# The batched serving load: Zipf set sizes, d = 768 (values exact in BF16), 4096 query
+# sets of 1-64 vectors per pass.  The load names neither the mixture, m, F, L, C nor k;
+# they are taken from LARGE.
+SERVING = dict(n_sets=200_000, size_lo=1, size_hi=128, d=768, n_components=4096,
+               n_queries=4096, q_lo=1, q_hi=64, m=4096, fanin=8, L=64, C=2000, k=10,
+               size_dist="zipf")

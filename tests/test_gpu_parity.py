@@ -272,6 +272,9 @@ def test_longest_codes(bv, orc, m):
     (500, 20, 140, 192, 2, 32, 150, 15),   # sets longer than one 128-row tile
     (3000, 1, 1, 64, 1, 3, 1500, 21),      # one-row sets: 128 candidates finish per tile
     (400, 2, 6, 1024, 2, 8, 300, 22),      # d = 1024: the shallowest stage ring
+    (600, 1, 128, 768, 1, 64, 400, 23),    # the serving load's d and sizes: 64-wide refine
+    (500, 8, 32, 384, 33, 64, 700, 24),    # every query set wider than 32
+    (300, 20, 140, 192, 60, 64, 150, 25),  # long sets and wide query sets together
 ])
 def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
@@ -281,10 +284,12 @@ def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
 
 
 def test_fast_form_falls_back_and_validates(bv, orc):
-    # query sets of more than 32 vectors use the FP32 refine
-    w = _workload(150, 2, 10, 128, 16, 5, 33, 50, 512, 8, seed=16)
-    case = Case(bv, orc, w, 16, bf16=True)
-    _check_query(bv, orc, case, k=5, C=60, A=3, M=1, fast=True)
+    # query sets of 33-64 vectors take the 64-wide tensor-core refine, larger ones the
+    # FP32 refine
+    for qlo, qhi, seed in ((33, 50, 16), (40, 64, 18), (65, 90, 19)):
+        w = _workload(150, 2, 10, 128, 16, 5, qlo, qhi, 512, 8, seed=seed)
+        case = Case(bv, orc, w, 16, bf16=True)
+        _check_query(bv, orc, case, k=5, C=60, A=3, M=1, fast=True)
     # the fast form needs the BF16 copy, which needs d % 64 == 0
     w2 = _workload(50, 2, 4, 48, 8, 3, 2, 4, 256, 4, seed=17)
     ix = bv.bvss_build(w2["vectors"].cuda(), w2["offsets"], w2["proj"], wta_l=8)
