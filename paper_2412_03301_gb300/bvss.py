@@ -76,6 +76,7 @@ SYMBOLS = {
     "bvss_plan_launch": (ctypes.c_int, [_vp, _vp]),
     "bvss_plan_tune": (ctypes.c_int, [_vp, _c_i32, _vp, ctypes.POINTER(ctypes.c_float)]),
     "bvss_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i64)]),
+    "bvss_plan_set_knobs": (ctypes.c_int, [_vp, ctypes.POINTER(_c_i32)]),
     "bvss_plan_free": (None, [_vp]),
     "bvss_free": (None, [_vp]),
     "bvss_last_error": (ctypes.c_char_p, []),
@@ -266,6 +267,11 @@ class Plan:
         _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
         return dict(scan={1: "tensor", 2: "popcount", 0: "alg2"}[kn[0]], cand_cta=kn[1],
                     lag=kn[2], mq=kn[3], launches=nl.value)
+
+    def set_knobs(self, scan=0, cand_cta=0, lag=0):
+        """Pin the tuner's choices (0 = default); scan 1 = tensor-core, 2 = popcount."""
+        kn = (_c_i32 * 3)(scan, cand_cta, lag)
+        _check(load().bvss_plan_set_knobs(self.handle, kn))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -980,8 +980,8 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
         rc = sweep(&Knobs::cand_cta, ctas, 3);
     }
     if (!rc && mma) {
-        int lags[2], nl = 0;
-        for (int l = 4; l <= 5; ++l)
+        int lags[8], nl = 0;
+        for (int l = 4; l <= 8; ++l)
             if (l < ns) lags[nl++] = l;
         rc = sweep(&Knobs::lag, lags, nl);
     }
@@ -1002,18 +1002,27 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
         knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
                                           : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
-        int lag = 0;
-        if (mma) {
-            const int ns = refine_mma_stages(d, p->max_qset);
-            lag = (p->kn.lag == 4 || p->kn.lag == 5) && p->kn.lag < ns
-                      ? p->kn.lag
-                      : refine_mma_default_lag(d, p->max_qset);
-        }
-        knobs[2] = lag;
+        knobs[2] = mma ? refine_mma_lag(d, p->max_qset, p->kn.lag) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
     }
     if (launches) *launches = p->launches;
     return BVSS_OK;
+}
+
+int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs) {
+    if (!p || !p->exec) return fail(BVSS_EINVAL, "plan is NULL");
+    if (!knobs) return fail(BVSS_EINVAL, "knobs are NULL");
+    if (knobs[0] < 0 || knobs[0] > 2) return fail(BVSS_EINVAL, "scan = %d: need 0, 1 or 2", knobs[0]);
+    if (knobs[1] < 0 || knobs[1] > 512)
+        return fail(BVSS_EINVAL, "candidates per CTA = %d: need 0..512", knobs[1]);
+    if (knobs[2] < 0) return fail(BVSS_EINVAL, "lag = %d: need >= 0", knobs[2]);
+    const Knobs old = p->kn;
+    p->kn.scan = knobs[0];
+    p->kn.cand_cta = knobs[1];
+    p->kn.lag = knobs[2];
+    const int rc = plan_capture(p);
+    if (rc) p->kn = old;
+    return rc;
 }
 
 void bvss_plan_free(bvss_plan *p) {

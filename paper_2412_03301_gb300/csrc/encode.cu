@@ -16,17 +16,45 @@ namespace bvss {
 namespace {
 
 constexpr int kEncThreads = 128;   // divides every valid m (m % 128 == 0)
+constexpr int kEncWide = 256;      // used when it divides m
+constexpr int kEncRepWords = 12288; // 48 KB for the copies of the vector
+
+// eight 16-byte read-only loads issued back to back (one asm statement, so the
+// compiler cannot interleave their uses and serialise the latencies)
+__device__ __forceinline__ void ld_nc_v4x8(const void *const (&p)[8], uint4 (&v)[8]) {
+    asm volatile(
+        "ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%32];\n\t"
+        "ld.global.nc.v4.u32 {%4, %5, %6, %7}, [%33];\n\t"
+        "ld.global.nc.v4.u32 {%8, %9, %10, %11}, [%34];\n\t"
+        "ld.global.nc.v4.u32 {%12, %13, %14, %15}, [%35];\n\t"
+        "ld.global.nc.v4.u32 {%16, %17, %18, %19}, [%36];\n\t"
+        "ld.global.nc.v4.u32 {%20, %21, %22, %23}, [%37];\n\t"
+        "ld.global.nc.v4.u32 {%24, %25, %26, %27}, [%38];\n\t"
+        "ld.global.nc.v4.u32 {%28, %29, %30, %31}, [%39];"
+        : "=r"(v[0].x), "=r"(v[0].y), "=r"(v[0].z), "=r"(v[0].w), "=r"(v[1].x), "=r"(v[1].y),
+          "=r"(v[1].z), "=r"(v[1].w), "=r"(v[2].x), "=r"(v[2].y), "=r"(v[2].z), "=r"(v[2].w),
+          "=r"(v[3].x), "=r"(v[3].y), "=r"(v[3].z), "=r"(v[3].w), "=r"(v[4].x), "=r"(v[4].y),
+          "=r"(v[4].z), "=r"(v[4].w), "=r"(v[5].x), "=r"(v[5].y), "=r"(v[5].z), "=r"(v[5].w),
+          "=r"(v[6].x), "=r"(v[6].y), "=r"(v[6].z), "=r"(v[6].w), "=r"(v[7].x), "=r"(v[7].y),
+          "=r"(v[7].z), "=r"(v[7].w)
+        : "l"(p[0]), "l"(p[1]), "l"(p[2]), "l"(p[3]), "l"(p[4]), "l"(p[5]), "l"(p[6]),
+          "l"(p[7]));
+}
 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_dev, int d,
-         int dpad, const uint16_t *__restrict__ proj, int m, int F, int L,
+         int dpad, int rep, const uint16_t *__restrict__ proj, int m, int F, int L,
          uint16_t *__restrict__ pos, uint32_t *__restrict__ mask) {
     extern __shared__ uint32_t sm[];
-    float *xs = reinterpret_cast<float *>(sm);       // dpad floats
-    uint32_t *key = sm + dpad;                       // m keys
+    // rep (a power of two <= 32) copies of the vector, interleaved: value k of copy c
+    // at xs[k * rep + c].  Lane l reads copy l % rep, so with rep = 32 every lane of a
+    // warp reads its own bank and the random gathers of W's rows never conflict.
+    float *xs = reinterpret_cast<float *>(sm);       // dpad * rep floats
+    uint32_t *key = sm + dpad * rep;                 // m keys (first: a plain copy of x)
     uint32_t *hist = key + m;                        // 2048 bins
     uint32_t *mw = hist + 2048;                      // m/32 code words
+    uint32_t *eqw = mw + (m >> 5);                   // m/32 words: outputs equal to the L-th
     __shared__ int scan_sh[THREADS / 32 + 1];
     __shared__ uint32_t sel_digit;
     __shared__ int sel_need;
@@ -36,27 +64,48 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
     if (n_dev && *n_dev < n) n = *n_dev;   // the vector count, when it lives on the device
     for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
         const float *xv = x + v * (int64_t)d;
-        for (int k = tid; k < d; k += THREADS) xs[k] = xv[k];
+        const int rs = __ffs(rep) - 1;
+        float *x0 = reinterpret_cast<float *>(key);    // plain copy, until the keys are written
+        for (int k = tid; k < d; k += THREADS) x0[k] = xv[k];
+        __syncthreads();
+        // replicate: a warp reads one value (broadcast) and writes its consecutive copies
+#pragma unroll 4
+        for (int e = tid; e < d * rep; e += THREADS) xs[e] = x0[e >> rs];
+        __syncthreads();
+        const float *xl = xs + (tid & 31 & (rep - 1));   // this lane's copy
         __syncthreads();
 
         // activations a_j (Def. 7: W v with W sparse binary), as sortable keys
         if (F == 8) {
-            for (int j = tid; j < m; j += THREADS) {
-                const uint4 r = *reinterpret_cast<const uint4 *>(proj + (int64_t)j * 8);
-                const uint32_t w4[4] = {r.x, r.y, r.z, r.w};
-                float a = 0.0f;
+            // eight rows of W per thread in flight (m is a multiple of THREADS)
+            constexpr int kU = 8;
+            for (int j0 = tid; j0 < m; j0 += kU * THREADS) {
+                uint4 r[kU];
+                const void *rp[kU];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    a = __fadd_rn(a, xs[w4[t] & 0xFFFFu]);
-                    a = __fadd_rn(a, xs[w4[t] >> 16]);
+                for (int i = 0; i < kU; ++i) {
+                    const int j = j0 + i * THREADS;
+                    rp[i] = proj + (int64_t)(j < m ? j : m - 1) * 8;   // past m: any valid row
                 }
-                key[j] = order_key(a);
+                ld_nc_v4x8(rp, r);
+#pragma unroll
+                for (int i = 0; i < kU; ++i) {
+                    const int j = j0 + i * THREADS;
+                    const uint32_t w4[4] = {r[i].x, r[i].y, r[i].z, r[i].w};
+                    float a = 0.0f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        a = __fadd_rn(a, xl[(w4[t] & 0xFFFFu) << rs]);
+                        a = __fadd_rn(a, xl[(w4[t] >> 16) << rs]);
+                    }
+                    if (j < m) key[j] = order_key(a);
+                }
             }
         } else {
             for (int j = tid; j < m; j += THREADS) {
                 const uint16_t *row = proj + (int64_t)j * F;
                 float a = 0.0f;
-                for (int t = 0; t < F; ++t) a = __fadd_rn(a, xs[row[t]]);
+                for (int t = 0; t < F; ++t) a = __fadd_rn(a, xl[(int)row[t] << rs]);
                 key[j] = order_key(a);
             }
         }
@@ -75,20 +124,35 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
                 if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & (nb - 1)], 1u);
             }
             __syncthreads();
-            const int B = nb / THREADS;          // bins owned by this thread
+            // bins owned by this thread, read 16 bytes at a time (B is a multiple of 4)
+            constexpr int BMAX = 2048 / THREADS;
+            const int B = nb / THREADS;
+            uint32_t hv[BMAX];
             int s = 0;
-            for (int b = 0; b < B; ++b) s += (int)hist[tid * B + b];
+#pragma unroll
+            for (int i = 0; i < BMAX / 4; ++i) {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                if (4 * i < B) q = reinterpret_cast<const uint4 *>(hist + tid * B)[i];
+                hv[4 * i] = q.x;
+                hv[4 * i + 1] = q.y;
+                hv[4 * i + 2] = q.z;
+                hv[4 * i + 3] = q.w;
+                s += (int)(q.x + q.y + q.z + q.w);
+            }
             int tot;
             const int excl = block_excl_scan<THREADS>(s, scan_sh, &tot);
             const int above = tot - excl - s;    // keys in higher bins
             if (above < need && above + s >= need) {
                 int cum = above;
-                for (int b = B - 1; b >= 0; --b) {
-                    const int c = (int)hist[tid * B + b];
+                bool found = false;
+#pragma unroll
+                for (int b = BMAX - 1; b >= 0; --b) {
+                    if (b >= B || found) continue;
+                    const int c = (int)hv[b];
                     if (cum + c >= need) {
                         sel_digit = (uint32_t)(tid * B + b);
                         sel_need = need - cum;
-                        break;
+                        found = true;
                     }
                     cum += c;
                 }
@@ -102,34 +166,39 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
         const int n_eq = (int)hist[T & 1023u];     // keys equal to T
         const bool all_ties = (need == n_eq);
 
-        // code bits: 32 consecutive outputs per warp
+        // code bits and the outputs equal to the L-th value: 32 consecutive outputs per warp
         for (int j = tid; j < m; j += THREADS) {
             const uint32_t k = key[j];
-            const bool sel = k > T || (k == T && all_ties);
-            const uint32_t b = __ballot_sync(0xffffffffu, sel);
-            if ((tid & 31) == 0) mw[j >> 5] = b;
+            const uint32_t b = __ballot_sync(0xffffffffu, k > T || (k == T && all_ties));
+            const uint32_t e = __ballot_sync(0xffffffffu, k == T);
+            if ((tid & 31) == 0) {
+                mw[j >> 5] = b;
+                eqw[j >> 5] = e;
+            }
         }
         __syncthreads();
+        const int WE = (W + THREADS - 1) / THREADS;   // code words per thread
+        const int w0 = tid * WE, w1 = min(W, w0 + WE);
         if (!all_ties) {
-            // several outputs share the L-th value: lower indices win
-            const int E = m / THREADS;
-            const int e0 = tid * E;
+            // several outputs share the L-th value: the first `need` of them in index order win
             int c = 0;
-            for (int j = e0; j < e0 + E; ++j) c += key[j] == T;
+            for (int w = w0; w < w1; ++w) c += __popc(eqw[w]);
             int tot;
             int r = block_excl_scan<THREADS>(c, scan_sh, &tot);
-            for (int j = e0; j < e0 + E && r < need; ++j) {
-                if (key[j] == T) {
-                    atomicOr(&mw[j >> 5], 1u << (j & 31));
+            for (int w = w0; w < w1 && r < need; ++w) {
+                uint32_t e = eqw[w], take = 0u;
+                while (e && r < need) {
+                    const uint32_t low = e & (0u - e);
+                    take |= low;
+                    e ^= low;
                     ++r;
                 }
+                mw[w] |= take;
             }
             __syncthreads();
         }
 
         // winner positions in ascending order
-        const int WE = (W + THREADS - 1) / THREADS;
-        const int w0 = tid * WE, w1 = min(W, w0 + WE);
         int c = 0;
         for (int w = w0; w < w1; ++w) c += __popc(mw[w]);
         int tot;
@@ -211,14 +280,21 @@ cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj
                           const int64_t *n_dev) {
     if (n <= 0) return cudaSuccess;
     const int dpad = (d + 3) & ~3;
-    const size_t smem = sizeof(uint32_t) * ((size_t)dpad + m + 2048 + m / 32);
-    auto kern = k_encode<kEncThreads>;
+    int rep = 32;                                   // copies of the vector that fit 48 KB
+    while (rep > 1 && (size_t)dpad * rep > (size_t)kEncRepWords) rep >>= 1;
+    // after the copies: the keys, histogram and code words, which also hold the plain
+    // copy of the vector while the copies are made
+    size_t tail = (size_t)m + 2048 + 2 * (m / 32);
+    if (tail < (size_t)dpad) tail = dpad;
+    const size_t smem = sizeof(uint32_t) * ((size_t)dpad * rep + tail);
+    const bool wide = m % kEncWide == 0;
+    auto kern = wide ? k_encode<kEncWide> : k_encode<kEncThreads>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = n < (int64_t)1 << 30 ? n : (int64_t)1 << 30;
-    kern<<<(unsigned)grid, kEncThreads, smem, st>>>(x, n, n_dev, d, dpad, proj, m, F, L, pos,
-                                                     mask);
+    kern<<<(unsigned)grid, wide ? kEncWide : kEncThreads, smem, st>>>(x, n, n_dev, d, dpad, rep,
+                                                                      proj, m, F, L, pos, mask);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@
 //   warps 4-7  producers: gather the tile rows one 64-dimension block at a
 //              time with 16-byte cp.async copies straight into the swizzled
 //              stage (8 lanes per 128-byte row segment, so copies coalesce; a
-//              ring of 5-8 stages, 4 or 5 kept in flight), then signal the
+//              ring of 5-10 stages, 4-8 kept in flight), then signal the
 //              stage's mbarrier;
 //   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
 //              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
@@ -48,7 +48,7 @@ namespace {
 
 constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
 constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
-constexpr int kMaxNS = 8;            // stages in the ring, at most
+constexpr int kMaxNS = 10;           // stages in the ring, at most
 constexpr int kCandCTA = 512;        // candidates per CTA
 constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
 constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
@@ -97,6 +97,8 @@ __host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
 
 // stages a producer keeps in flight for a ring of ns (it holds that many arrivals back)
 inline int lag_for(int ns) { return ns >= 6 ? 5 : 4; }
+constexpr int kMinLag = 4, kMaxLag = 8;   // instantiated lags
+inline bool refine_lag_valid(int lag, int ns) { return lag >= kMinLag && lag <= kMaxLag && lag < ns; }
 
 // most stages that fit, at least 5
 inline int pick_stages(int d, int MQ) {
@@ -628,6 +630,12 @@ int refine_mma_default_lag(int d, int max_mq) {
     return ns ? lag_for(ns) : 0;
 }
 
+int refine_mma_lag(int d, int max_mq, int lag) {
+    const int ns = refine_mma_stages(d, max_mq);
+    if (!ns) return 0;
+    return refine_lag_valid(lag, ns) ? lag : lag_for(ns);
+}
+
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
@@ -641,10 +649,13 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
     // a producer holds `lag` arrivals back, so the ring needs more stages than that
-    if (!((lag == 4 || lag == 5) && lag < ns)) lag = lag_for(ns);
-    const bool l5 = lag == 5;
-    auto kern = MQ == 32 ? (l5 ? k_refine_mma<32, 5> : k_refine_mma<32, 4>)
-                         : (l5 ? k_refine_mma<64, 5> : k_refine_mma<64, 4>);
+    if (!refine_lag_valid(lag, ns)) lag = lag_for(ns);
+    using Kern = decltype(&k_refine_mma<32, 4>);
+    static const Kern k32[] = {k_refine_mma<32, 4>, k_refine_mma<32, 5>, k_refine_mma<32, 6>,
+                               k_refine_mma<32, 7>, k_refine_mma<32, 8>};
+    static const Kern k64[] = {k_refine_mma<64, 4>, k_refine_mma<64, 5>, k_refine_mma<64, 6>,
+                               k_refine_mma<64, 7>, k_refine_mma<64, 8>};
+    const Kern kern = (MQ == 32 ? k32 : k64)[lag - kMinLag];
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,
