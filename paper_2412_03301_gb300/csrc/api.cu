@@ -85,6 +85,8 @@ void free_workspace(Workspace &w) {
     dfree(w.hist);
     dfree(w.thr);
     dfree(w.chunk);
+    dfree(w.bmin);
+    dfree(w.bound);
     dfree(w.cand);
     dfree(w.cand_dist);
     dfree(w.pair);
@@ -203,6 +205,8 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.hist, (size_t)nq * ((m > 2 * L ? m : 2 * L) + 1)));
     BVSS_CU(dalloc(&w.thr, (size_t)nq * 4));
     BVSS_CU(dalloc(&w.chunk, (size_t)nq * n_chunks * kSelRangeWords));
+    BVSS_CU(dalloc(&w.bmin, (size_t)nq * ((ix->n_sets + kSelBlock - 1) / kSelBlock)));
+    BVSS_CU(dalloc(&w.bound, (size_t)nq));
     BVSS_CU(dalloc(&w.cand, (size_t)nq * C));
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
@@ -374,16 +378,18 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
                               hs, st));
     else if (tensor_scan)
         BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
-                                w.q8, w.qpop, nb, w.h, hs, ix->err, st));
+                                w.q8, w.qpop, nb, w.h, hs, ix->err, st, w.bmin));
     else
         BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, w.gate, ix->NW, gate_mode, w.sq, nb, w.h,
                             hs, st));
     ++n;
     if (ev) BVSS_CU(cudaEventRecord(ev[3], st));
     // lines 10-18 (Alg. 2 line 9); scores run up to m (Hamming of sketches) or 2L (Haus^H)
+    // the tensor-core scan also leaves the block minima that let the select skip blocks
+    const bool bounded = !alg2 && tensor_scan;
     BVSS_CU(launch_select(w.h, ix->n_sets, hs, alg2 ? 2 * L : m, nb, C, w.hist, w.thr, w.chunk,
-                          w.cand, st));
-    n += kSelectKernels;
+                          w.cand, st, bounded ? w.bmin : nullptr, bounded ? w.bound : nullptr));
+    n += kSelectKernels + (bounded ? 1 : 0);
     if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
     // lines 19-23
     const bool mma = fast && refine_mma_supported(d, b.max_mq);

@@ -13,6 +13,7 @@ namespace bvss {
 constexpr int kMaxPlanes = 8;          // cached first-layer gate planes (one per M)
 constexpr uint16_t kGatedOut = 0xFFFF; // h of a set outside F1
 constexpr int kSelChunk = 16384;       // sets per CTA in the candidate select
+constexpr int kSelBlock = 128;         // sets per block minimum (the scan's tile width)
 constexpr int kSelRangeWords = 32;     // per chunk: 8 warp ranges x (lt, eq, tie rank, slot)
 constexpr int kOffRing = 4;            // pinned staging slots for query offsets
 constexpr int kProfEvents = BVSS_N_STAGES + 1;  // events per profiled batch
@@ -41,6 +42,8 @@ struct Workspace {
     uint32_t *hist = nullptr;     // histogram of h                      cap_q x (m + 1)
     int32_t *thr = nullptr;       // per query: H*, n_lt, take_eq, n_sel cap_q x 4
     int32_t *chunk = nullptr;     // per (query, chunk): lt, eq, eq_before, out_off
+    uint16_t *bmin = nullptr;     // minimum h per block of kSelBlock sets  cap_q x n_blk
+    int32_t *bound = nullptr;     // per query: bound on the select threshold  cap_q
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     int2 *pair = nullptr;         // (query vector, row) attaining each candidate's value
@@ -136,10 +139,11 @@ cudaError_t launch_sketch_pop(const uint32_t *sketch, int64_t n_sets, int W, int
 // |S_Q| (qpop, n_q rounded up to 256 ints)
 cudaError_t launch_expand_q(const uint32_t *sq, int n_q, int W, uint8_t *q8, int32_t *qpop,
                             cudaStream_t st);
+// bmin (may be null): n_q x ceil(n_sets / kSelBlock) minimum scores per block of sets
 cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
                             const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
                             const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
-                            cudaStream_t st);
+                            cudaStream_t st, uint16_t *bmin = nullptr);
 
 // ---- alg2.cu: Haus^H scores of the plain BioVSS search (Alg. 2 lines 6-8) ----
 // h[q][j] = Haus^H between query set q's codes (qpos, L positions per vector,
@@ -150,10 +154,13 @@ cudaError_t launch_haus_h(const uint16_t *qpos, const int64_t *qoff, int n_q,
 
 // ---- select.cu
 constexpr int kSelectKernels = 5;   // kernels launch_select runs --------------------------------------------------------------
-// Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.
+// Alg. 6 lines 10-18: the min(C, |F1|) smallest (h, id), listed by ascending id.  With
+// bmin (n_q x ceil(n_sets / kSelBlock) block minima of h) the passes over h skip blocks
+// that cannot hold a candidate; bound is then n_q ints of scratch.
 cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, int n_q,
                           int C, uint32_t *hist, int32_t *thr, int32_t *chunk,
-                          int32_t *cand, cudaStream_t st);
+                          int32_t *cand, cudaStream_t st, const uint16_t *bmin = nullptr,
+                          int32_t *bound = nullptr);
 
 // ---- refine.cu --------------------------------------------------------------
 // Alg. 6 lines 19-23: exact Hausdorff of each candidate, then top-k.

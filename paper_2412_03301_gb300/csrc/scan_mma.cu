@@ -26,7 +26,9 @@
 //              two pairs of TMEM accumulators of 128 columns;
 //   warps 0-3  epilogue: lane = query row of each block; per 32 sets, one
 //              tensor-memory load, h = |S_Q| + |S_i| - 2 <S_Q, S_i>, the
-//              layer-1 bit, and 64-byte row stores into h.
+//              layer-1 bit, and 64-byte row stores into h; per tile, the
+//              minimum of the row's 128 scores (the candidate select reads
+//              only tiles whose minimum can reach its threshold).
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include "bvss_internal.cuh"
@@ -38,6 +40,7 @@ namespace {
 
 constexpr int kQM = 128;              // query sketches per MMA (M); a tile holds two blocks
 constexpr int kSN = 128;              // set sketches per tile (MMA N)
+static_assert(kSN == kSelBlock, "one block minimum per tile");
 constexpr int kNS = 4;                // stages
 constexpr int kPR = 8;                // packed-word ring slots per producer thread
 constexpr int kPLag = 6;              // packed-word copies in flight per producer thread
@@ -119,7 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, int64_t n_sets,
            int W, const uint32_t *__restrict__ gate, int64_t NW, int gate_mode,
            const uint8_t *__restrict__ q8, const int32_t *__restrict__ qpop, int n_q, int QP,
-           uint16_t *__restrict__ h, int64_t hs, int *__restrict__ err) {
+           uint16_t *__restrict__ h, int64_t hs, uint16_t *__restrict__ bmin, int64_t n_blk,
+           int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -285,6 +289,7 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
             tc_fence_after();
 #pragma unroll
             for (int b2 = 0; b2 < 2; ++b2) {
+                uint32_t tmin = kGatedOut;   // minimum score of the row over the tile
 #pragma unroll
                 for (int c = 0; c < kSN / 32; ++c) {
                     uint32_t v[32];
@@ -307,6 +312,8 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
                                                     ? (uint32_t)(qp_b + sp_s[32 * c + j + 1] - 2 * d1)
                                                     : (uint32_t)kGatedOut;
                             pk[j >> 1] = (h0 & 0xffffu) | (h1 << 16);
+                            if (sb + j < n_sets) tmin = min(tmin, h0);
+                            if (sb + j + 1 < n_sets) tmin = min(tmin, h1);
                         }
                         uint16_t *dst = h + (int64_t)qh[b2] * hs + sb;
                         if (sb + 32 <= n_sets) {
@@ -323,6 +330,7 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
                     }
                     __syncwarp();
                 }
+                if (bmin && qh[b2] >= 0) bmin[(int64_t)qh[b2] * n_blk + st] = (uint16_t)tmin;
             }
             tc_fence_before();
             __syncwarp();
@@ -391,7 +399,7 @@ cudaError_t launch_expand_q(const uint32_t *sq, int n_q, int W, uint8_t *q8, int
 cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
                             const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
                             const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
-                            cudaStream_t st) {
+                            cudaStream_t st, uint16_t *bmin) {
     if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
     const int QP = (n_q + 2 * kQM - 1) / (2 * kQM);
     cudaError_t e = cudaFuncSetAttribute(k_scan_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -403,7 +411,8 @@ cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t
     if (grid > n_tiles) grid = n_tiles;
     k_scan_mma<<<(unsigned)grid, kThreads, kSmemBytes, st>>>(sketch, spop, n_sets, W, gate, NW,
                                                              gate_mode, q8, qpop, n_q, QP, h,
-                                                             hs, err);
+                                                             hs, bmin, (n_sets + kSN - 1) / kSN,
+                                                             err);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,13 @@
 //   4. per query: exclusive scans over chunks                     (k_offsets)
 //   5. stable compaction in id order                              (k_write)
 // The result lists the C' candidate ids in ascending id order, -1 padded.
+//
+// With the minimum score of every block of kSelBlock sets (written by the scan),
+// the passes read only blocks that can hold a candidate.  k_bound takes U = the
+// C-th smallest block minimum: C blocks each hold a set with h <= U, so
+// H* <= U, and a block whose minimum exceeds U (for k_hist) or H* (for k_count
+// and k_write) holds no candidate and no score the threshold depends on.  With
+// fewer than C blocks in F1 there is no bound and every such block is read.
 #include <mutex>
 
 #include "block_util.cuh"
@@ -22,29 +29,93 @@ namespace {
 
 constexpr int kSelThreads = 256;
 
+// U per query: the C-th smallest block minimum below kGatedOut, or kGatedOut - 1
+// (every block of F1) when fewer than C blocks hold a set of F1
+__global__ void __launch_bounds__(kSelThreads)
+k_bound(const uint16_t *__restrict__ bmin, int64_t n_blk, int m, int C,
+        int32_t *__restrict__ bound) {
+    extern __shared__ uint32_t sh[];   // m + 1 bins
+    __shared__ int scan_sh[kSelThreads / 32 + 1];
+    __shared__ int res;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    for (int b = tid; b <= m; b += kSelThreads) sh[b] = 0;
+    if (tid == 0) res = (int)kGatedOut - 1;
+    __syncthreads();
+    const uint16_t *bq = bmin + (int64_t)q * n_blk;
+    for (int64_t b = tid; b < n_blk; b += kSelThreads) {
+        const int v = bq[b];
+        if (v <= m) atomicAdd(&sh[v], 1u);
+    }
+    __syncthreads();
+    const int nb = m + 1;
+    const int B = (nb + kSelThreads - 1) / kSelThreads;
+    const int b0 = tid * B, b1 = min(nb, b0 + B);
+    int s = 0;
+    for (int b = b0; b < b1; ++b) s += (int)sh[b];
+    int tot;
+    const int excl = block_excl_scan<kSelThreads>(s, scan_sh, &tot);
+    if (tot >= C && excl < C && excl + s >= C) {
+        int cum = excl;
+        for (int b = b0; b < b1; ++b) {
+            cum += (int)sh[b];
+            if (cum >= C) {
+                res = b;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) bound[q] = res;
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_hist(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs, int m,
+       const uint16_t *__restrict__ bmin, const int32_t *__restrict__ bound,
        uint32_t *__restrict__ hist) {
     extern __shared__ uint32_t sh[];   // m + 1 bins
-    const int q = blockIdx.y;
+    constexpr int kBlkPerChunk = kSelChunk / kSelBlock;
+    __shared__ int act[kBlkPerChunk];
+    __shared__ int n_act;
+    const int q = blockIdx.y, tid = threadIdx.x, lane = tid & 31;
     const int64_t c0 = (int64_t)blockIdx.x * kSelChunk;
     const int64_t end = c0 + kSelChunk < n_sets ? c0 + kSelChunk : n_sets;
-    for (int b = threadIdx.x; b <= m; b += kSelThreads) sh[b] = 0;
+    const int nb = (int)((end - c0 + kSelBlock - 1) / kSelBlock);
+    const int64_t n_blk = (n_sets + kSelBlock - 1) / kSelBlock;
+    const uint16_t *bq = bmin ? bmin + (int64_t)q * n_blk + c0 / kSelBlock : nullptr;
+    const int U = bmin ? bound[q] : 0xFFFF;
+    for (int b = tid; b <= m; b += kSelThreads) sh[b] = 0;
+    if (tid < 32) {
+        // the chunk's blocks that can hold a score at or below U, in order
+        int base = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const bool a = b < nb && (!bq || (int)bq[b] <= U);
+            const uint32_t bal = __ballot_sync(0xffffffffu, a);
+            if (a) act[base + __popc(bal & ((1u << lane) - 1u))] = b;
+            base += __popc(bal);
+        }
+        if (lane == 0) n_act = base;
+    }
     __syncthreads();
     const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
-#pragma unroll 4
-    for (int64_t i8 = c0 / 8 + threadIdx.x; i8 * 8 < end; i8 += kSelThreads) {
-        const uint4 v = row4[i8];
+    // half a warp per block: 16 lanes x 8 scores
+    const int hw = tid >> 4, hl = tid & 15;
+    const int na = n_act;
+#pragma unroll 2
+    for (int i = hw; i < na; i += kSelThreads / 16) {
+        const int64_t s0 = c0 + (int64_t)act[i] * kSelBlock + hl * 8;
+        if (s0 >= end) continue;
+        const uint4 v = row4[s0 / 8];
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t val = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
-            if (i8 * 8 + e < end && val != kGatedOut) atomicAdd(&sh[val], 1u);
+            if (s0 + e < end && val != kGatedOut) atomicAdd(&sh[val], 1u);
         }
     }
     __syncthreads();
     uint32_t *hq = hist + (int64_t)q * (m + 1);
-    for (int b = threadIdx.x; b <= m; b += kSelThreads)
+    for (int b = tid; b <= m; b += kSelThreads)
         if (sh[b]) atomicAdd(&hq[b], sh[b]);
 }
 
@@ -101,20 +172,53 @@ __device__ __forceinline__ void sel_range(int64_t n_sets, int warp, int64_t &w0,
     w1 = w0 + kSelSpan < chunk_end ? w0 + kSelSpan : chunk_end;
 }
 
+static_assert(kSelSpan / kSelBlock <= 32, "a warp's blocks fit one ballot");
+
+// bit i set: block i of the warp's range [w0, w1) can hold a score <= H
+__device__ __forceinline__ uint32_t active_blocks(const uint16_t *bq, int64_t w0, int64_t w1,
+                                                  int H) {
+    const int lane = threadIdx.x & 31;
+    const int nb = w1 > w0 ? (int)((w1 - w0 + kSelBlock - 1) / kSelBlock) : 0;
+    const bool a = lane < nb && (!bq || (int)bq[w0 / kSelBlock + lane] <= H);
+    return __ballot_sync(0xffffffffu, a);
+}
+
+// the next two active blocks, in order: lanes 0-15 take the first, 16-31 the second
+// (-1 when there is none); returns false when none is left
+__device__ __forceinline__ bool next_pair(uint32_t &act, int &mine) {
+    if (!act) return false;
+    const int b0 = __ffs(act) - 1;
+    act &= act - 1;
+    int b1 = -1;
+    if (act) {
+        b1 = __ffs(act) - 1;
+        act &= act - 1;
+    }
+    mine = (threadIdx.x & 16) ? b1 : b0;
+    return true;
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
-        const int32_t *__restrict__ thr, int32_t *__restrict__ ranges) {
+        const int32_t *__restrict__ thr, const uint16_t *__restrict__ bmin,
+        int32_t *__restrict__ ranges) {
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int H = thr[q * 4];
+    const int64_t n_blk = (n_sets + kSelBlock - 1) / kSelBlock;
+    const uint16_t *bq = bmin ? bmin + (int64_t)q * n_blk : nullptr;
     int64_t w0, w1;
     sel_range(n_sets, warp, w0, w1);
     int lt = 0, eq = 0;
     if (H >= 0) {
         const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
-#pragma unroll 4
-        for (int64_t i0 = w0 + lane * 8; i0 < w1; i0 += 256) {
+        // blocks whose minimum is above H* count nothing
+        uint32_t act = active_blocks(bq, w0, w1, H);
+        int mine;
+        while (next_pair(act, mine)) {
+            const int64_t i0 = w0 + (int64_t)mine * kSelBlock + (lane & 15) * 8;
+            if (mine < 0 || i0 >= w1) continue;
             const uint4 v = row4[i0 / 8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -183,7 +287,7 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
 __global__ void __launch_bounds__(kSelThreads)
 k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
         const int32_t *__restrict__ thr, const int32_t *__restrict__ ranges, int C,
-        int32_t *__restrict__ cand) {
+        const uint16_t *__restrict__ bmin, int32_t *__restrict__ cand) {
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
     const int H = thr[q * 4];
@@ -196,10 +300,17 @@ k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
     if (o[0] == 0 && (o[1] == 0 || o[2] >= take)) return;   // nothing selected in this range
     int rank = o[2], pos = o[3];
     const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+    const int64_t n_blk = (n_sets + kSelBlock - 1) / kSelBlock;
+    const uint16_t *bq = bmin ? bmin + (int64_t)q * n_blk : nullptr;
     int32_t *out = cand + (int64_t)q * C;
-    for (int64_t i0 = w0 + lane * 8; i0 - lane * 8 < w1; i0 += 256) {
+    // blocks whose minimum is above H* hold no candidate; the others two at a time, in
+    // id order over the lanes
+    uint32_t act = active_blocks(bq, w0, w1, H);
+    int mine;
+    while (next_pair(act, mine)) {
+        const int64_t i0 = w0 + (int64_t)(mine < 0 ? 0 : mine) * kSelBlock + (lane & 15) * 8;
         int val[8];
-        if (i0 < w1) {
+        if (mine >= 0 && i0 < w1) {
             const uint4 v = row4[i0 / 8];
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -239,8 +350,9 @@ k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
 
 cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, int n_q, int C,
                           uint32_t *hist, int32_t *thr, int32_t *chunk, int32_t *cand,
-                          cudaStream_t st) {
+                          cudaStream_t st, const uint16_t *bmin, int32_t *bound) {
     if (n_q <= 0) return cudaSuccess;
+    if (bmin && !bound) return cudaErrorInvalidValue;
     const int n_chunks = (int)((n_sets + kSelChunk - 1) / kSelChunk);
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n_q * (m + 1), st);
     if (e != cudaSuccess) return e;
@@ -248,11 +360,17 @@ cudaError_t launch_select(const uint16_t *h, int64_t n_sets, int64_t hs, int m, 
     e = cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 g2(n_chunks, n_q);
-    k_hist<<<g2, kSelThreads, smem, st>>>(h, n_sets, hs, m, hist);
+    if (bmin) {
+        e = cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_bound<<<n_q, kSelThreads, smem, st>>>(bmin, (n_sets + kSelBlock - 1) / kSelBlock, m, C,
+                                                bound);
+    }
+    k_hist<<<g2, kSelThreads, smem, st>>>(h, n_sets, hs, m, bmin, bound, hist);
     k_thresh<<<n_q, kSelThreads, 0, st>>>(hist, m, C, thr, cand);
-    k_count<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk);
+    k_count<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, bmin, chunk);
     k_offsets<<<n_q, kSelThreads, 0, st>>>(thr, n_chunks * kSelWarps, chunk);
-    k_write<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk, C, cand);
+    k_write<<<g2, kSelThreads, 0, st>>>(h, n_sets, hs, thr, chunk, C, bmin, cand);
     return cudaGetLastError();
 }
 

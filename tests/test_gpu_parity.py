@@ -147,11 +147,11 @@ def test_scan_forms_agree(bv, orc, n_sets, nq, m, L, A, M):
 
 def test_profile_stages_and_launch_count(bv, small):
     """The profiler sees every stage and counts the kernels each form launches:
-    encode, prep, gate, [FP8 query operand], scan, 5 select kernels, refine,
-    [re-score], top-k."""
+    encode, prep, gate, [FP8 query operand], scan, [select bound], 5 select kernels,
+    refine, [re-score], top-k."""
     w = small.w
     qv = small.qv_cuda
-    for popc, want in ((False, 12), (True, 11)):
+    for popc, want in ((False, 13), (True, 11)):
         bv.bvss_profile_enable(small.ix, True)
         bv.bvss_profile_read(small.ix, reset=True)
         bv.bvss_query(small.ix, qv, w["q_offsets"], k=10, C=200, A=3, M=1, popc_scan=popc)
@@ -175,6 +175,22 @@ def test_query_results_without_trace_match(bv, small):
     bv.bvss_query(small.ix, hq, w["q_offsets"], k=10, C=s["C"], A=3, M=1, out_ids=hi,
                   out_dist=hd)
     assert torch.equal(hi, ids.cpu()) and torch.equal(hd, dist.cpu())
+
+
+@pytest.mark.parametrize("C,A,M", [(1, 3, 1), (10, 3, 1), (100, 3, 0), (157, 3, 1), (158, 3, 0),
+                                   (500, 1, 1), (40, 2, 2)])
+def test_select_skips_blocks_exactly(bv, orc, C, A, M):
+    # 20,000 sets = 157 blocks of 128: with C below the number of blocks in F1 the select
+    # reads only blocks whose minimum score can reach the threshold; the candidate lists
+    # must still equal the oracle's (ties at the threshold broken by id), and the
+    # popcount scan (no block minima, every block read) must agree
+    w = _workload(20000, 2, 6, 64, 16, 6, 2, 8, 512, 8, seed=27)
+    case = Case(bv, orc, w, 8)
+    _check_query(bv, orc, case, k=1, C=C, A=A, M=M)
+    ta = bv.bvss_query_trace(case.ix, case.qv_cuda, w["q_offsets"], k=1, C=C, A=A, M=M)
+    tb = bv.bvss_query_trace(case.ix, case.qv_cuda, w["q_offsets"], k=1, C=C, A=A, M=M,
+                             popc_scan=True)
+    assert torch.equal(ta["cand"], tb["cand"]) and torch.equal(ta["n_cand"], tb["n_cand"])
 
 
 @pytest.mark.parametrize("A,M,C", [(1, 1, 200), (3, 0, 200), (3, 2, 50), (32, 1, 200),
