@@ -266,11 +266,11 @@ class Plan:
         nl = _c_i64()
         _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
         return dict(scan={1: "tensor", 2: "popcount", 0: "alg2"}[kn[0]], cand_cta=kn[1],
-                    lag=kn[2], mq=kn[3], launches=nl.value)
+                    stages=kn[2], mq=kn[3], launches=nl.value)
 
-    def set_knobs(self, scan=0, cand_cta=0, lag=0):
+    def set_knobs(self, scan=0, cand_cta=0, stages=0):
         """Pin the tuner's choices (0 = default); scan 1 = tensor-core, 2 = popcount."""
-        kn = (_c_i32 * 3)(scan, cand_cta, lag)
+        kn = (_c_i32 * 3)(scan, cand_cta, stages)
         _check(load().bvss_plan_set_knobs(self.handle, kn))
 
     def close(self):

@@ -301,7 +301,7 @@ cudaEvent_t *prof_reserve(bvss_index *ix) {
 struct Knobs {
     int scan = 0;       // 1: tensor-core sketch scan, 2: popcount scan, 0: by the search flags
     int cand_cta = 0;   // tensor-core refine: candidates per CTA (0: 512)
-    int lag = 0;        // tensor-core refine: stages of copies in flight (0: by the ring depth)
+    int stages = 0;     // tensor-core refine: depth of the copy ring (0: the most that fit)
 };
 
 int check_search(const bvss_index *ix, const bvss_search *s) {
@@ -395,7 +395,7 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     const bool mma = fast && refine_mma_supported(d, b.max_mq);
     if (mma)
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, ix->vec16, ix->vnorm16, ix->set_off,
-                                  d, w.cand, w.thr, C, w.pair, ix->err, st, kn.cand_cta, kn.lag));
+                                  d, w.cand, w.thr, C, w.pair, ix->err, st, kn.cand_cta, kn.stages));
     else if (refine_tma_supported(d, b.max_mq))
         BVSS_CU(launch_refine_tma(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
@@ -986,10 +986,9 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
         rc = sweep(&Knobs::cand_cta, ctas, 3);
     }
     if (!rc && mma) {
-        int lags[8], nl = 0;
-        for (int l = 4; l <= 8; ++l)
-            if (l < ns) lags[nl++] = l;
-        rc = sweep(&Knobs::lag, lags, nl);
+        int rings[4], nr = 0;
+        for (int r = ns; r >= 4 && nr < 3; r -= 2) rings[nr++] = r;
+        rc = sweep(&Knobs::stages, rings, nr);
     }
     p->kn = best;
     const int rc2 = plan_capture(p);
@@ -1008,7 +1007,7 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
         knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
                                           : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
-        knobs[2] = mma ? refine_mma_lag(d, p->max_qset, p->kn.lag) : 0;
+        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
     }
     if (launches) *launches = p->launches;
@@ -1021,11 +1020,11 @@ int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs) {
     if (knobs[0] < 0 || knobs[0] > 2) return fail(BVSS_EINVAL, "scan = %d: need 0, 1 or 2", knobs[0]);
     if (knobs[1] < 0 || knobs[1] > 512)
         return fail(BVSS_EINVAL, "candidates per CTA = %d: need 0..512", knobs[1]);
-    if (knobs[2] < 0) return fail(BVSS_EINVAL, "lag = %d: need >= 0", knobs[2]);
+    if (knobs[2] < 0) return fail(BVSS_EINVAL, "stages = %d: need >= 0", knobs[2]);
     const Knobs old = p->kn;
     p->kn.scan = knobs[0];
     p->kn.cand_cta = knobs[1];
-    p->kn.lag = knobs[2];
+    p->kn.stages = knobs[2];
     const int rc = plan_capture(p);
     if (rc) p->kn = old;
     return rc;

@@ -181,19 +181,17 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
                            cudaStream_t st);
 // records each candidate's critical (query vector, row) pair; launch_rescore then
 // writes its FP32 distance as the candidate's distance
-// cand_cta: candidates per CTA (1..512, 0 = 512); lag: stages of copies a producer keeps in
-// flight, 4..8 and below the ring depth (otherwise, and for 0, the default for the ring).
+// cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy ring (4 up to
+// the most that fit; otherwise, and for 0, the most that fit).
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
-                              int cand_cta = 0, int lag = 0);
-// stages of the refine's ring for this dimension and batch (0 if the kernel cannot run),
-// and the copy lag used when none is asked for
+                              int cand_cta = 0, int stages = 0);
+// stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
 int refine_mma_stages(int d, int max_mq);
-int refine_mma_default_lag(int d, int max_mq);
-// the lag a launch with this requested lag runs with (0 if the kernel cannot run)
-int refine_mma_lag(int d, int max_mq, int lag);
+// the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
+int refine_mma_ring(int d, int max_mq, int stages);
 cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
                            const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
                            int C, const int2 *pair, float *cand_dist, cudaStream_t st);

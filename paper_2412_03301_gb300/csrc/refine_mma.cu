@@ -13,18 +13,21 @@
 // Warp roles (no block-wide barrier between set-up and tear-down):
 //   warps 4-7  producers: gather the tile rows one 64-dimension block at a
 //              time with 16-byte cp.async copies straight into the swizzled
-//              stage (8 lanes per 128-byte row segment, so copies coalesce; a
-//              ring of 5-10 stages, 4-8 kept in flight), then signal the
-//              stage's mbarrier;
-//   warp 8     one thread issues the MMAs (K = 16 each) and commits them to the
-//              stage's "empty" mbarrier and, per tile, to a "full" mbarrier of
-//              one of two TMEM accumulators;
+//              stage (8 lanes per 128-byte row segment, so copies coalesce),
+//              each lane's copies arriving on the stage's mbarrier when they
+//              land (cp.async.mbarrier.arrive), so producers never wait for
+//              their own copies and the whole ring (4-10 stages) is in flight;
+//   warp 8     one thread waits for a stage, fences the producers' copies
+//              into the async proxy, issues the MMAs (K = 16 each) and
+//              commits them to the stage's "empty" mbarrier and, per tile, to
+//              a "full" mbarrier of one of two TMEM accumulators;
 //   warps 0-3  epilogue.  Row phase (lane = row 32w + lane): squared
 //              distances |q|^2 + |v|^2 - 2 q.v to all query vectors from
-//              MQ / 32 tensor-memory loads, their minimum with its arg-min (the row's
-//              key), the distances written to a swizzled shared-memory block.
-//              After a barrier over the four warps, column phase (lane = query
-//              vector, and lane + 32 when MQ = 64): warp w walks, whole, the candidates whose first row in
+//              MQ / 32 tensor-memory loads, their minimum with its arg-min
+//              (the row's key), the distances written to a swizzled
+//              shared-memory block.  After a barrier over the four warps,
+//              column phase (lane = query vector, and lane + 32 when
+//              MQ = 64): warp w walks, whole, the candidates whose first row in
 //              the tile lies in rows 32w..32w+31, keeping per query vector the
 //              minimum over the candidate's rows (with the row) and the maximum
 //              of the rows' keys; when a candidate ends, the larger of the two
@@ -95,10 +98,7 @@ __host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
     return L;
 }
 
-// stages a producer keeps in flight for a ring of ns (it holds that many arrivals back)
-inline int lag_for(int ns) { return ns >= 6 ? 5 : 4; }
-constexpr int kMinLag = 4, kMaxLag = 8;   // instantiated lags
-inline bool refine_lag_valid(int lag, int ns) { return lag >= kMinLag && lag <= kMaxLag && lag < ns; }
+constexpr int kMinNS = 4;   // smallest ring a caller may ask for
 
 // most stages that fit, at least 5
 inline int pick_stages(int d, int MQ) {
@@ -128,7 +128,7 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | low;
 }
 
-template <int MQ, int LAG>
+template <int MQ>
 __global__ void __launch_bounds__(kThreads, 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
@@ -323,18 +323,10 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     if (src[k]) cp_async16(dst + sw128_off(pg + 16 * k, pc), src[k] + kb * kKB);
-                cp_async_commit();
-                if (u >= LAG) {
-                    cp_async_wait<LAG>();
-                    fence_proxy_async();
-                    mbar_arrive(&full[(u - LAG) % ns]);
-                }
+                cp_async_mbar_arrive(&full[s]);   // fires when these copies have landed
             }
         }
         cp_async_wait<0>();
-        fence_proxy_async();
-        if (ok)
-            for (int v = total > LAG ? total - LAG : 0; v < total; ++v) mbar_arrive(&full[v % ns]);
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
@@ -351,6 +343,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     const int u = t * KB + kb, s = u % ns;
                     ok = wait_or_abort(&full[s], (uint32_t)((u / ns) & 1), abort_flag, err);
                     if (!ok) break;
+                    fence_proxy_async();   // the producers' copies, seen by the tensor core
                     tc_fence_after();
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -625,37 +618,24 @@ int refine_mma_stages(int d, int max_mq) {
     return refine_mma_supported(d, max_mq) ? pick_stages(d, mq_for(max_mq)) : 0;
 }
 
-int refine_mma_default_lag(int d, int max_mq) {
+int refine_mma_ring(int d, int max_mq, int stages) {
     const int ns = refine_mma_stages(d, max_mq);
-    return ns ? lag_for(ns) : 0;
-}
-
-int refine_mma_lag(int d, int max_mq, int lag) {
-    const int ns = refine_mma_stages(d, max_mq);
-    if (!ns) return 0;
-    return refine_lag_valid(lag, ns) ? lag : lag_for(ns);
+    return stages >= kMinNS && stages < ns ? stages : ns;
 }
 
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
-                              int cand_cta, int lag) {
+                              int cand_cta, int stages) {
     if (n_q <= 0) return cudaSuccess;
     if (!refine_mma_supported(d, max_mq)) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
-    const int ns = pick_stages(d, MQ);
+    const int ns = refine_mma_ring(d, max_mq, stages);
     const Layout Lo = make_layout(d, ns, MQ);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
-    // a producer holds `lag` arrivals back, so the ring needs more stages than that
-    if (!refine_lag_valid(lag, ns)) lag = lag_for(ns);
-    using Kern = decltype(&k_refine_mma<32, 4>);
-    static const Kern k32[] = {k_refine_mma<32, 4>, k_refine_mma<32, 5>, k_refine_mma<32, 6>,
-                               k_refine_mma<32, 7>, k_refine_mma<32, 8>};
-    static const Kern k64[] = {k_refine_mma<64, 4>, k_refine_mma<64, 5>, k_refine_mma<64, 6>,
-                               k_refine_mma<64, 7>, k_refine_mma<64, 8>};
-    const Kern kern = (MQ == 32 ? k32 : k64)[lag - kMinLag];
+    const auto kern = MQ == 32 ? k_refine_mma<32> : k_refine_mma<64>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,

@@ -97,7 +97,7 @@ def test_tuned_plan_gives_the_same_results(bv, orc, serving):
     assert ms > 0
     kn = plan.info()
     assert kn["scan"] in ("tensor", "popcount") and kn["cand_cta"] in (128, 256, 512)
-    assert 4 <= kn["lag"] <= 8 and kn["launches"] >= 8
+    assert 4 <= kn["stages"] <= 10 and kn["launches"] >= 8
     ids1, dist1 = plan.launch()
     bv.bvss_sync(ix)
     assert torch.equal(ids0, ids1) and torch.equal(dist0, dist1)
