@@ -17,7 +17,9 @@ namespace {
 
 constexpr int kEncThreads = 128;   // divides every valid m (m % 128 == 0)
 constexpr int kEncWide = 256;      // used when it divides m
-constexpr int kEncRepWords = 12288; // 48 KB for the copies of the vector
+constexpr int kEncRepWords = 3072;  // 12 KB for the copies of the vector: 8 at d = 384,
+                                    // which keeps 6 CTAs per SM (measured faster than 32
+                                    // conflict-free copies at 3 CTAs per SM)
 
 // eight 16-byte read-only loads issued back to back (one asm statement, so the
 // compiler cannot interleave their uses and serialise the latencies)
@@ -48,8 +50,9 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
          uint16_t *__restrict__ pos, uint32_t *__restrict__ mask) {
     extern __shared__ uint32_t sm[];
     // rep (a power of two <= 32) copies of the vector, interleaved: value k of copy c
-    // at xs[k * rep + c].  Lane l reads copy l % rep, so with rep = 32 every lane of a
-    // warp reads its own bank and the random gathers of W's rows never conflict.
+    // at xs[k * rep + c].  Lane l reads copy l % rep, so lanes l and l' can only meet in
+    // a bank when l = l' mod rep: with rep = 32 the random gathers of W's rows never
+    // conflict, with rep = 8 at most four lanes share a bank.
     float *xs = reinterpret_cast<float *>(sm);       // dpad * rep floats
     uint32_t *key = sm + dpad * rep;                 // m keys (first: a plain copy of x)
     uint32_t *hist = key + m;                        // 2048 bins
