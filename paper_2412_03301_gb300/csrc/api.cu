@@ -405,7 +405,7 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     ++n;
     if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
     if (mma) {
-        BVSS_CU(launch_rescore(qv, b.qoff, nb, ix->vec, ix->set_off, d, w.cand, w.thr, C, w.pair,
+        BVSS_CU(launch_rescore(qv, b.qoff, nb, ix->vec, ix->n_vec, d, w.thr, C, w.pair,
                                w.cand_dist, st));
         ++n;
     }

@@ -46,7 +46,7 @@ struct Workspace {
     int32_t *bound = nullptr;     // per query: bound on the select threshold  cap_q
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
-    int2 *pair = nullptr;         // (query vector, row) attaining each candidate's value
+    longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
     float *out_dist = nullptr;
     int cap_k = 0;
@@ -186,15 +186,15 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
-                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
+                              const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta = 0, int stages = 0);
 // stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
 int refine_mma_stages(int d, int max_mq);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
 int refine_mma_ring(int d, int max_mq, int stages);
 cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
-                           const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
-                           int C, const int2 *pair, float *cand_dist, cudaStream_t st);
+                           int64_t n_vec, int d, const int32_t *thr, int C,
+                           const longlong2 *pair, float *cand_dist, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf

@@ -134,7 +134,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
              const int64_t *__restrict__ set_off, int d, int ns,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int cpc,
-             int2 *__restrict__ pair, int *__restrict__ err) {
+             longlong2 *__restrict__ pair, int *__restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     const int q = blockIdx.y;
     const int n_sel = thr[q * 4 + 3];
@@ -500,7 +500,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                             pa = (int)(kmax & 0xff);
                             pr = (int)((kmax >> 8) & 0xffffff);
                         }
-                        if (lane == 0) pair[(int64_t)q * C + c0 + c] = make_int2(pa, pr);
+                        // the pair as (query vector, global row of the database vector)
+                        if (lane == 0)
+                            pair[(int64_t)q * C + c0 + c] = make_longlong2(pa, grow0[c] + pr);
                     } else {
                         // continues into the next tile
 #pragma unroll
@@ -522,24 +524,24 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
 }
 
 // distance of each candidate's recorded pair, directly in FP32; one warp per
-// candidate, all of the row's loads issued before the first use
+// candidate.  The pair holds the database vector's global row, so the row's loads
+// follow a single dependent load; all of them are issued before the first use.
 __global__ void __launch_bounds__(256)
 k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-          const float *__restrict__ vec, const int64_t *__restrict__ set_off,
-          const int32_t *__restrict__ cand, const int32_t *__restrict__ thr,
-          const int2 *__restrict__ pair, int C, int d, float *__restrict__ cand_dist) {
+          const float *__restrict__ vec, int64_t n_vec, const int32_t *__restrict__ thr,
+          const longlong2 *__restrict__ pair, int C, int d, float *__restrict__ cand_dist) {
     const int q = blockIdx.y;
     const int n_sel = thr[q * 4 + 3];
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= n_sel) return;
-    int2 pr = pair[(int64_t)q * C + c];
-    const int64_t id = cand[(int64_t)q * C + c];
-    // keep the pair inside its sets whatever the array holds
-    pr.x = min(max(pr.x, 0), (int)(qoff[q + 1] - qoff[q]) - 1);
-    pr.y = min(max(pr.y, 0), (int)(set_off[id + 1] - set_off[id]) - 1);
-    const float4 *x4 = reinterpret_cast<const float4 *>(qvec + (qoff[q] + pr.x) * d);
-    const float4 *y4 = reinterpret_cast<const float4 *>(vec + (set_off[id] + pr.y) * d);
+    const longlong2 pr = pair[(int64_t)q * C + c];
+    // keep the pair inside the arrays whatever they hold
+    const int64_t a0 = qoff[q], mq = qoff[q + 1] - a0;
+    const int64_t qa = a0 + min(max(pr.x, 0ll), (long long)mq - 1);
+    const int64_t row = min(max(pr.y, 0ll), (long long)n_vec - 1);
+    const float4 *x4 = reinterpret_cast<const float4 *>(qvec + qa * d);
+    const float4 *y4 = reinterpret_cast<const float4 *>(vec + row * d);
     const int n4 = d / 4;
     float s = 0.0f;
     for (int k0 = 0; k0 < n4; k0 += 32 * 4) {
@@ -626,7 +628,7 @@ int refine_mma_ring(int d, int max_mq, int stages) {
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const __nv_bfloat16 *vec16, const float *vnorm16,
                               const int64_t *set_off, int d, const int32_t *cand,
-                              const int32_t *thr, int C, int2 *pair, int *err, cudaStream_t st,
+                              const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta, int stages) {
     if (n_q <= 0) return cudaSuccess;
     if (!refine_mma_supported(d, max_mq)) return cudaErrorInvalidValue;
@@ -644,11 +646,11 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
 }
 
 cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
-                           const int64_t *set_off, int d, const int32_t *cand, const int32_t *thr,
-                           int C, const int2 *pair, float *cand_dist, cudaStream_t st) {
+                           int64_t n_vec, int d, const int32_t *thr, int C,
+                           const longlong2 *pair, float *cand_dist, cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
-    k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, set_off, cand, thr, pair,
-                                                       C, d, cand_dist);
+    k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, n_vec, thr, pair, C, d,
+                                                       cand_dist);
     return cudaGetLastError();
 }
 

@@ -85,13 +85,21 @@ k_hist(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs, int m,
     const int U = bmin ? bound[q] : 0xFFFF;
     for (int b = tid; b <= m; b += kSelThreads) sh[b] = 0;
     if (tid < 32) {
-        // the chunk's blocks that can hold a score at or below U, in order
+        // the chunk's blocks that can hold a score at or below U, in order (the minima
+        // are loaded together, before the first comparison)
+        constexpr int kR = kBlkPerChunk / 32;
+        int bmv[kR];
+#pragma unroll
+        for (int i = 0; i < kR; ++i) {
+            const int b = 32 * i + lane;
+            bmv[i] = b < nb ? (bq ? (int)bq[b] : 0) : 0x10000;
+        }
         int base = 0;
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-            const int b = b0 + lane;
-            const bool a = b < nb && (!bq || (int)bq[b] <= U);
+#pragma unroll
+        for (int i = 0; i < kR; ++i) {
+            const bool a = bmv[i] <= U;
             const uint32_t bal = __ballot_sync(0xffffffffu, a);
-            if (a) act[base + __popc(bal & ((1u << lane) - 1u))] = b;
+            if (a) act[base + __popc(bal & ((1u << lane) - 1u))] = 32 * i + lane;
             base += __popc(bal);
         }
         if (lane == 0) n_act = base;
@@ -174,13 +182,18 @@ __device__ __forceinline__ void sel_range(int64_t n_sets, int warp, int64_t &w0,
 
 static_assert(kSelSpan / kSelBlock <= 32, "a warp's blocks fit one ballot");
 
-// bit i set: block i of the warp's range [w0, w1) can hold a score <= H
-__device__ __forceinline__ uint32_t active_blocks(const uint16_t *bq, int64_t w0, int64_t w1,
-                                                  int H) {
+// minimum score of block `lane` of the warp's range [w0, w1) (0 without block minima,
+// 0xFFFF past the range); loaded before the threshold is known
+__device__ __forceinline__ int lane_block_min(const uint16_t *bq, int64_t w0, int64_t w1) {
     const int lane = threadIdx.x & 31;
     const int nb = w1 > w0 ? (int)((w1 - w0 + kSelBlock - 1) / kSelBlock) : 0;
-    const bool a = lane < nb && (!bq || (int)bq[w0 / kSelBlock + lane] <= H);
-    return __ballot_sync(0xffffffffu, a);
+    if (lane >= nb) return 0x10000;
+    return bq ? (int)bq[w0 / kSelBlock + lane] : 0;
+}
+
+// bit i set: block i of the warp's range can hold a score <= H
+__device__ __forceinline__ uint32_t active_blocks(int bm, int H) {
+    return __ballot_sync(0xffffffffu, bm <= H);
 }
 
 // the next two active blocks, in order: lanes 0-15 take the first, 16-31 the second
@@ -210,11 +223,12 @@ k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
     const uint16_t *bq = bmin ? bmin + (int64_t)q * n_blk : nullptr;
     int64_t w0, w1;
     sel_range(n_sets, warp, w0, w1);
+    const int bm = lane_block_min(bq, w0, w1);
     int lt = 0, eq = 0;
     if (H >= 0) {
         const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
         // blocks whose minimum is above H* count nothing
-        uint32_t act = active_blocks(bq, w0, w1, H);
+        uint32_t act = active_blocks(bm, H);
         int mine;
         while (next_pair(act, mine)) {
             const int64_t i0 = w0 + (int64_t)mine * kSelBlock + (lane & 15) * 8;
@@ -290,22 +304,25 @@ k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
         const uint16_t *__restrict__ bmin, int32_t *__restrict__ cand) {
     const int q = blockIdx.y;
     const int n_chunks = gridDim.x;
-    const int H = thr[q * 4];
-    if (H < 0) return;   // uniform over the CTA
-    const int take = thr[q * 4 + 2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t w0, w1;
     sel_range(n_sets, warp, w0, w1);
+    // the threshold, this range's record and the block minima, all in flight together
+    const int H = thr[q * 4];
+    const int take = thr[q * 4 + 2];
     const int32_t *o = ranges + (((int64_t)q * n_chunks + blockIdx.x) * kSelWarps + warp) * 4;
-    if (o[0] == 0 && (o[1] == 0 || o[2] >= take)) return;   // nothing selected in this range
-    int rank = o[2], pos = o[3];
-    const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
+    const int4 rec = *reinterpret_cast<const int4 *>(o);
     const int64_t n_blk = (n_sets + kSelBlock - 1) / kSelBlock;
     const uint16_t *bq = bmin ? bmin + (int64_t)q * n_blk : nullptr;
+    const int bm = lane_block_min(bq, w0, w1);
+    if (H < 0) return;   // uniform over the CTA
+    if (rec.x == 0 && (rec.y == 0 || rec.z >= take)) return;   // nothing selected in this range
+    int rank = rec.z, pos = rec.w;
+    const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
     int32_t *out = cand + (int64_t)q * C;
     // blocks whose minimum is above H* hold no candidate; the others two at a time, in
     // id order over the lanes
-    uint32_t act = active_blocks(bq, w0, w1, H);
+    uint32_t act = active_blocks(bm, H);
     int mine;
     while (next_pair(act, mine)) {
         const int64_t i0 = w0 + (int64_t)(mine < 0 ? 0 : mine) * kSelBlock + (lane & 15) * 8;
