@@ -65,6 +65,9 @@ extern "C" {
 
 /* Build parameters (Def. 7 and Alg. 6's Theta minus the search knobs). */
 /* bvss_params.flags */
+#define BVSS_BUILD_FP8 2    /* also keep an FP8 E4M3 copy (1 byte per value, one FP32 scale per
+                               vector: its largest magnitude maps to 448) for BVSS_SEARCH_FP8;
+                               needs d % 128 == 0 */
 #define BVSS_BUILD_BF16 1   /* also keep a BF16 copy of the vectors (2 bytes per value) for
                                the tensor-core refine of BVSS_SEARCH_FAST; needs d % 64 == 0 */
 
@@ -73,7 +76,7 @@ typedef struct bvss_params {
     int32_t m;       /* code length b = Bloom filter length; multiple of 128, <= BVSS_MAX_M */
     int32_t fanin;   /* F: input dims summed by each output of W, 1..min(d, BVSS_MAX_FANIN) */
     int32_t wta_l;   /* L_wta: winners kept by WTA, 1..min(m, BVSS_MAX_L) */
-    int32_t flags;   /* 0 or BVSS_BUILD_BF16 */
+    int32_t flags;   /* 0 or an OR of BVSS_BUILD_BF16 and BVSS_BUILD_FP8 */
     int32_t reserved[3];
 } bvss_params;
 
@@ -97,13 +100,24 @@ typedef struct bvss_params {
                                (Haus^H, id); A and M are not used and the trace's cq, sq and plist
                                are not written (its h holds Haus^H).  Query sets of at most 32
                                vectors.  Combines with BVSS_SEARCH_FAST */
+#define BVSS_SEARCH_FP8 8   /* refine on the tensor cores from the FP8 copy (BVSS_BUILD_FP8): the
+                               query vectors are scaled and rounded to E4M3 the same way, the
+                               squared distances are |q|^2 + |v|^2 - 2 s_q s_v (q8 . v8) of the
+                               scaled values, and each candidate's distance is the FP32 distance
+                               of the pair that attains its Hausdorff value there.  Approximate:
+                               FP8 rounding (relative error up to 2^-4 per value) can pick another
+                               pair, so a distance can be off by about twice the rounding error
+                               of the vectors involved, and the candidate order with it.  Batches
+                               with a query set of more than 32 vectors use the BF16 copy if the
+                               index has one, else the FP32 refine */
 
 typedef struct bvss_search {
     int32_t k;      /* results per query set, >= 1 */
     int32_t C;      /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
-    int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2 */
+    int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2,
+                       BVSS_SEARCH_FP8 */
     int32_t reserved;
 } bvss_search;
 

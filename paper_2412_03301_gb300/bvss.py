@@ -34,9 +34,11 @@ class bvss_search(ctypes.Structure):
 
 
 BVSS_BUILD_BF16 = 1
+BVSS_BUILD_FP8 = 2
 BVSS_SEARCH_FAST = 1
 BVSS_SEARCH_POPC_SCAN = 2
 BVSS_SEARCH_ALG2 = 4
+BVSS_SEARCH_FP8 = 8
 
 
 class bvss_trace(ctypes.Structure):
@@ -165,7 +167,7 @@ class Index:
 
 
 def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: int,
-               bf16: bool = False, stream=None) -> Index:
+               bf16: bool = False, fp8: bool = False, stream=None) -> Index:
     """Build an index (Alg. 1, 3, 4, 5). vectors: (V, d) float32, host or CUDA."""
     lib = load()
     assert vectors.dtype == torch.float32 and vectors.is_contiguous()
@@ -173,7 +175,7 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
     proj = np.ascontiguousarray(proj, dtype=np.uint16)
     p = bvss_params(d=vectors.shape[1], m=proj.shape[0],
                     fanin=proj.shape[1] if fanin is None else fanin, wta_l=wta_l,
-                    flags=BVSS_BUILD_BF16 if bf16 else 0)
+                    flags=(BVSS_BUILD_BF16 if bf16 else 0) | (BVSS_BUILD_FP8 if fp8 else 0))
     h = ctypes.c_void_p()
     dev = vectors.device if vectors.is_cuda else torch.device("cuda", torch.cuda.current_device())
     with torch.cuda.device(dev):
@@ -183,14 +185,14 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
     return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
 
 
-def _search_flags(fast, popc_scan, alg2=False):
+def _search_flags(fast, popc_scan, alg2=False, fp8=False):
     return ((BVSS_SEARCH_FAST if fast else 0) | (BVSS_SEARCH_POPC_SCAN if popc_scan else 0)
-            | (BVSS_SEARCH_ALG2 if alg2 else 0))
+            | (BVSS_SEARCH_ALG2 if alg2 else 0) | (BVSS_SEARCH_FP8 if fp8 else 0))
 
 
 def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
                M: int = 1, fast: bool = False, popc_scan: bool = False, alg2: bool = False,
-               out_ids=None, out_dist=None, stream=None):
+               fp8: bool = False, out_ids=None, out_dist=None, stream=None):
     """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
 
     q_vectors and the outputs may live on the host or on the index's GPU."""
@@ -202,7 +204,7 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
         out_ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2, fp8))
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -219,7 +221,7 @@ class Plan:
 
     def __init__(self, ix: Index, n_queries: int, max_vectors: int, max_qset: int, *, k: int,
                  C: int, A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
-                 alg2: bool = False, stream=None):
+                 alg2: bool = False, fp8: bool = False, stream=None):
         lib = load()
         dev = ix.device
         self.ix = ix
@@ -228,7 +230,7 @@ class Plan:
         self.q_offsets = torch.arange(n_queries + 1, dtype=torch.int64, device=dev)
         self.ids = torch.empty((n_queries, k), dtype=torch.int64, device=dev)
         self.dist = torch.empty((n_queries, k), dtype=torch.float32, device=dev)
-        s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
+        s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2, fp8))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.bvss_plan_create(ix.handle, ctypes.byref(s), n_queries, max_vectors,
@@ -288,7 +290,7 @@ class Plan:
 
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
                      A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
-                     alg2: bool = False, stream=None):
+                     alg2: bool = False, fp8: bool = False, stream=None):
     """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
 
     Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
@@ -311,7 +313,7 @@ def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C
     tr = bvss_trace(**{name: t[name].data_ptr() for name in t})
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2))
+    s = bvss_search(k=k, C=C, A=A, M=M, flags=_search_flags(fast, popc_scan, alg2, fp8))
     _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                                 _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
     t["ids"] = ids

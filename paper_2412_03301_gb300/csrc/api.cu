@@ -101,6 +101,9 @@ void free_index(bvss_index *ix) {
     dfree(ix->vnorm);
     dfree(ix->vec16);
     dfree(ix->vnorm16);
+    dfree(ix->vec8);
+    dfree(ix->vscale8);
+    dfree(ix->vnorm8);
     dfree(ix->set_off);
     dfree(ix->proj);
     dfree(ix->codes);
@@ -132,9 +135,11 @@ int check_params(const bvss_params *p) {
                     BVSS_MAX_FANIN);
     if (p->wta_l < 1 || p->wta_l > BVSS_MAX_L || p->wta_l > p->m)
         return fail(BVSS_EINVAL, "wta_l = %d: need 1 <= L <= min(m, %d)", p->wta_l, BVSS_MAX_L);
-    if (p->flags & ~BVSS_BUILD_BF16) return fail(BVSS_EINVAL, "unknown build flags");
+    if (p->flags & ~(BVSS_BUILD_BF16 | BVSS_BUILD_FP8)) return fail(BVSS_EINVAL, "unknown build flags");
     if ((p->flags & BVSS_BUILD_BF16) && p->d % 64 != 0)
         return fail(BVSS_EINVAL, "BVSS_BUILD_BF16 needs d %% 64 == 0 (d = %d)", p->d);
+    if ((p->flags & BVSS_BUILD_FP8) && p->d % 128 != 0)
+        return fail(BVSS_EINVAL, "BVSS_BUILD_FP8 needs d %% 128 == 0 (d = %d)", p->d);
     return BVSS_OK;
 }
 
@@ -313,11 +318,22 @@ int check_search(const bvss_index *ix, const bvss_search *s) {
     if ((s->flags & BVSS_SEARCH_ALG2) == 0 && (s->A < 1 || s->A > L || s->A > BVSS_MAX_A))
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
-    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2))
+    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2 | BVSS_SEARCH_FP8))
         return fail(BVSS_EINVAL, "unknown search flags");
     if ((s->flags & BVSS_SEARCH_FAST) && !ix->vec16)
         return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
+    if ((s->flags & BVSS_SEARCH_FP8) && !ix->vec8)
+        return fail(BVSS_EINVAL, "BVSS_SEARCH_FP8 needs an index built with BVSS_BUILD_FP8");
     return BVSS_OK;
+}
+
+// Refine a batch runs: 2 FP8 tensor cores, 1 BF16 tensor cores, 0 FP32.
+int refine_form(const bvss_index *ix, int flags, int max_mq) {
+    const int d = ix->p.d;
+    if ((flags & BVSS_SEARCH_FP8) && ix->vec8 && refine_mma_supported(d, max_mq, true)) return 2;
+    if ((flags & (BVSS_SEARCH_FAST | BVSS_SEARCH_FP8)) && ix->vec16 && refine_mma_supported(d, max_mq))
+        return 1;
+    return 0;
 }
 
 // Everything a query batch needs besides the index, for enqueue_batch.
@@ -342,7 +358,6 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     const int L = ix->p.wta_l, m = ix->p.m, d = ix->p.d, W = ix->W;
     const int k = s->k, C = s->C, A = s->A, M = s->M, nb = b.nb;
     const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
-    const bool fast = (s->flags & BVSS_SEARCH_FAST) != 0;
     const bool tensor_scan =
         kn.scan ? kn.scan == 1 : (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
     const int gate_mode = M == 0 ? 0 : (M > 255 ? 2 : 1);
@@ -392,10 +407,15 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     n += kSelectKernels + (bounded ? 1 : 0);
     if (ev) BVSS_CU(cudaEventRecord(ev[4], st));
     // lines 19-23
-    const bool mma = fast && refine_mma_supported(d, b.max_mq);
+    // the FP8 copy for query sets it takes, else the BF16 one, else FP32
+    const int form = refine_form(ix, s->flags, b.max_mq);
+    const bool mma = form > 0;
     if (mma)
-        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, ix->vec16, ix->vnorm16, ix->set_off,
-                                  d, w.cand, w.thr, C, w.pair, ix->err, st, kn.cand_cta, kn.stages));
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq,
+                                  form == 2 ? (const void *)ix->vec8 : (const void *)ix->vec16,
+                                  ix->vscale8, form == 2 ? ix->vnorm8 : ix->vnorm16, form == 2,
+                                  ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
+                                  kn.cand_cta, kn.stages));
     else if (refine_tma_supported(d, b.max_mq))
         BVSS_CU(launch_refine_tma(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
@@ -737,6 +757,12 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
             BVSS_CU(dalloc(&ix->vnorm16, (size_t)nv));
             BVSS_CU(launch_to_bf16(ix->vec, nv, p.d, ix->vec16, ix->vnorm16, st));
         }
+        if (p.flags & BVSS_BUILD_FP8) {
+            BVSS_CU(dalloc(&ix->vec8, (size_t)nv * p.d));
+            BVSS_CU(dalloc(&ix->vscale8, (size_t)nv));
+            BVSS_CU(dalloc(&ix->vnorm8, (size_t)nv));
+            BVSS_CU(launch_to_fp8(ix->vec, nv, p.d, ix->vec8, ix->vscale8, ix->vnorm8, st));
+        }
         BVSS_CU(launch_encode(ix->vec, nv, p.d, ix->proj, p.m, p.fanin, p.wta_l, ix->codes,
                               nullptr, st));
         BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,
@@ -955,8 +981,9 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
     BVSS_CU(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     const int d = p->ix->p.d;
     const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
-    const bool mma = (p->s.flags & BVSS_SEARCH_FAST) && refine_mma_supported(d, p->max_qset);
-    const int ns = mma ? refine_mma_stages(d, p->max_qset) : 0;
+    const int form = refine_form(p->ix, p->s.flags, p->max_qset);
+    const bool mma = form > 0;
+    const int ns = mma ? refine_mma_stages(d, p->max_qset, form == 2) : 0;
     Knobs best = p->kn;
     float best_t = 0.0f;
     int rc = plan_time(p, best, reps, &best_t);
@@ -1002,12 +1029,13 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
     if (!p) return fail(BVSS_EINVAL, "plan is NULL");
     const int d = p->ix->p.d;
     const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
-    const bool mma = (p->s.flags & BVSS_SEARCH_FAST) && refine_mma_supported(d, p->max_qset);
+    const int form = refine_form(p->ix, p->s.flags, p->max_qset);
+    const bool mma = form > 0;
     if (knobs) {
         knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
                                           : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
-        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages) : 0;
+        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, form == 2) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
     }
     if (launches) *launches = p->launches;

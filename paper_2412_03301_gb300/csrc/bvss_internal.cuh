@@ -64,6 +64,9 @@ struct bvss_index {
     float *vnorm = nullptr;      // n_vec squared norms (FP32)
     __nv_bfloat16 *vec16 = nullptr;   // n_vec x d BF16 copy (BVSS_BUILD_BF16)
     float *vnorm16 = nullptr;         // squared norms of the BF16 values
+    uint8_t *vec8 = nullptr;          // n_vec x d FP8 E4M3 copy (BVSS_BUILD_FP8)
+    float *vscale8 = nullptr;         // its per-vector scales
+    float *vnorm8 = nullptr;          // squared norms of the scaled FP8 values
     int64_t *set_off = nullptr;  // n_sets + 1
     uint16_t *proj = nullptr;    // m x F
     uint16_t *codes = nullptr;   // n_vec x L, ascending positions
@@ -175,23 +178,29 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
                               const float *vec, const float *vnorm, const int64_t *set_off,
                               int d, const int32_t *cand, const int32_t *thr, int C,
                               float *cand_dist, int *err, cudaStream_t st);
-// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 64)
-bool refine_mma_supported(int d, int max_mq);
+// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 64) or
+// FP8 vectors (query sets <= 32)
+// f8: the FP8 copy (query sets <= 32, d % 128 == 0) instead of the BF16 one
+bool refine_mma_supported(int d, int max_mq, bool f8 = false);
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st);
+// FP8 E4M3 copy with one scale per vector and the squared norms of the scaled values
+cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *scale,
+                          float *norm, cudaStream_t st);
 // records each candidate's critical (query vector, row) pair; launch_rescore then
-// writes its FP32 distance as the candidate's distance
-// cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy ring (4 up to
-// the most that fit; otherwise, and for 0, the most that fit).
+// writes its FP32 distance as the candidate's distance.  vecb: the BF16 copy, or with
+// f8 the FP8 copy and its per-vector scales vscale; vnorm: squared norms of the stored
+// values.  cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy
+// ring (4 up to the most that fit; otherwise, and for 0, the most that fit).
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
-                              const __nv_bfloat16 *vec16, const float *vnorm16,
-                              const int64_t *set_off, int d, const int32_t *cand,
+                              const void *vecb, const float *vscale, const float *vnorm,
+                              bool f8, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta = 0, int stages = 0);
 // stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
-int refine_mma_stages(int d, int max_mq);
+int refine_mma_stages(int d, int max_mq, bool f8 = false);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
-int refine_mma_ring(int d, int max_mq, int stages);
+int refine_mma_ring(int d, int max_mq, int stages, bool f8 = false);
 cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
                            int64_t n_vec, int d, const int32_t *thr, int C,
                            const longlong2 *pair, float *cand_dist, cudaStream_t st);

@@ -41,6 +41,7 @@
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "bvss_internal.cuh"
 #include "ptx_util.cuh"
@@ -65,22 +66,24 @@ constexpr int kSmemMax = 232448;
 struct Meta {
     int slot;     // candidate slot of the row, -1 past the end
     int row_in;   // row index inside its set
-    float vn;     // squared norm of the row's BF16 values
-    int pad;
+    float vn;     // squared norm of the row's stored values (BF16, or FP8 times its scale)
+    float sc;     // FP8 copy: the row's scale (1 for BF16)
 };
 
 struct Layout {
-    int q, stages, meta, dist, rkey, carry, bars, grow0, vrow0, qn, misc, total;
+    int q, stages, meta, dist, rkey, carry, bars, grow0, vrow0, qn, qsc, misc, total;
 };
+
+constexpr float kE4M3Max = 448.0f;   // largest finite FP8 E4M3 value
 
 // Tiles of row metadata the ring must hold: producers run at most ns stages
 // ahead of the MMA, which runs at most two tiles ahead of the epilogue.
 __host__ __device__ inline int meta_ring(int KB, int ns) { return (ns + KB) / KB + 3; }
 
-// MQ query rows x 128 bytes per K-block
-__host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
+// KB K-blocks of 128 bytes per row (64 BF16 or 128 FP8 values); MQ query rows x 128
+// bytes per K-block
+__host__ __device__ inline Layout make_layout(int KB, int ns, int MQ) {
     Layout L;
-    const int KB = d / kKB;
     const int MR = meta_ring(KB, ns);
     int o = 0;
     L.q = o;       o += KB * MQ * 128;
@@ -93,6 +96,7 @@ __host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
     L.qn = o;      o += MQ * 4;
+    L.qsc = o;     o += MQ * 4;                    // FP8: scale of each query vector
     L.misc = o;    o += 16;                        // TMEM address, abort flag
     L.total = o + 1024;                            // slack to align the base to 1024 bytes
     return L;
@@ -101,11 +105,38 @@ __host__ __device__ inline Layout make_layout(int d, int ns, int MQ) {
 constexpr int kMinNS = 4;   // smallest ring a caller may ask for
 
 // most stages that fit, at least 5
-inline int pick_stages(int d, int MQ) {
+inline int pick_stages(int KB, int MQ) {
     for (int ns = kMaxNS; ns >= 5; --ns)
-        if (make_layout(d, ns, MQ).total <= kSmemMax && meta_ring(d / kKB, ns) <= kMaxMeta)
+        if (make_layout(KB, ns, MQ).total <= kSmemMax && meta_ring(KB, ns) <= kMaxMeta)
             return ns;
     return 0;
+}
+
+// 16 FP8 E4M3 values (16 bytes) -> floats
+__device__ __forceinline__ void fp8x16_to_float(const uint4 pk, float (&f)[16]) {
+    const uint32_t w[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_fp8x2_storage_t two = (__nv_fp8x2_storage_t)(w[i >> 1] >> (16 * (i & 1)));
+        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(two, __NV_E4M3);
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+        f[2 * i] = v.x;
+        f[2 * i + 1] = v.y;
+    }
+}
+
+// 16 floats -> 16 FP8 E4M3 values (round to nearest, saturating)
+__device__ __forceinline__ uint4 float16_to_fp8(const float (&f)[16]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[4 * i], f[4 * i + 1]),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[4 * i + 2], f[4 * i + 3]),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        w[i] = (lo & 0xFFFFu) | (hi << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // wait for a phase, or give up when the limit passes or another role gave up
@@ -128,10 +159,14 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | low;
 }
 
-template <int MQ>
+// F8: the database rows are the FP8 copy (vecb: d bytes per row, with scale vscale and
+// squared norm vnorm of the scaled values) and the query vectors are quantised the same
+// way in the CTA; otherwise both are BF16 (vecb: 2d bytes per row).
+template <int MQ, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-             const __nv_bfloat16 *__restrict__ vec16, const float *__restrict__ vnorm16,
+             const unsigned char *__restrict__ vecb, const float *__restrict__ vscale,
+             const float *__restrict__ vnorm,
              const int64_t *__restrict__ set_off, int d, int ns,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int cpc,
              longlong2 *__restrict__ pair, int *__restrict__ err) {
@@ -147,9 +182,10 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     constexpr int kQBlock = MQ * 128;               // query rows x 128 bytes per K-block
     constexpr int kRowB = MQ * 4;                    // bytes of one row's distances
     constexpr uint32_t kTmemCols = 2 * MQ;           // two accumulators of MQ columns
-    const int KB = d / kKB;
+    const int RB = F8 ? d : 2 * d;                  // bytes of one stored row
+    const int KB = RB / 128;
     const int MR = meta_ring(KB, ns);
-    const Layout Lo = make_layout(d, ns, MQ);
+    const Layout Lo = make_layout(KB, ns, MQ);
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *Qs = smem + Lo.q;
@@ -164,6 +200,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     int64_t *grow0 = reinterpret_cast<int64_t *>(smem + Lo.grow0);
     int *vrow0 = reinterpret_cast<int *>(smem + Lo.vrow0);
     float *qn = reinterpret_cast<float *>(smem + Lo.qn);
+    float *qsc = reinterpret_cast<float *>(smem + Lo.qsc);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lo.misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lo.misc + 4);
 
@@ -181,9 +218,43 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         vrow0[c] = n;
     }
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
-    // query rows 0..MQ-1 in BF16, K-major 128-byte swizzle (rows >= mq are zero)
-    const int nch = d / 8;                         // 16-byte chunks per row
-    for (int e = tid; e < MQ * nch; e += kThreads) {
+    if (F8) {
+        // scale of each query vector: its largest magnitude maps to the largest E4M3 value
+        for (int a = warp; a < MQ; a += kThreads / 32) {
+            float mx = 0.0f;
+            if (a < mq)
+                for (int k = lane; k < d; k += 32) mx = fmaxf(mx, fabsf(qvec[(a0 + a) * d + k]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) qsc[a] = mx > 0.0f ? mx / kE4M3Max : 1.0f;
+        }
+        __syncthreads();
+    }
+    // query rows 0..MQ-1 (BF16, or FP8 over their scales), K-major 128-byte swizzle
+    // (rows >= mq are zero)
+    const int nch = RB / 16;                       // 16-byte chunks per row
+    for (int e = tid; e < MQ * nch && F8; e += kThreads) {
+        const int a = e / nch, ch = e - (e / nch) * nch;
+        float x[16];
+        if (a < mq) {
+            const float4 *src = reinterpret_cast<const float4 *>(qvec + (a0 + a) * d + ch * 16);
+            const float inv = 1.0f / qsc[a];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 u = src[i];
+                x[4 * i] = u.x * inv;
+                x[4 * i + 1] = u.y * inv;
+                x[4 * i + 2] = u.z * inv;
+                x[4 * i + 3] = u.w * inv;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = 0.0f;
+        }
+        *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) =
+            float16_to_fp8(x);
+    }
+    for (int e = tid; e < MQ * nch && !F8; e += kThreads) {
         const int a = e / nch, ch = e - (e / nch) * nch;
         float x[8];
         if (a < mq) {
@@ -248,17 +319,25 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         for (int ch = lane; ch < nch; ch += 32) {
             const uint4 pk =
                 *reinterpret_cast<const uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7));
-            const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+            if (F8) {
+                float f[16];
+                fp8x16_to_float(pk, f);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[i]));
-                sq = fmaf(f.x, f.x, sq);
-                sq = fmaf(f.y, f.y, sq);
+                for (int i = 0; i < 16; ++i) sq = fmaf(f[i], f[i], sq);
+            } else {
+                const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 f =
+                        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[i]));
+                    sq = fmaf(f.x, f.x, sq);
+                    sq = fmaf(f.y, f.y, sq);
+                }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) qn[a] = sq;
+        if (lane == 0) qn[a] = F8 ? sq * qsc[a] * qsc[a] : sq;   // of the stored values
     }
     tc_fence_before();
     __syncthreads();
@@ -266,7 +345,6 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     const uint32_t tmem = *tmem_slot;
     const int R = vrow0[ncand];
     const int n_tiles = (R + kRowsN - 1) / kRowsN;
-    const int total = n_tiles * KB;
 
     if (warp >= 4 && warp <= 7) {
         // ---- producers ----------------------------------------------------------
@@ -277,12 +355,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         const int p = tid - 128;
         const int pc = p & 7, pg = p >> 3;
         int n_slot = -1, n_row = 0;
-        float n_vn = 0.0f;
+        float n_vn = 0.0f, n_sc = 1.0f;
         auto locate = [&](int t) {
             const int v = t * kRowsN + p;
             n_slot = -1;
             n_row = 0;
             n_vn = 0.0f;
+            n_sc = 1.0f;
             if (v < R) {
                 int c = 0;
 #pragma unroll
@@ -290,7 +369,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     if (c + b < ncand && vrow0[c + b] <= v) c += b;
                 n_slot = c;
                 n_row = v - vrow0[c];
-                n_vn = vnorm16[grow0[c] + n_row];
+                n_vn = vnorm[grow0[c] + n_row];
+                if (F8) n_sc = vscale[grow0[c] + n_row];
             }
         };
         locate(0);
@@ -301,18 +381,18 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             m.slot = n_slot;
             m.row_in = n_row;
             m.vn = n_vn;
-            m.pad = 0;
+            m.sc = n_sc;
             Meta *mt = meta + (t % MR) * kRowsN;
             mt[p] = m;
             mbar_arrive(&mfull[t % MR]);
             // every producer's row metadata of this tile is visible after this barrier,
             // which all producers also leave together if one of them gave up
             if (!named_barrier_and(4, kProd, ok)) break;
-            const __nv_bfloat16 *src[8];
+            const unsigned char *src[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const Meta mk = mt[pg + 16 * k];
-                src[k] = mk.slot >= 0 ? vec16 + (grow0[mk.slot] + mk.row_in) * d + pc * 8 : nullptr;
+                src[k] = mk.slot >= 0 ? vecb + (grow0[mk.slot] + mk.row_in) * RB + pc * 16 : nullptr;
             }
             if (t + 1 < n_tiles) locate(t + 1);
             for (int kb = 0; kb < KB; ++kb, ++u) {
@@ -322,7 +402,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 unsigned char *dst = stages + s * kStageBytes;
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
-                    if (src[k]) cp_async16(dst + sw128_off(pg + 16 * k, pc), src[k] + kb * kKB);
+                    if (src[k]) cp_async16(dst + sw128_off(pg + 16 * k, pc), src[k] + kb * 128);
                 cp_async_mbar_arrive(&full[s]);   // fires when these copies have landed
             }
         }
@@ -330,7 +410,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(kRowsN, MQ);
+            constexpr uint32_t idesc = F8 ? umma_idesc_e4m3(kRowsN, MQ) : umma_idesc_bf16(kRowsN, MQ);
             const uint32_t qaddr = smem_u32(Qs), saddr = smem_u32(stages);
             bool ok = true;
             for (int t = 0; t < n_tiles && ok; ++t) {
@@ -345,11 +425,16 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     if (!ok) break;
                     fence_proxy_async();   // the producers' copies, seen by the tensor core
                     tc_fence_after();
+                    // four MMAs per 128-byte K-block: K = 16 BF16 or 32 FP8 values each
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        umma_bf16(dt, umma_desc_sw128(saddr + s * kStageBytes + 32 * k),
-                                  umma_desc_sw128(qaddr + kb * kQBlock + 32 * k), idesc,
-                                  (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ad = umma_desc_sw128(saddr + s * kStageBytes + 32 * k);
+                        const uint64_t bd = umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
+                        if (F8)
+                            umma_f8(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                        else
+                            umma_bf16(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (ok) umma_commit(&tfull[buf]);
@@ -362,6 +447,10 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         float qreg[MQ];
 #pragma unroll
         for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
+        // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1
+        float qs2[F8 ? MQ : 1];
+#pragma unroll
+        for (int a = 0; a < (F8 ? MQ : 1); ++a) qs2[a] = F8 ? 2.0f * qsc[a] : 2.0f;
         unsigned char *dw = dist + warp * 32 * kRowB;
         const int r = warp * 32 + lane;
         const int coff = ((lane >> 2) << 4) + (lane & 3) * 4;   // column phase: my query vector's word
@@ -401,7 +490,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                         for (int i = 0; i < 4; ++i) {
                             const int a = c4 * 4 + i;
                             // qreg is +inf past the query, which keeps those entries out
-                            const float d2 = fmaxf(qreg[a] + m.vn - 2.0f * __uint_as_float(v[a]), 0.0f);
+                            const float w2 = F8 ? qs2[F8 ? a : 0] * m.sc : 2.0f;
+                            const float d2 = fmaxf(qreg[a] + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
                             x[i] = d2;
                             if (d2 < best) {
                                 best = d2;
@@ -597,14 +687,61 @@ __global__ void k_to_bf16(const float *__restrict__ x, int64_t n, int d,
     }
 }
 
+// FP8 E4M3 copy of the vectors with one FP32 scale per vector (its largest magnitude
+// maps to the largest finite E4M3 value), and the squared norms of the scaled values
+__global__ void k_to_fp8(const float *__restrict__ x, int64_t n, int d, uint8_t *__restrict__ y,
+                         float *__restrict__ scale, float *__restrict__ norm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
+         v += warps) {
+        const float *xv = x + v * d;
+        float mx = 0.0f;
+        for (int k = lane; k < d; k += 32) mx = fmaxf(mx, fabsf(xv[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.0f ? mx / kE4M3Max : 1.0f;
+        const float inv = 1.0f / sc;
+        float s = 0.0f;
+        for (int c = lane; c < d / 16; c += 32) {
+            float f[16];
+            const float4 *src = reinterpret_cast<const float4 *>(xv + 16 * c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 u = src[i];
+                f[4 * i] = u.x * inv;
+                f[4 * i + 1] = u.y * inv;
+                f[4 * i + 2] = u.z * inv;
+                f[4 * i + 3] = u.w * inv;
+            }
+            const uint4 pk = float16_to_fp8(f);
+            *reinterpret_cast<uint4 *>(y + v * d + 16 * c) = pk;
+            float g[16];
+            fp8x16_to_float(pk, g);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) s = fmaf(g[i], g[i], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            scale[v] = sc;
+            norm[v] = s * sc * sc;
+        }
+    }
+}
+
 }  // namespace
 
 // query-set width of the kernel instance for the batch's largest query set
 inline int mq_for(int max_mq) { return max_mq <= 32 ? 32 : 64; }
 
-bool refine_mma_supported(int d, int max_mq) {
-    if (d % kKB != 0 || d < kKB || max_mq < 1 || max_mq > kMaxQ) return false;
-    return pick_stages(d, mq_for(max_mq)) > 0;
+// K-blocks of 128 bytes per stored row
+inline int kblocks(int d, bool f8) { return f8 ? d / 128 : d / 64; }
+
+bool refine_mma_supported(int d, int max_mq, bool f8) {
+    if (max_mq < 1 || max_mq > (f8 ? 32 : kMaxQ)) return false;
+    if (f8 ? (d % 128 != 0 || d < 128) : (d % kKB != 0 || d < kKB)) return false;
+    return pick_stages(kblocks(d, f8), mq_for(max_mq)) > 0;
 }
 
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
@@ -616,32 +753,45 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
     return cudaGetLastError();
 }
 
-int refine_mma_stages(int d, int max_mq) {
-    return refine_mma_supported(d, max_mq) ? pick_stages(d, mq_for(max_mq)) : 0;
+cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *scale,
+                          float *norm, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (d % 16 != 0) return cudaErrorInvalidValue;
+    int64_t g = (n * 32 + 255) / 256;
+    if (g > (1 << 20)) g = 1 << 20;
+    k_to_fp8<<<(unsigned)g, 256, 0, st>>>(x, n, d, y, scale, norm);
+    return cudaGetLastError();
 }
 
-int refine_mma_ring(int d, int max_mq, int stages) {
-    const int ns = refine_mma_stages(d, max_mq);
+int refine_mma_stages(int d, int max_mq, bool f8) {
+    return refine_mma_supported(d, max_mq, f8) ? pick_stages(kblocks(d, f8), mq_for(max_mq)) : 0;
+}
+
+int refine_mma_ring(int d, int max_mq, int stages, bool f8) {
+    const int ns = refine_mma_stages(d, max_mq, f8);
     return stages >= kMinNS && stages < ns ? stages : ns;
 }
 
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
-                              const __nv_bfloat16 *vec16, const float *vnorm16,
-                              const int64_t *set_off, int d, const int32_t *cand,
+                              const void *vecb, const float *vscale, const float *vnorm,
+                              bool f8, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta, int stages) {
     if (n_q <= 0) return cudaSuccess;
-    if (!refine_mma_supported(d, max_mq)) return cudaErrorInvalidValue;
+    if (!refine_mma_supported(d, max_mq, f8)) return cudaErrorInvalidValue;
+    if (f8 && !vscale) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
-    const int ns = refine_mma_ring(d, max_mq, stages);
-    const Layout Lo = make_layout(d, ns, MQ);
+    const int ns = refine_mma_ring(d, max_mq, stages, f8);
+    const Layout Lo = make_layout(kblocks(d, f8), ns, MQ);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
-    const auto kern = MQ == 32 ? k_refine_mma<32> : k_refine_mma<64>;
+    const auto kern = f8 ? k_refine_mma<32, true>
+                         : (MQ == 32 ? k_refine_mma<32, false> : k_refine_mma<64, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(qvec, qoff, vec16, vnorm16, set_off, d, ns,
-                                                    cand, thr, C, cpc, pair, err);
+    kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(
+        qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
+        thr, C, cpc, pair, err);
     return cudaGetLastError();
 }
 
