@@ -21,7 +21,9 @@
 //              into the async proxy, issues the MMAs (K = 16 each) and
 //              commits them to the stage's "empty" mbarrier and, per tile, to
 //              a "full" mbarrier of one of two TMEM accumulators;
-//   warps 0-3  epilogue.  Row phase (lane = row 32w + lane): squared
+//   warps 0-3  epilogue (for the 32-wide instances the column phase below runs
+//              in warps 9-12 instead, on double-buffered distance blocks, so it
+//              overlaps the next tile's row phase).  Row phase (lane = row 32w + lane): squared
 //              distances |q|^2 + |v|^2 - 2 q.v to all query vectors from
 //              MQ / 32 tensor-memory loads, their minimum with its arg-min
 //              (the row's key), the distances written to a swizzled
@@ -54,8 +56,13 @@ constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
 constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
 constexpr int kMaxNS = 10;           // stages in the ring, at most
 constexpr int kCandCTA = 512;        // candidates per CTA
-constexpr int kMaxMeta = 12;         // tiles of row metadata in flight, at most
-constexpr int kThreads = 9 * 32;     // warps 0-3 epilogue, 4-7 producers, 8 MMA
+constexpr int kMaxMeta = 14;         // tiles of row metadata in flight, at most
+// warps 0-3 epilogue (row phase, and the column phase unless split), 4-7 producers, 8 MMA,
+// and with a split epilogue 9-12 the column phase
+__host__ __device__ constexpr int threads_for(bool split) { return (split ? 13 : 9) * 32; }
+// the column phase gets warps of its own (and double-buffered distance blocks) for the
+// 32-wide instances; the 64-wide one has no room for a second distance block
+__host__ __device__ constexpr bool split_for(int MQ) { return MQ == 32; }
 constexpr int kProd = 128;
 constexpr int kEpi = 128;
 constexpr int kMaxQ = 64;            // query vectors per query set, at most
@@ -77,22 +84,27 @@ struct Layout {
 constexpr float kE4M3Max = 448.0f;   // largest finite FP8 E4M3 value
 
 // Tiles of row metadata the ring must hold: producers run at most ns stages
-// ahead of the MMA, which runs at most two tiles ahead of the epilogue.
-__host__ __device__ inline int meta_ring(int KB, int ns) { return (ns + KB) / KB + 3; }
+// ahead of the MMA, which runs at most two tiles ahead of the row phase, which with a
+// split epilogue runs at most two tiles ahead of the column phase.
+__host__ __device__ inline int meta_ring(int KB, int ns, bool split) {
+    return (ns + KB) / KB + 3 + (split ? 2 : 0);
+}
 
 // KB K-blocks of 128 bytes per row (64 BF16 or 128 FP8 values); MQ query rows x 128
 // bytes per K-block
 __host__ __device__ inline Layout make_layout(int KB, int ns, int MQ) {
     Layout L;
-    const int MR = meta_ring(KB, ns);
+    const bool split = split_for(MQ);
+    const int nd = split ? 2 : 1;                  // distance blocks
+    const int MR = meta_ring(KB, ns, split);
     int o = 0;
     L.q = o;       o += KB * MQ * 128;
     L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
-    L.dist = o;    o += kRowsN * MQ * 4;           // row-phase distances, MQ per row
-    L.rkey = o;    o += kRowsN * 8;                // per row minimum (the row's key), this tile
+    L.dist = o;    o += nd * kRowsN * MQ * 4;      // row-phase distances, MQ per row
+    L.rkey = o;    o += nd * kRowsN * 8;           // per row minimum (the row's key), per block
     L.carry = o;   o += 2 * (MQ + 1) * 8;          // state of a candidate continuing into the next tile
-    L.bars = o;    o += (2 * kMaxNS + 4 + kMaxMeta) * 8;
+    L.bars = o;    o += (2 * kMaxNS + 8 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
     L.qn = o;      o += MQ * 4;
@@ -107,7 +119,8 @@ constexpr int kMinNS = 4;   // smallest ring a caller may ask for
 // most stages that fit, at least 5
 inline int pick_stages(int KB, int MQ) {
     for (int ns = kMaxNS; ns >= 5; --ns)
-        if (make_layout(KB, ns, MQ).total <= kSmemMax && meta_ring(KB, ns) <= kMaxMeta)
+        if (make_layout(KB, ns, MQ).total <= kSmemMax &&
+            meta_ring(KB, ns, split_for(MQ)) <= kMaxMeta)
             return ns;
     return 0;
 }
@@ -163,7 +176,7 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
 // squared norm vnorm of the scaled values) and the query vectors are quantised the same
 // way in the CTA; otherwise both are BF16 (vecb: 2d bytes per row).
 template <int MQ, bool F8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_for(split_for(MQ)), 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const unsigned char *__restrict__ vecb, const float *__restrict__ vscale,
              const float *__restrict__ vnorm,
@@ -184,7 +197,10 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     constexpr uint32_t kTmemCols = 2 * MQ;           // two accumulators of MQ columns
     const int RB = F8 ? d : 2 * d;                  // bytes of one stored row
     const int KB = RB / 128;
-    const int MR = meta_ring(KB, ns);
+    constexpr bool SPLIT = split_for(MQ);
+    constexpr int kThreads = threads_for(SPLIT);
+    constexpr int kDistBytes = kRowsN * MQ * 4;      // one distance block
+    const int MR = meta_ring(KB, ns, SPLIT);
     const Layout Lo = make_layout(KB, ns, MQ);
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -196,7 +212,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     unsigned long long *rkey = reinterpret_cast<unsigned long long *>(smem + Lo.rkey);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bars);
     uint64_t *full = bars, *empty = bars + kMaxNS, *tfull = bars + 2 * kMaxNS,
-             *tempty = bars + 2 * kMaxNS + 2, *mfull = bars + 2 * kMaxNS + 4;
+             *tempty = bars + 2 * kMaxNS + 2, *dfull = bars + 2 * kMaxNS + 4,
+             *dempty = bars + 2 * kMaxNS + 6, *mfull = bars + 2 * kMaxNS + 8;
     int64_t *grow0 = reinterpret_cast<int64_t *>(smem + Lo.grow0);
     int *vrow0 = reinterpret_cast<int *>(smem + Lo.vrow0);
     float *qn = reinterpret_cast<float *>(smem + Lo.qn);
@@ -284,6 +301,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], kEpi / 32);
+            mbar_init(&dfull[b], kEpi / 32);    // split epilogue: row phase -> column phase
+            mbar_init(&dempty[b], kEpi / 32);   // and back
         }
         for (int i = 0; i < MR; ++i) mbar_init(&mfull[i], kProd);
         *abort_flag = 0;
@@ -441,167 +460,206 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             }
         }
     } else {
-        // ---- epilogue: warps 0-3 ----------------------------------------------------
+        // ---- epilogue ----------------------------------------------------------------
         const float INF = __int_as_float(0x7f800000);
         constexpr int H = MQ / 32;                   // query vectors per lane in the column phase
-        float qreg[MQ];
-#pragma unroll
-        for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
-        // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1
-        float qs2[F8 ? MQ : 1];
-#pragma unroll
-        for (int a = 0; a < (F8 ? MQ : 1); ++a) qs2[a] = F8 ? 2.0f * qsc[a] : 2.0f;
-        unsigned char *dw = dist + warp * 32 * kRowB;
-        const int r = warp * 32 + lane;
         const int coff = ((lane >> 2) << 4) + (lane & 3) * 4;   // column phase: my query vector's word
-        bool ok = true;
-        for (int t = 0; t < n_tiles; ++t) {
-            // all four warps leave together if one of them gave up
-            if (!named_barrier_and(1, kEpi, ok)) break;
-            const int buf = t & 1;
-            ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
-                 wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err);
-            ok = __all_sync(0xffffffffu, ok);   // the tensor-memory load below is warp-wide
-            const Meta *mt = meta + (t % MR) * kRowsN;
+        // column phase of tile t for group warp gw (lane = query vector): the candidates
+        // whose first row in the tile lies in rows 32gw..32gw+31, from the tile's distance
+        // block dblk and row keys kblk
+        auto column_phase = [&](int t, const Meta *mt, const unsigned char *dblk,
+                                const unsigned long long *kblk, int gw) {
             const int t0 = t * kRowsN;
             const int rows_t = min(kRowsN, R - t0);
-            if (ok) {
-                tc_fence_after();
-                const int rows_w = min(32, rows_t - warp * 32);
-                uint32_t v[MQ];
-                if (rows_w > 0) {
+        // column phase: lane = query vector; candidates whose first row in this
+        // tile lies in rows lo..hi-1 belong to this warp
+        const int lo = gw * 32, hi = min(lo + 32, rows_t);
+        int c = mt[lo].slot;
+        int j = lo;
+        if (lo > 0 && vrow0[c] - t0 < lo) {   // begun in an earlier warp's rows
+            j = vrow0[c + 1] - t0;
+            ++c;
+        }
+        const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
+        unsigned long long *cout = carry + (t & 1) * (MQ + 1);
+        while (j < hi) {
+            const int cs = vrow0[c] - t0;                 // < 0: continues from the last tile
+            const int je = min(vrow0[c + 1] - t0, rows_t);
+            // per query vector lane + 32 h: minimum over the candidate's rows, with the row
+            float bmin[H];
+            int brow[H];
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                bmin[h] = INF;
+                brow[h] = 0;
+            }
+            unsigned long long kmax = 0;
+            if (cs < 0) {
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const unsigned long long k0 = cin[32 * h + lane];
+                    bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
+                    brow[h] = (int)(uint32_t)k0;
+                }
+                kmax = cin[MQ];
+            }
+            for (int j0 = j; j0 < je; j0 += 4) {
+                float x[4][H];
+                unsigned long long kk[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
 #pragma unroll
                     for (int h = 0; h < H; ++h)
-                        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * MQ + 32 * h),
-                                  *reinterpret_cast<uint32_t(*)[32]>(v + 32 * h));
+                        x[i][h] = *reinterpret_cast<const float *>(
+                            dblk + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
+                    kk[i] = kblk[jr];
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
-                if (rows_w > 0) {
-                    // row phase: lane = row r
-                    const Meta m = mt[r];
-                    float best = INF;
-                    int ba = 0;
 #pragma unroll
-                    for (int c4 = 0; c4 < MQ / 4; ++c4) {
-                        float x[4];
+                for (int i = 0; i < 4; ++i) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int a = c4 * 4 + i;
-                            // qreg is +inf past the query, which keeps those entries out
-                            const float w2 = F8 ? qs2[F8 ? a : 0] * m.sc : 2.0f;
-                            const float d2 = fmaxf(qreg[a] + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
-                            x[i] = d2;
-                            if (d2 < best) {
-                                best = d2;
-                                ba = a;
-                            }
+                    for (int h = 0; h < H; ++h)
+                        if (x[i][h] < bmin[h]) {
+                            bmin[h] = x[i][h];
+                            brow[h] = j0 + i - cs;   // row inside the candidate's set
                         }
-                        // 128-byte halves of the row, 16-byte chunks swizzled by the row
-                        *reinterpret_cast<float4 *>(dw + lane * kRowB + (c4 >> 3) * 128 +
-                                                    (((c4 & 7) ^ (lane & 7)) << 4)) =
-                            make_float4(x[0], x[1], x[2], x[3]);
-                    }
-                    rkey[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
+                    kmax = kk[i] > kmax ? kk[i] : kmax;
                 }
             }
-            named_barrier_sync(2, kEpi);   // the tile's distances and row keys are visible
-            if (ok && warp * 32 < rows_t) {
-                // column phase: lane = query vector; candidates whose first row in this
-                // tile lies in rows lo..hi-1 belong to this warp
-                const int lo = warp * 32, hi = min(lo + 32, rows_t);
-                int c = mt[lo].slot;
-                int j = lo;
-                if (lo > 0 && vrow0[c] - t0 < lo) {   // begun in an earlier warp's rows
-                    j = vrow0[c + 1] - t0;
-                    ++c;
+            if (vrow0[c + 1] - t0 <= rows_t) {
+                // complete: max over query vectors of the row minima vs max over rows;
+                // the query side's pair is the lowest query vector attaining it
+                uint32_t bits[H], lmx = 0;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    bits[h] = 32 * h + lane < mq ? __float_as_uint(bmin[h]) : 0u;
+                    lmx = bits[h] > lmx ? bits[h] : lmx;
                 }
-                const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
-                unsigned long long *cout = carry + (t & 1) * (MQ + 1);
-                while (j < hi) {
-                    const int cs = vrow0[c] - t0;                 // < 0: continues from the last tile
-                    const int je = min(vrow0[c + 1] - t0, rows_t);
-                    // per query vector lane + 32 h: minimum over the candidate's rows, with the row
-                    float bmin[H];
-                    int brow[H];
+                const uint32_t mx = __reduce_max_sync(0xffffffffu, lmx);
+                int pa = -1, pr = 0;
 #pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        bmin[h] = INF;
-                        brow[h] = 0;
+                for (int h = 0; h < H; ++h) {
+                    const uint32_t who =
+                        __ballot_sync(0xffffffffu, 32 * h + lane < mq && bits[h] == mx);
+                    const int src = __ffs(who) - 1;
+                    const int rsrc = (int)__shfl_sync(0xffffffffu, (uint32_t)brow[h],
+                                                      src < 0 ? 0 : src);
+                    if (pa < 0 && who != 0u) {
+                        pa = 32 * h + src;
+                        pr = rsrc;
                     }
-                    unsigned long long kmax = 0;
-                    if (cs < 0) {
+                }
+                if (mx < (uint32_t)(kmax >> 32)) {
+                    pa = (int)(kmax & 0xff);
+                    pr = (int)((kmax >> 8) & 0xffffff);
+                }
+                // the pair as (query vector, global row of the database vector)
+                if (lane == 0)
+                    pair[(int64_t)q * C + c0 + c] = make_longlong2(pa, grow0[c] + pr);
+            } else {
+                // continues into the next tile
 #pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            const unsigned long long k0 = cin[32 * h + lane];
-                            bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
-                            brow[h] = (int)(uint32_t)k0;
-                        }
-                        kmax = cin[MQ];
+                for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
+                if (lane == 0) cout[MQ] = kmax;
+            }
+            j = je;
+            ++c;
+        }
+        };
+        if (!SPLIT || warp < 4) {
+            // ---- row phase (and, unless split, the column phase): warps 0-3 ----------
+            float qreg[MQ];
+#pragma unroll
+            for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
+            // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1
+            float qs2[F8 ? MQ : 1];
+#pragma unroll
+            for (int a = 0; a < (F8 ? MQ : 1); ++a) qs2[a] = F8 ? 2.0f * qsc[a] : 2.0f;
+            const int r = warp * 32 + lane;
+            bool ok = true;
+            for (int t = 0; t < n_tiles; ++t) {
+                // all four warps leave together if one of them gave up
+                if (!named_barrier_and(1, kEpi, ok)) break;
+                const int buf = t & 1;
+                const int db = SPLIT ? buf : 0;      // this tile's distance block
+                ok = wait_or_abort(&mfull[t % MR], (uint32_t)((t / MR) & 1), abort_flag, err) &&
+                     wait_or_abort(&tfull[buf], (uint32_t)((t >> 1) & 1), abort_flag, err) &&
+                     (!SPLIT || wait_or_abort(&dempty[buf], (uint32_t)(((t >> 1) & 1) ^ 1),
+                                              abort_flag, err));
+                ok = __all_sync(0xffffffffu, ok);   // the tensor-memory load below is warp-wide
+                const Meta *mt = meta + (t % MR) * kRowsN;
+                const int rows_t = min(kRowsN, R - t * kRowsN);
+                unsigned char *dblk = dist + db * kDistBytes;
+                unsigned long long *kblk = rkey + db * kRowsN;
+                if (ok) {
+                    tc_fence_after();
+                    const int rows_w = min(32, rows_t - warp * 32);
+                    uint32_t v[MQ];
+                    if (rows_w > 0) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) +
+                                          (uint32_t)(buf * MQ + 32 * h),
+                                      *reinterpret_cast<uint32_t(*)[32]>(v + 32 * h));
                     }
-                    for (int j0 = j; j0 < je; j0 += 4) {
-                        float x[4][H];
-                        unsigned long long kk[4];
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                    if (rows_w > 0) {
+                        // row phase: lane = row r
+                        const Meta m = mt[r];
+                        unsigned char *dw = dblk + warp * 32 * kRowB;
+                        float best = INF;
+                        int ba = 0;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
+                        for (int c4 = 0; c4 < MQ / 4; ++c4) {
+                            float x[4];
 #pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                x[i][h] = *reinterpret_cast<const float *>(
-                                    dist + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
-                            kk[i] = rkey[jr];
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                if (x[i][h] < bmin[h]) {
-                                    bmin[h] = x[i][h];
-                                    brow[h] = j0 + i - cs;   // row inside the candidate's set
+                            for (int i = 0; i < 4; ++i) {
+                                const int a = c4 * 4 + i;
+                                // qreg is +inf past the query, which keeps those entries out
+                                const float w2 = F8 ? qs2[F8 ? a : 0] * m.sc : 2.0f;
+                                const float d2 =
+                                    fmaxf(qreg[a] + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
+                                x[i] = d2;
+                                if (d2 < best) {
+                                    best = d2;
+                                    ba = a;
                                 }
-                            kmax = kk[i] > kmax ? kk[i] : kmax;
-                        }
-                    }
-                    if (vrow0[c + 1] - t0 <= rows_t) {
-                        // complete: max over query vectors of the row minima vs max over rows;
-                        // the query side's pair is the lowest query vector attaining it
-                        uint32_t bits[H], lmx = 0;
-#pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            bits[h] = 32 * h + lane < mq ? __float_as_uint(bmin[h]) : 0u;
-                            lmx = bits[h] > lmx ? bits[h] : lmx;
-                        }
-                        const uint32_t mx = __reduce_max_sync(0xffffffffu, lmx);
-                        int pa = -1, pr = 0;
-#pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            const uint32_t who =
-                                __ballot_sync(0xffffffffu, 32 * h + lane < mq && bits[h] == mx);
-                            const int src = __ffs(who) - 1;
-                            const int rsrc = (int)__shfl_sync(0xffffffffu, (uint32_t)brow[h],
-                                                              src < 0 ? 0 : src);
-                            if (pa < 0 && who != 0u) {
-                                pa = 32 * h + src;
-                                pr = rsrc;
                             }
+                            // 128-byte halves of the row, 16-byte chunks swizzled by the row
+                            *reinterpret_cast<float4 *>(dw + lane * kRowB + (c4 >> 3) * 128 +
+                                                        (((c4 & 7) ^ (lane & 7)) << 4)) =
+                                make_float4(x[0], x[1], x[2], x[3]);
                         }
-                        if (mx < (uint32_t)(kmax >> 32)) {
-                            pa = (int)(kmax & 0xff);
-                            pr = (int)((kmax >> 8) & 0xffffff);
-                        }
-                        // the pair as (query vector, global row of the database vector)
-                        if (lane == 0)
-                            pair[(int64_t)q * C + c0 + c] = make_longlong2(pa, grow0[c] + pr);
-                    } else {
-                        // continues into the next tile
-#pragma unroll
-                        for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
-                        if (lane == 0) cout[MQ] = kmax;
+                        kblk[r] = dkey(best, ((uint32_t)(m.row_in & 0xffffff) << 8) | (uint32_t)ba);
                     }
-                    j = je;
-                    ++c;
                 }
+                if (SPLIT) {
+                    // hand the block to the column warps
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&dfull[buf]);
+                    continue;
+                }
+                named_barrier_sync(2, kEpi);   // the tile's distances and row keys are visible
+                if (ok && warp * 32 < rows_t) column_phase(t, mt, dblk, kblk, warp);
+            }
+        } else if (warp >= 9) {
+            // ---- column phase: warps 9-12 (split epilogue) ----------------------------
+            const int gw = warp - 9;
+            bool ok = true;
+            for (int t = 0; t < n_tiles; ++t) {
+                // the previous tile's carry is visible after this barrier, which all four
+                // warps also leave together if one of them gave up
+                if (!named_barrier_and(3, kEpi, ok)) break;
+                const int buf = t & 1;
+                ok = __all_sync(0xffffffffu, wait_or_abort(&dfull[buf], (uint32_t)((t >> 1) & 1),
+                                                           abort_flag, err));
+                if (ok && gw * 32 < min(kRowsN, R - t * kRowsN))
+                    column_phase(t, meta + (t % MR) * kRowsN, dist + buf * kDistBytes,
+                                 rkey + buf * kRowsN, gw);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dempty[buf]);
             }
         }
     }
@@ -789,7 +847,7 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                          : (MQ == 32 ? k_refine_mma<32, false> : k_refine_mma<64, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, n_q), kThreads, Lo.total, st>>>(
+    kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(
         qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
         thr, C, cpc, pair, err);
     return cudaGetLastError();
