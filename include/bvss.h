@@ -86,8 +86,8 @@ typedef struct bvss_params {
                                from BF16 vectors with FP32 accumulation (tcgen05), the pair that
                                attains each Hausdorff value re-scored in FP32.  Exact for inputs
                                on the 2^-8 grid; otherwise BF16 rounding can pick a slightly
-                               different pair.  Needs an index built with BVSS_BUILD_BF16 and
-                               query sets of at most 32 vectors (larger sets use the FP32 refine) */
+                               different pair.  Needs an index built with BVSS_BUILD_BF16; batches
+                               with a query set of more than 64 vectors use the FP32 refine */
 
 #define BVSS_SEARCH_POPC_SCAN 2  /* score sketches (Alg. 6 line 12) with CUDA-core popcounts over
                                     the sets that pass layer 1, instead of the default tensor-core
