@@ -211,6 +211,15 @@ __device__ __forceinline__ bool next_pair(uint32_t &act, int &mine) {
     return true;
 }
 
+// this lane's eight scores of block `mine` of the range [w0, w1) (lanes 0-15 and 16-31
+// each cover one block); all 0xFFFF when there is no such block
+__device__ __forceinline__ uint4 lane_block_scores(const uint4 *row4, int64_t w0, int64_t w1,
+                                                   int mine) {
+    const int64_t i0 = w0 + (int64_t)(mine < 0 ? 0 : mine) * kSelBlock + (threadIdx.x & 15) * 8;
+    if (mine < 0 || i0 >= w1) return make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    return row4[i0 / 8];
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
         const int32_t *__restrict__ thr, const uint16_t *__restrict__ bmin,
@@ -229,19 +238,26 @@ k_count(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
         const uint4 *row4 = reinterpret_cast<const uint4 *>(h + (int64_t)q * hs);
         // blocks whose minimum is above H* count nothing
         uint32_t act = active_blocks(bm, H);
-        int mine;
-        while (next_pair(act, mine)) {
-            const int64_t i0 = w0 + (int64_t)mine * kSelBlock + (lane & 15) * 8;
-            if (mine < 0 || i0 >= w1) continue;
-            const uint4 v = row4[i0 / 8];
+        int mine = -1;
+        bool have = next_pair(act, mine);
+        uint4 v = lane_block_scores(row4, w0, w1, have ? mine : -1);
+        while (have) {
+            // the next pair's scores are in flight while this pair is counted
+            int nmine = -1;
+            const bool nhave = next_pair(act, nmine);
+            const uint4 nv = lane_block_scores(row4, w0, w1, nhave ? nmine : -1);
+            const int64_t i0 = w0 + (int64_t)(mine < 0 ? 0 : mine) * kSelBlock + (lane & 15) * 8;
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int val = (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
-                const bool in = i0 + e < w1;
+                const bool in = mine >= 0 && i0 + e < w1;
                 lt += in && val < H;
                 eq += in && val == H;
             }
+            v = nv;
+            mine = nmine;
+            have = nhave;
         }
     }
     lt = (int)__reduce_add_sync(0xffffffffu, (uint32_t)lt);
@@ -323,19 +339,27 @@ k_write(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs,
     // blocks whose minimum is above H* hold no candidate; the others two at a time, in
     // id order over the lanes
     uint32_t act = active_blocks(bm, H);
-    int mine;
-    while (next_pair(act, mine)) {
-        const int64_t i0 = w0 + (int64_t)(mine < 0 ? 0 : mine) * kSelBlock + (lane & 15) * 8;
+    int mine = -1;
+    bool have = next_pair(act, mine);
+    uint4 v = lane_block_scores(row4, w0, w1, have ? mine : -1);
+    while (have) {
+        // the next pair's scores are in flight while this pair is written
+        int nmine = -1;
+        const bool nhave = next_pair(act, nmine);
+        const uint4 nv = lane_block_scores(row4, w0, w1, nhave ? nmine : -1);
+        const int cur = mine;
+        const uint4 cv = v;
+        v = nv;
+        mine = nmine;
+        have = nhave;
+        const int64_t i0 = w0 + (int64_t)(cur < 0 ? 0 : cur) * kSelBlock + (lane & 15) * 8;
         int val[8];
-        if (mine >= 0 && i0 < w1) {
-            const uint4 v = row4[i0 / 8];
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        {
+            const uint32_t w[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                val[e] = i0 + e < w1 ? (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu) : 0xFFFF;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) val[e] = 0xFFFF;
+                val[e] = cur >= 0 && i0 + e < w1 ? (int)((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu)
+                                                 : 0xFFFF;
         }
         int n_lt = 0, n_eq = 0;
 #pragma unroll
