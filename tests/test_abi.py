@@ -82,3 +82,47 @@ def test_invalid_build_arguments_fail_without_gpu(lib):
                       ctypes.c_void_p(1), ctypes.byref(p), None, ctypes.byref(out))
     assert rc == bvss.BVSS_EINVAL and b"empty" in b.bvss_last_error()
     assert not out.value
+
+
+def test_plan_and_fp8_arguments_fail_without_gpu(lib):
+    """The plan entry points reject a NULL plan or index, and the FP8 copy's d % 128
+    rule is checked with the other build parameters, before any CUDA call."""
+    from paper_2412_03301_gb300 import bvss
+    b = bvss.load()
+    s = bvss.bvss_search(k=1, C=1, A=1, M=1, flags=0)
+    out = ctypes.c_void_p()
+    rc = b.bvss_plan_create(None, ctypes.byref(s), 1, 1, 1, None, None, None, None, None,
+                            ctypes.byref(out))
+    assert rc == bvss.BVSS_EINVAL and out.value is None
+    assert b.bvss_plan_launch(None, None) == bvss.BVSS_EINVAL
+    assert b.bvss_plan_tune(None, 1, None, None) == bvss.BVSS_EINVAL
+    assert b.bvss_plan_info(None, None, None) == bvss.BVSS_EINVAL
+    kn = (ctypes.c_int32 * 3)(0, 0, 0)
+    assert b.bvss_plan_set_knobs(None, kn) == bvss.BVSS_EINVAL
+    b.bvss_plan_free(None)                                   # a no-op
+    p = bvss.bvss_params(d=64, m=128, fanin=2, wta_l=4, flags=bvss.BVSS_BUILD_FP8)
+    rc = b.bvss_build(ctypes.c_void_p(1), ctypes.c_void_p(1), 1, ctypes.c_void_p(1),
+                      ctypes.byref(p), None, ctypes.byref(out))
+    assert rc == bvss.BVSS_EINVAL and b"BVSS_BUILD_FP8" in b.bvss_last_error()
+    p = bvss.bvss_params(d=64, m=128, fanin=2, wta_l=4, flags=8)   # unknown build flag
+    rc = b.bvss_build(ctypes.c_void_p(1), ctypes.c_void_p(1), 1, ctypes.c_void_p(1),
+                      ctypes.byref(p), None, ctypes.byref(out))
+    assert rc == bvss.BVSS_EINVAL
+
+
+def test_zipf_set_sizes_follow_the_stated_law():
+    """The serving load's reading of "Zipf-distributed in 1-128": P(size = k) is
+    proportional to 1/k on 1..128 (exponent 1)."""
+    import numpy as np
+    from paper_2412_03301_gb300 import datagen
+    n = 400_000
+    z = datagen.zipf_sizes(n, 1, 128, seed=5)
+    assert z.min() >= 1 and z.max() <= 128
+    k = np.arange(1, 129)
+    p = (1.0 / k) / (1.0 / k).sum()
+    freq = np.bincount(z, minlength=129)[1:] / n
+    # a few standard deviations of a binomial count on the small sizes, and the mean
+    for i in range(8):
+        assert abs(freq[i] - p[i]) < 5 * np.sqrt(p[i] * (1 - p[i]) / n), i
+    assert abs(z.mean() - (k * p).sum()) < 0.2
+    assert np.array_equal(z, datagen.zipf_sizes(n, 1, 128, seed=5))   # seeded
