@@ -1,0 +1,81 @@
+"""The benchmark's own arithmetic (CPU): recall with and without ties, the roofline
+of the dominant kernel and its neighbour, and traffic that only counts while the
+kernel's source is the one the counters were taken on."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec = importlib.util.spec_from_file_location("bench_under_test",
+                                                      os.path.join(ROOT, "bench.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def test_recall_strict_and_with_ties(bench):
+    gt_ids = np.array([[1, 2, 3], [4, 5, 6]])
+    gt_d2 = np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3]])
+    got = np.array([[3, 2, 9], [4, 5, 6]])
+    # query 0: ids 3 and 2 are in the truth; 9 ties the third distance exactly
+    got_d2 = np.array([[0.3, 0.2, 0.3], [0.1, 0.2, 0.3]])
+    strict, ties = bench.recall_at_k(got, gt_ids, gt_d2, got_d2, 3)
+    assert strict == pytest.approx((2 / 3 + 1) / 2)
+    assert ties == pytest.approx(1.0)
+    # a padded (-1) slot counts as a miss
+    got[1, 2] = -1
+    got_d2[1, 2] = np.inf
+    strict, ties = bench.recall_at_k(got, gt_ids, gt_d2, got_d2, 3)
+    assert strict == pytest.approx((2 / 3 + 2 / 3) / 2)
+    assert ties == pytest.approx((1 + 2 / 3) / 2)
+
+
+def test_roofline_picks_the_slower_kernel_and_reports_both(bench):
+    from paper_2412_03301_gb300 import datagen
+    c = dict(datagen.LARGE)
+    c["A"], c["M"] = 3, 1
+    hbm, _ = bench.measured_peaks()
+    rows = 33_483_707
+    per = {"encode": 0.5, "gate": 0.2, "scan": 4.0, "select": 1.0, "refine": 5.0,
+           "rescore": 0.6, "topk": 0.1}
+    r = bench.roofline(c, {k: 2 * v for k, v in per.items()}, 2, 1000, 1, rows * 20, rows, True)
+    assert r["kernel"] == "k_refine_mma" and r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(rows * 384 * 2 / 5e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / hbm)
+    other = r["other_kernels"][0]
+    assert other["kernel"] == "k_scan_mma" and other["bound"] == "tensor"
+    assert other["achieved"] == pytest.approx(2.0 * 1000 * c["n_sets"] * c["m"] / 4e-3 / 1e12)
+    # the scan dominates when it is the slower one
+    per["scan"], per["refine"] = 6.0, 5.0
+    r = bench.roofline(c, per, 1, 1000, 1, rows * 20, rows, True)
+    assert r["kernel"] == "k_scan_mma" and r["other_kernels"][0]["kernel"] == "k_refine_mma"
+
+
+def test_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    import hashlib
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.md").write_text(
+        "| kernel | source | sha256 | dram_bytes_per_unit | unit | capture |\n"
+        "|---|---|---|---|---|---|\n"
+        "| k_x | k.cu | %s | 123.5 | row | test |\n" % sha)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_per_unit("k_x") == pytest.approx(123.5)
+    assert bench.traffic_per_unit("k_y") is None
+    src.write_text("kernel v2\n")                      # the kernel changed: no traffic
+    assert bench.traffic_per_unit("k_x") is None
