@@ -148,8 +148,18 @@ def exact_topk(vec, vnorm, set_of_row, n_sets, qvec, qoff, qids, k, chunk=1 << 2
     """Exact Hausdorff top-k over every set for the listed query sets.
 
     Squared distances |q|^2 + |v|^2 - 2 q.v in FP32 (exact for values on the
-    2^-8 grid).  Returns (ids (len(qids), k), sorted squared distances, all
-    squared distances of the k-th place)."""
+    2^-8 grid).  Ties go to the lower id.  Returns (ids (len(qids), k), their
+    squared distances, ascending)."""
+    # TF32 would round the GEMM's inputs to 11 significant bits: the tool must stay FP32
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        return _exact_topk(vec, vnorm, set_of_row, n_sets, qvec, qoff, qids, k, chunk)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def _exact_topk(vec, vnorm, set_of_row, n_sets, qvec, qoff, qids, k, chunk):
     V = vec.shape[0]
     out_ids, out_d2 = [], []
     for q in qids:
@@ -335,20 +345,31 @@ def measured_peaks():
         return 6800.0, "of fallback"
 
 
+# DRAM bytes per unit of work (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture, divided by the units the captured launch processed), with the SHA-256 of the
+# kernel's source file at capture time; the summaries are in profiles/.
+TRAFFIC = {
+    "k_refine_mma": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
+                         sha256="c5eb024e7d65a0b587fe3af5b71d52400b236dbc97a731d724bb6bcac9ff9f2d",
+                         bytes_per_unit=779.5, unit="candidate row"),
+    "k_refine": dict(source="paper_2412_03301_gb300/csrc/refine.cu",
+                     sha256="6c5ad74bce97e56f0ef9f81aa61baf4f5f2a700f738ffa6bc0c9eadcc846e9ca",
+                     bytes_per_unit=1367.8, unit="candidate row"),
+}
+
+
 def traffic_per_unit(kernel):
-    """DRAM bytes per unit of work from profiles/traffic.md, if the kernel's
-    source still has the SHA-256 the capture was taken with (else None)."""
+    """DRAM bytes per unit of work of `kernel` from TRAFFIC, if its source file still
+    has the SHA-256 the capture was taken with (else None: the counters are stale)."""
     import hashlib
-    try:
-        for line in open(os.path.join(ROOT, "profiles", "traffic.md")):
-            f = [x.strip() for x in line.strip().strip("|").split("|")]
-            if len(f) >= 5 and f[0] == kernel:
-                src = os.path.join(ROOT, f[1])
-                sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-                return float(f[3]) if sha == f[2] else None
-    except Exception:
+    t = TRAFFIC.get(kernel)
+    if t is None:
         return None
-    return None
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, t["source"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return float(t["bytes_per_unit"]) if sha == t["sha256"] else None
 
 
 def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=False):

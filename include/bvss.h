@@ -313,9 +313,10 @@ int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int6
  * neither, nor any allocating library routine: its scratch memory is one
  * fixed array of about 5.2 MB compiled into the library, which every GPU that
  * loads the library holds until the process exits.
- *   h          device, n_queries rows of h_stride uint16 Hamming scores
- *              (0xFFFF = set outside F1), 16-byte aligned; the layout of
- *              bvss_trace.h with rows padded to h_stride
+ *   h          device, n_queries rows of h_stride uint16 Hamming scores,
+ *              16-byte aligned; the layout of bvss_trace.h with rows padded
+ *              to h_stride.  A score in 0..m is a set of F1; any larger
+ *              value (0xFFFF by convention) marks a set outside F1
  *   n_sets     1 .. BVSS_NOALLOC_MAX_SETS
  *   h_stride   row stride in elements, >= n_sets, multiple of 8
  *   m          code length (largest valid score), 1 .. BVSS_NOALLOC_MAX_M
@@ -326,6 +327,8 @@ int bvss_profile_read(bvss_index *ix, double *stage_ms, int64_t *n_batches, int6
  * Sizes beyond the limits return BVSS_EINVAL with a message.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process: do not call it again on
+ * a device after cudaDeviceReset (or any teardown of its primary context).
  * Every call shares the one array and leaves its contents behind (the call
  * clears what has to start at zero), so calls that overlap on the GPU --
  * on two streams, or from two host threads -- race and must be serialised

@@ -118,7 +118,9 @@ k_hist(const uint16_t *__restrict__ h, int64_t n_sets, int64_t hs, int m,
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint32_t val = (w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu;
-            if (s0 + e < end && val != kGatedOut) atomicAdd(&sh[val], 1u);
+            // a score above m (only a caller of bvss_select_noalloc can pass one) counts
+            // as outside F1, as in k_count and k_write, which never match it against H* <= m
+            if (s0 + e < end && val <= (uint32_t)m) atomicAdd(&sh[val], 1u);
         }
     }
     __syncthreads();

@@ -68,14 +68,17 @@ def test_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypatch):
     src.write_text("kernel v1\n")
     import hashlib
     sha = hashlib.sha256(src.read_bytes()).hexdigest()
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    (prof / "traffic.md").write_text(
-        "| kernel | source | sha256 | dram_bytes_per_unit | unit | capture |\n"
-        "|---|---|---|---|---|---|\n"
-        "| k_x | k.cu | %s | 123.5 | row | test |\n" % sha)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC", {"k_x": dict(source="k.cu", sha256=sha,
+                                                       bytes_per_unit=123.5, unit="row")})
     assert bench.traffic_per_unit("k_x") == pytest.approx(123.5)
     assert bench.traffic_per_unit("k_y") is None
     src.write_text("kernel v2\n")                      # the kernel changed: no traffic
     assert bench.traffic_per_unit("k_x") is None
+
+
+def test_committed_traffic_entries_name_existing_sources(bench):
+    import os
+    for name, t in bench.TRAFFIC.items():
+        assert os.path.exists(os.path.join(bench.ROOT, t["source"])), name
+        assert len(t["sha256"]) == 64 and t["bytes_per_unit"] > 0

@@ -90,3 +90,63 @@ def test_sizes_beyond_the_limits_are_rejected(setup):
     h = h[:4]
     assert _call(lib, h, 2000, 16384, 10, cand, cnt) == bvss.BVSS_EINVAL
     assert b"m = 16384" in lib.bvss_last_error()
+
+
+def _synthetic_h(rng, n_q, n_sets, stride, m, p_out, p_above):
+    """Seeded scores in 0..m with many ties, some 0xFFFF (outside F1) and some
+    values in (m, 0xFFFE] (also outside F1 by the entry point's contract)."""
+    h = rng.integers(0, m + 1, size=(n_q, n_sets)).astype(np.int64)
+    u = rng.random((n_q, n_sets))
+    h[u < p_out] = 0xFFFF
+    above = (u >= p_out) & (u < p_out + p_above)
+    h[above] = rng.integers(m + 1, 0xFFFF, size=int(above.sum()))
+    full = np.full((n_q, stride), 0xFFFF, np.int64)
+    full[:, :n_sets] = h
+    return h, torch.from_numpy(full.astype(np.uint16).view(np.int16)).cuda()
+
+
+def test_several_chunks_match_the_oracle_heap(setup, orc):
+    """50,000 sets span four of the select's 16,384-set chunks, so the fixed
+    array's per-range records, the cross-chunk tie ranks and the output slots
+    of later chunks are all used; the oracle's literal bounded heap (Alg. 6
+    lines 10-18) over the same scores decides the expected lists."""
+    bvss, lib, ix, w = setup
+    rng = np.random.default_rng(11)
+    n_sets, stride = 50_000, 50_008
+    for m, n_q, C in ((64, 5, 1000), (4096, 3, 16384)):
+        h, dh = _synthetic_h(rng, n_q, n_sets, stride, m, 0.1, 0.02)
+        cand = torch.full((n_q, C), 7, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(n_q, dtype=torch.int32, device="cuda")
+        for _ in range(2):   # two calls in a row on the same array
+            cand.fill_(7)
+            assert _call(lib, dh, n_sets, m, C, cand, cnt) == 0, bvss.bvss_last_error()
+            got, got_n = cand.cpu().numpy(), cnt.cpu().numpy()
+            for q in range(n_q):
+                gate = (h[q] <= m).astype(np.uint8)
+                ref = orc.heap_select(h[q].astype(np.int32), gate, C)
+                assert got_n[q] == ref.shape[0]
+                assert np.array_equal(got[q, :ref.shape[0]], ref)
+                assert np.all(got[q, ref.shape[0]:] == -1)
+
+
+def test_bad_layouts_are_rejected(setup):
+    bvss, lib, ix, w = setup
+    cand = torch.zeros((2, 10), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
+    h = torch.zeros((2, 2056), dtype=torch.int16, device="cuda")
+    # more sets than the array's per-chunk records cover
+    rc = lib.bvss_select_noalloc(ctypes.c_void_p(h.data_ptr()), 16777217, 16777224, 64, 2, 10,
+                                 ctypes.c_void_p(cand.data_ptr()),
+                                 ctypes.c_void_p(cnt.data_ptr()), None)
+    assert rc == bvss.BVSS_EINVAL and b"n_sets" in lib.bvss_last_error()
+    # a row stride that is not a multiple of 8 scores
+    rc = lib.bvss_select_noalloc(ctypes.c_void_p(h.data_ptr()), 2000, 2052, 64, 2, 10,
+                                 ctypes.c_void_p(cand.data_ptr()),
+                                 ctypes.c_void_p(cnt.data_ptr()), None)
+    assert rc == bvss.BVSS_EINVAL and b"h_stride" in lib.bvss_last_error()
+    # h not on a 16-byte boundary
+    rc = lib.bvss_select_noalloc(ctypes.c_void_p(h.data_ptr() + 2), 2000, 2048, 64, 2, 10,
+                                 ctypes.c_void_p(cand.data_ptr()),
+                                 ctypes.c_void_p(cnt.data_ptr()), None)
+    assert rc == bvss.BVSS_EINVAL and b"aligned" in lib.bvss_last_error()
+    torch.cuda.synchronize()
