@@ -262,13 +262,27 @@ def bruteforce_topk(Q, vectors, set_off, k):
 class Index:
     """The oracle's index: codes, sketches, counts and inverted lists."""
 
-    def __init__(self, vectors, set_off, proj, L):
+    def __init__(self, vectors, set_off, proj, L, threads=1):
         self.vectors = _c(vectors, np.float32)
         self.set_off = _c(set_off, np.int64)
         self.proj = _c(proj, np.uint16)
         self.m = self.proj.shape[0]
         self.L = L
-        self.pos, self.mask = encode(self.vectors, self.proj, L)
+        if threads > 1:
+            # the vectors are encoded independently (Alg. 1 line 4): chunks on host
+            # threads (the C calls release the GIL), the same codes as one call
+            from concurrent.futures import ThreadPoolExecutor
+            n = self.vectors.shape[0]
+            step = max(1, -(-n // (4 * threads)))
+            with ThreadPoolExecutor(threads) as ex:
+                parts = list(ex.map(lambda v0: encode(self.vectors[v0:v0 + step], self.proj, L),
+                                    range(0, n, step)))
+            self.pos = np.concatenate([p[0] for p in parts]) if parts else \
+                np.zeros((0, L), np.uint16)
+            self.mask = np.concatenate([p[1] for p in parts]) if parts else \
+                np.zeros((0, (self.m + 31) // 32), np.uint32)
+        else:
+            self.pos, self.mask = encode(self.vectors, self.proj, L)
         self.sketch, self.count = build_filters(self.pos, self.set_off, self.m)
         self.inv = InvertedIndex(self.count)
 

@@ -60,3 +60,14 @@ def test_intermediates_by_numpy(orc, small):
             o = np.lexsort((r["cand"], d))[:5]
             want = [int(r["cand"][j]) for j in o] + [-1] * (5 - len(o))
             assert r["ids"].tolist() == want
+
+
+def test_threaded_index_build_is_identical(orc):
+    """Encoding the database in chunks on host threads gives the same index."""
+    from paper_2412_03301_gb300 import datagen
+    w = datagen.workload(n_sets=300, size_lo=1, size_hi=9, d=32, n_components=16,
+                         n_queries=1, q_lo=1, q_hi=2, m=512, fanin=4, seed=71)
+    a = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], 12)
+    b = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], 12, threads=4)
+    for name in ("pos", "mask", "sketch", "count"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
