@@ -61,6 +61,7 @@ extern "C" {
 #define BVSS_MAX_L 1024        /* WTA winners per code */
 #define BVSS_MAX_A 64          /* inverted lists read per query */
 #define BVSS_MAX_C 16384       /* candidate budget per query set */
+#define BVSS_MAX_K 1024        /* results per query set */
 #define BVSS_MAX_QSET 128      /* vectors per query set */
 
 /* Build parameters (Def. 7 and Alg. 6's Theta minus the search knobs). */
@@ -84,10 +85,12 @@ typedef struct bvss_params {
 /* bvss_search.flags */
 #define BVSS_SEARCH_FAST 1  /* refine on the tensor cores: squared distances in the GEMM form
                                from BF16 vectors with FP32 accumulation (tcgen05), the pair that
-                               attains each Hausdorff value re-scored in FP32.  Exact for inputs
-                               on the 2^-8 grid; otherwise BF16 rounding can pick a slightly
-                               different pair.  Needs an index built with BVSS_BUILD_BF16; batches
-                               with a query set of more than 64 vectors use the FP32 refine */
+                               attains each Hausdorff value re-scored in FP32 (the trace's
+                               cand_dist outside the boundary band).  The top k are exact as in
+                               bvss_query; the band is wider by the copy's rounding error (zero
+                               for inputs on the 2^-8 grid).  Needs an index built with
+                               BVSS_BUILD_BF16; batches with a query set of more than 64 vectors
+                               use the FP32 refine */
 
 #define BVSS_SEARCH_POPC_SCAN 2  /* score sketches (Alg. 6 line 12) with CUDA-core popcounts over
                                     the sets that pass layer 1, instead of the default tensor-core
@@ -107,12 +110,13 @@ typedef struct bvss_params {
                                of the pair that attains its Hausdorff value there.  Approximate:
                                FP8 rounding (relative error up to 2^-4 per value) can pick another
                                pair, so a distance can be off by about twice the rounding error
-                               of the vectors involved, and the candidate order with it.  Batches
+                               of the vectors involved.  The top k are still exact as in
+                               bvss_query, through a boundary band that this error widens.  Batches
                                with a query set of more than 32 vectors use the BF16 copy if the
                                index has one, else the FP32 refine */
 
 typedef struct bvss_search {
-    int32_t k;      /* results per query set, >= 1 */
+    int32_t k;      /* results per query set, 1..BVSS_MAX_K */
     int32_t C;      /* candidate budget (c and T of Alg. 6), k <= C <= BVSS_MAX_C */
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
@@ -134,7 +138,9 @@ typedef struct bvss_trace {
     uint16_t *h;         /* n_q x N  Hamming(S_Q, S_i) (line 12); 0xFFFF = not in F1 */
     int32_t *cand;       /* n_q x C  candidate ids (F2), ascending; -1 padded */
     int32_t *n_cand;     /* n_q      number of candidates, min(C, |F1|) */
-    float *cand_dist;    /* n_q x C  Hausdorff distance of cand[j]; +inf padded */
+    float *cand_dist;    /* n_q x C  Hausdorff distance of cand[j] (the exact FP32 / FP64
+                            value inside the boundary band, the refine's value outside it);
+                            +inf padded */
 } bvss_trace;
 
 /*
@@ -162,8 +168,15 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
 /*
  * bvss_query -- Alg. 6 for a batch of query sets: FlyHash the query vectors,
  * C_Q / S_Q / P, first-layer gate (count >= M at one of the A positions),
- * the min(C, |F1|) smallest (Hamming, id) pairs, exact Hausdorff (Def. 4) of
- * those candidates in FP32, then the k smallest (distance, id).
+ * the min(C, |F1|) smallest (Hamming, id) pairs, the Hausdorff distance
+ * (Def. 4) of those candidates, then the k smallest (distance, id).
+ * The k results are exact for every refine form: each candidate's refine value
+ * comes with a rigorous error bound (rounding of the stored copy, FP32
+ * accumulation); every candidate whose interval reaches the k-th smallest upper
+ * bound is re-scored directly in FP32 over all pairs, and candidates that FP32
+ * cannot order at the top k are re-scored in FP64 on the GPU.  The order is
+ * then that of the FP64 Hausdorff distance, ties by id, and every returned
+ * distance is within (d + 4) 2^-24 (relative) of it.
  *   q_vectors   host or device, Vq x d FP32, query sets stored one after
  *               another; Vq = q_offsets[n_queries]
  *   q_offsets   host, n_queries + 1 int64, q_offsets[0] = 0, strictly
@@ -289,7 +302,8 @@ void bvss_plan_free(bvss_plan *p);
 #define BVSS_STAGE_REFINE 4   /* Hausdorff of the candidates (lines 19-22) */
 #define BVSS_STAGE_RESCORE 5  /* FP32 distance of each candidate's critical pair
                                  (BVSS_SEARCH_FAST only; 0 otherwise) */
-#define BVSS_STAGE_TOPK 6     /* k smallest (distance, id) and result copies (line 23) */
+#define BVSS_STAGE_TOPK 6     /* boundary re-score and the k smallest (distance, id)
+                                 (line 23; see bvss_query) */
 #define BVSS_N_STAGES 7
 
 /* Turn per-stage timing of later bvss_query calls on (on != 0) or off. */

@@ -90,6 +90,7 @@ void free_workspace(Workspace &w) {
     dfree(w.cand);
     dfree(w.cand_dist);
     dfree(w.pair);
+    dfree(w.band);
     dfree(w.out_ids);
     dfree(w.out_dist);
     w = Workspace();
@@ -104,6 +105,7 @@ void free_index(bvss_index *ix) {
     dfree(ix->vec8);
     dfree(ix->vscale8);
     dfree(ix->vnorm8);
+    dfree(ix->rstat);
     dfree(ix->set_off);
     dfree(ix->proj);
     dfree(ix->codes);
@@ -215,6 +217,7 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand, (size_t)nq * C));
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
+    BVSS_CU(dalloc(&w.band, band_workspace_ints(nq, C)));
     if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
     if (need_out) {
         BVSS_CU(dalloc(&w.out_ids, (size_t)nq * k));
@@ -274,6 +277,9 @@ int sync_and_check(bvss_index *ix, cudaStream_t st) {
         if (e == kErrPlanInput)
             return fail(BVSS_EINVAL, "a plan's query offsets were out of range; its results "
                                      "are not valid");
+        if (e == kErrBandOverflow)
+            return fail(BVSS_ECUDA, "more than 4096 candidates lie within FP32 rounding of "
+                                    "the k-th distance; the order among them is not exact");
         return fail(BVSS_ETIMEOUT, "a kernel's bounded wait gave up (device status %d)", e);
     }
     return BVSS_OK;
@@ -312,7 +318,8 @@ struct Knobs {
 int check_search(const bvss_index *ix, const bvss_search *s) {
     if (!s) return fail(BVSS_EINVAL, "search parameters are NULL");
     const int L = ix->p.wta_l;
-    if (s->k < 1) return fail(BVSS_EINVAL, "k = %d: need k >= 1", s->k);
+    if (s->k < 1 || s->k > BVSS_MAX_K)
+        return fail(BVSS_EINVAL, "k = %d: need 1 <= k <= %d", s->k, BVSS_MAX_K);
     if (s->C < s->k || s->C > BVSS_MAX_C)
         return fail(BVSS_EINVAL, "C = %d: need k <= C <= %d", s->C, BVSS_MAX_C);
     if ((s->flags & BVSS_SEARCH_ALG2) == 0 && (s->A < 1 || s->A > L || s->A > BVSS_MAX_A))
@@ -430,8 +437,11 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
         ++n;
     }
     if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
-    BVSS_CU(launch_topk(w.cand, w.cand_dist, w.thr, nb, C, k, b.ids, b.dist, st));
-    ++n;
+    // line 23: the k smallest (distance, id), decided exactly around the k-th
+    BVSS_CU(launch_band_topk(qv, b.qoff, nb, d, form, ix->rstat, ix->vec, ix->set_off, w.cand,
+                             w.thr, C, k, w.pair, w.cand_dist, w.band, b.ids, b.dist, ix->err,
+                             st));
+    n += kBandKernels;
     *launches += n;
     return BVSS_OK;
 }
@@ -763,6 +773,9 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
             BVSS_CU(dalloc(&ix->vnorm8, (size_t)nv));
             BVSS_CU(launch_to_fp8(ix->vec, nv, p.d, ix->vec8, ix->vscale8, ix->vnorm8, st));
         }
+        BVSS_CU(dalloc(&ix->rstat, 4));
+        BVSS_CU(launch_round_stats(ix->vec, nv, p.d, ix->vec16, ix->vec8, ix->vscale8, ix->rstat,
+                                   st));
         BVSS_CU(launch_encode(ix->vec, nv, p.d, ix->proj, p.m, p.fanin, p.wta_l, ix->codes,
                               nullptr, st));
         BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,

@@ -17,6 +17,7 @@ constexpr int kSelBlock = 128;         // sets per block minimum (the scan's til
 constexpr int kSelRangeWords = 32;     // per chunk: 8 warp ranges x (lt, eq, tie rank, slot)
 constexpr int kOffRing = 4;            // pinned staging slots for query offsets
 constexpr int kProfEvents = BVSS_N_STAGES + 1;  // events per profiled batch
+constexpr int kErrBandOverflow = 16;   // device status: more near-ties at the k-th than fit
 
 // A bit plane of the first-layer gate for one minimum count M:
 // word w of row p holds bit b = (C_{32w+b}[p] >= M), for every set (Def. 9 in
@@ -47,6 +48,7 @@ struct Workspace {
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
+    int32_t *band = nullptr;      // boundary band slots and counts      band_workspace_ints
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
     float *out_dist = nullptr;
     int cap_k = 0;
@@ -67,6 +69,8 @@ struct bvss_index {
     uint8_t *vec8 = nullptr;          // n_vec x d FP8 E4M3 copy (BVSS_BUILD_FP8)
     float *vscale8 = nullptr;         // its per-vector scales
     float *vnorm8 = nullptr;          // squared norms of the scaled FP8 values
+    float *rstat = nullptr;           // [0] largest norm, [1] / [2] largest rounding-error
+                                      // norm of the BF16 / FP8 copy (rounded up)
     int64_t *set_off = nullptr;  // n_sets + 1
     uint16_t *proj = nullptr;    // m x F
     uint16_t *codes = nullptr;   // n_vec x L, ascending positions
@@ -206,6 +210,22 @@ cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, cons
                            const longlong2 *pair, float *cand_dist, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
+// ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------
+// form: the refine that ran (0 FP32, 1 BF16 tensor cores, 2 FP8 tensor cores); stats: the
+// index's rstat; pair: the MMA forms' records (value in the high word of .x); band:
+// band_workspace_ints(n_q, C) ints of scratch.  Band members' cand_dist become their exact
+// values; cand_dist[q][n_sel..C) is padded with +inf; results as launch_topk.
+size_t band_workspace_ints(int64_t n_q, int C);
+cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int d, int form,
+                             const float *stats, const float *vec, const int64_t *set_off,
+                             const int32_t *cand, const int32_t *thr, int C, int k,
+                             const longlong2 *pair, float *cand_dist, int32_t *band,
+                             int64_t *out_ids, float *out_dist, int *err, cudaStream_t st);
+constexpr int kBandKernels = 3;
+// rstat of an index (x16 / x8 may be null: their entries stay 0)
+cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,
+                               const uint8_t *x8, const float *sc8, float *stats,
+                               cudaStream_t st);
 // also pads cand_dist[q][n_sel..C) with +inf
 cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *thr,
                         int n_q, int C, int k, int64_t *out_ids, float *out_dist,

@@ -549,13 +549,18 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                         pr = rsrc;
                     }
                 }
+                uint32_t hbits = mx;   // the candidate's squared value, as bits
                 if (mx < (uint32_t)(kmax >> 32)) {
                     pa = (int)(kmax & 0xff);
                     pr = (int)((kmax >> 8) & 0xffffff);
+                    hbits = (uint32_t)(kmax >> 32);
                 }
-                // the pair as (query vector, global row of the database vector)
+                // the pair as (query vector, global row of the database vector), with the
+                // squared Hausdorff value of the stored copies in the high word of .x
                 if (lane == 0)
-                    pair[(int64_t)q * C + c0 + c] = make_longlong2(pa, grow0[c] + pr);
+                    pair[(int64_t)q * C + c0 + c] = make_longlong2(
+                        (long long)(((unsigned long long)hbits << 32) | (uint32_t)pa),
+                        grow0[c] + pr);
             } else {
                 // continues into the next tile
 #pragma unroll
@@ -686,7 +691,7 @@ k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     const longlong2 pr = pair[(int64_t)q * C + c];
     // keep the pair inside the arrays whatever they hold
     const int64_t a0 = qoff[q], mq = qoff[q + 1] - a0;
-    const int64_t qa = a0 + min(max(pr.x, 0ll), (long long)mq - 1);
+    const int64_t qa = a0 + min(max((long long)(int32_t)(uint32_t)pr.x, 0ll), (long long)mq - 1);
     const int64_t row = min(max(pr.y, 0ll), (long long)n_vec - 1);
     const float4 *x4 = reinterpret_cast<const float4 *>(qvec + qa * d);
     const float4 *y4 = reinterpret_cast<const float4 *>(vec + row * d);
