@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--alg2-queries", type=int, default=100,
                     help="query sets for the plain BioVSS search (Alg. 2) line; 0 skips it")
+    ap.add_argument("--offgrid", type=int, default=1,
+                    help="1: also time the three refine forms on the large workload off the "
+                         "2^-8 grid and check them against the FP64 oracle")
+    ap.add_argument("--offgrid-recall-queries", type=int, default=100)
     ap.add_argument("--serving-queries", type=int, default=4096,
                     help="query sets per pass of the batched serving line (200k Zipf-sized "
                          "sets, d=768, one graph launch per pass); 0 skips it")
@@ -210,6 +214,111 @@ def true_d2_of(vec, vnorm, qvec, qoff, offsets, qids, ids):
             D.clamp_(min=0)
             out[j, c] = float(torch.maximum(D.min(1).values.max(), D.min(0).values.max()))
     return out
+
+
+# --------------------------------------------------------------------------
+# the large workload off the 2^-8 grid: every form against the FP64 oracle
+# --------------------------------------------------------------------------
+def fp64_recall(ids, gt_ids, qvec, qoff, vec_of, k):
+    """Recall@k decided in FP64: the true top k of each query set are the k smallest
+    oracle Hausdorff distances (Def. 4, FP64) among the ground truth's list (which holds
+    them: its FP32 errors are far below the spacing it leaves beyond k) and the returned
+    ids, ties by id.  vec_of(i) -> set i's vectors (numpy).  Returns (recall, the FP64
+    distances of the returned ids)."""
+    from oracle import oracle
+    rec, dist = [], np.full(ids.shape, np.inf)
+    for j in range(ids.shape[0]):
+        Q = qvec[qoff[j]:qoff[j + 1]]
+        pool = sorted(set(int(i) for i in gt_ids[j]) | set(int(i) for i in ids[j] if i >= 0))
+        hd = {i: oracle.haus(Q, vec_of(i)) for i in pool}
+        true = sorted(pool, key=lambda i: (hd[i], i))[:k]
+        rec.append(len(set(true) & set(int(i) for i in ids[j])) / k)
+        for c_, i in enumerate(ids[j]):
+            if i >= 0:
+                dist[j, c_] = hd[int(i)]
+    return float(np.mean(rec)), dist
+
+
+def offgrid_line(args, dev, stream):
+    """The large workload (1M sets, d = 384) drawn with the same seed but not rounded to
+    the 2^-8 grid, so BF16 / FP8 copies and FP32 sums all round: the three refine forms
+    timed on it, their ids compared, recall@10 decided in FP64 and every returned distance
+    compared with the oracle's FP64 Hausdorff value on sampled query sets."""
+    from paper_2412_03301_gb300 import bvss, datagen
+    c = dict(datagen.LARGE)
+    c["A"], c["M"] = 3, 1
+    w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
+                         d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],
+                         q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
+                         seed=args.seed, device=dev, grid=False)
+    off, qv, qo = w["offsets"], w["q_vectors"], w["q_offsets"]
+    nq = qo.shape[0] - 1
+    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=True, fp8=True)
+    kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"])
+    out_ids = torch.empty((nq, c["k"]), dtype=torch.int64, device=dev)
+    out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
+    forms, res = {}, {}
+    steps = max(1, min(args.steps, 5))
+    for name, f in (("plain", {}), ("fast", {"fast": True}), ("fp8", {"fp8": True})):
+        for _ in range(args.warmup):
+            bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kw, **f)
+        torch.cuda.synchronize(dev)
+        bvss.bvss_profile_enable(ix, True)
+        bvss.bvss_profile_read(ix, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kw, **f)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st, _, nl = bvss.bvss_profile_read(ix, reset=True)
+        bvss.bvss_profile_enable(ix, False)
+        bvss.bvss_sync(ix, stream)
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = (out_ids.cpu().numpy().copy(), out_dist.cpu().numpy().astype(np.float64))
+        forms[name] = {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                       "stages_ms_per_step": {k_: v / steps for k_, v in st.items()},
+                       "gpu_launches_per_step": nl // steps}
+    ids_p = res["plain"][0]
+    same = {name: int((res[name][0] == ids_p).all(axis=1).sum()) for name in ("fast", "fp8")}
+    # recall and distance errors against the FP64 oracle on the first query sets
+    nr = min(args.offgrid_recall_queries, nq)
+    vec = w["vectors"]
+    vnorm = (vec * vec).sum(1)
+    set_of_row = torch.repeat_interleave(torch.arange(c["n_sets"], device=dev),
+                                         torch.from_numpy(np.diff(off)).to(dev))
+    gt_ids, _ = exact_topk(vec, vnorm, set_of_row, c["n_sets"], qv, qo, list(range(nr)),
+                           c["k"] + 5)
+    gt_ids = gt_ids.cpu().numpy()
+    del vnorm, set_of_row
+    qvec_h = qv[:int(qo[nr])].cpu().numpy()
+    cache = {}
+
+    def vec_of(i):
+        if i not in cache:
+            cache[i] = vec[int(off[i]):int(off[i + 1])].cpu().numpy()
+        return cache[i]
+
+    for name in ("plain", "fast", "fp8"):
+        ids, dist = res[name][0][:nr], res[name][1][:nr]
+        r, d64 = fp64_recall(ids, gt_ids, qvec_h, qo, vec_of, c["k"])
+        ok = np.isfinite(d64)
+        rel = np.abs(dist[ok] - d64[ok]) / np.maximum(d64[ok], 1e-30)
+        forms[name].update({"recall_at_10_fp64": r, "queries": nr,
+                            "dist_rel_err_max": float(rel.max()) if rel.size else 0.0,
+                            "dist_rel_err_mean": float(rel.mean()) if rel.size else 0.0,
+                            "dist_rel_err_bound": (36 + -(-c["d"] // 32)) * 2.0 ** -24})
+    ix.close()
+    del w
+    torch.cuda.empty_cache()
+    return {"workload": "N=%d sets of %d-%d vectors, d=%d FP32 unit vectors NOT rounded to the "
+                        "2^-8 grid, %d-component mixture; FlyHash m=%d F=%d L=%d; %d query sets; "
+                        "A=%d M=%d C=%d k=%d" % (c["n_sets"], c["size_lo"], c["size_hi"], c["d"],
+                                                c["n_components"], c["m"], c["fanin"], c["L"],
+                                                nq, c["A"], c["M"], c["C"], c["k"]),
+            "forms": forms, "same_ids_as_plain": same, "query_sets": nq}
 
 
 # --------------------------------------------------------------------------
@@ -749,6 +858,8 @@ def run_ours(args, rank, world, local_rank):
     roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok)
     ix.close()
     torch.cuda.empty_cache()
+    offgrid = (offgrid_line(args, dev, stream)
+               if args.offgrid and args.workload == "large" and rank == 0 else None)
     serving = (serving_line(args, dev, stream)
                if args.serving_queries > 0 and args.workload == "large" else None)
     line = {
@@ -775,6 +886,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "alg2": alg2,
         "fp8": fp8,
+        "offgrid": offgrid,
         "serving": serving,
         "clocks": clk,
         "build_s": build_s,

@@ -176,7 +176,9 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
  * bound is re-scored directly in FP32 over all pairs, and candidates that FP32
  * cannot order at the top k are re-scored in FP64 on the GPU.  The order is
  * then that of the FP64 Hausdorff distance, ties by id, and every returned
- * distance is within (d + 4) 2^-24 (relative) of it.
+ * distance is within (36 + ceil(d / 32)) 2^-24 (relative) of it.  More than
+ * max(256, 4 k) candidates within FP32 rounding of the k-th distance (many
+ * identical sets) exceed the stage's room; the next bvss_sync reports it.
  *   q_vectors   host or device, Vq x d FP32, query sets stored one after
  *               another; Vq = q_offsets[n_queries]
  *   q_offsets   host, n_queries + 1 int64, q_offsets[0] = 0, strictly

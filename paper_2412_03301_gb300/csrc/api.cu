@@ -90,7 +90,6 @@ void free_workspace(Workspace &w) {
     dfree(w.cand);
     dfree(w.cand_dist);
     dfree(w.pair);
-    dfree(w.band);
     dfree(w.out_ids);
     dfree(w.out_dist);
     w = Workspace();
@@ -217,7 +216,6 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand, (size_t)nq * C));
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
-    BVSS_CU(dalloc(&w.band, band_workspace_ints(nq, C)));
     if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
     if (need_out) {
         BVSS_CU(dalloc(&w.out_ids, (size_t)nq * k));
@@ -278,8 +276,9 @@ int sync_and_check(bvss_index *ix, cudaStream_t st) {
             return fail(BVSS_EINVAL, "a plan's query offsets were out of range; its results "
                                      "are not valid");
         if (e == kErrBandOverflow)
-            return fail(BVSS_ECUDA, "more than 4096 candidates lie within FP32 rounding of "
-                                    "the k-th distance; the order among them is not exact");
+            return fail(BVSS_ECUDA, "more than max(256, 4 k) candidates lie within FP32 "
+                                    "rounding of the k-th distance; the order among them is "
+                                    "not exact");
         return fail(BVSS_ETIMEOUT, "a kernel's bounded wait gave up (device status %d)", e);
     }
     return BVSS_OK;
@@ -438,8 +437,8 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     }
     if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
     // line 23: the k smallest (distance, id), decided exactly around the k-th
-    BVSS_CU(launch_band_topk(qv, b.qoff, nb, d, form, ix->rstat, ix->vec, ix->set_off, w.cand,
-                             w.thr, C, k, w.pair, w.cand_dist, w.band, b.ids, b.dist, ix->err,
+    BVSS_CU(launch_band_topk(qv, b.qoff, nb, b.max_mq, d, form, ix->rstat, ix->vec, ix->set_off,
+                             w.cand, w.thr, C, k, w.pair, w.cand_dist, b.ids, b.dist, ix->err,
                              st));
     n += kBandKernels;
     *launches += n;

@@ -9,28 +9,35 @@
 //     2 q.v), re-scored directly as r = |q - v|.  The GEMM form's squared distance
 //     is off by at most D = (d + 8) 2^-23 (N_Q + N_V)^2 (N = largest norm), so the
 //     GEMM-form Hausdorff value is within D of H^2 and r^2 within 2D of it:
-//     lo = sqrt(r^2 - 2D) (1 - eta), hi = sqrt(r^2 + 2D) (1 + eta).
+//     lo = sqrt(r^2 - 2D) (1 - eta_d), hi = sqrt(r^2 + 2D) (1 + 2 eta_d).
 //   BF16 / FP8 forms: the GEMM-form Hausdorff value h of the rounded copies, packed
 //     into the pair record by the refine.  Rounding moves a vector x by e_x = |x - x'|
 //     and every pair distance by at most e_q + e_v (triangle inequality), so the
 //     Hausdorff value of the rounded sets is within e = max e_q + max e_v of H
 //     (max and min are 1-Lipschitz), and h is within D of that value squared:
 //     lo = sqrt(h - D) - e, hi = sqrt(h + D) + e.
-//   eta = (d + 4) 2^-24 bounds the relative error of a direct FP32 distance
-//     (d squared differences summed with FMA, then a square root).
-// Then (k' = min(k, candidates)):
-//   k_band_sel    tau = the k'-th smallest hi; the band B = {lo <= tau} holds every
-//                 candidate that can be among the k' nearest;
-//   k_band_exact  the direct FP32 Hausdorff value H32 of every member of B, all pairs
-//                 (one CTA per candidate, 32 x 32 pair tiles, 32 dimensions at a time);
-//   k_band_order  S = the members whose interval H32 (1 +- eta) reaches the k'-th
-//                 smallest H32, sorted by (H32, id); members of S whose interval
-//                 overlaps a neighbour's at or above rank k' are re-scored in FP64
-//                 (the same tiles in double), then S is ordered by (value, id) and
-//                 the first k' are the result.
+//   eta_d = (d + 4) 2^-24 bounds the relative error of a direct FP32 distance summed
+//     in one chain over d dimensions (the re-scored pairs, norms, rounding errors).
+//   eta = (40 + ceil(d / 32)) 2^-24 bounds that of this stage's own FP32 distances:
+//     each lane sums at most ceil(d / 32) squared differences (each within 2u of
+//     (q - v)^2) and a 5-level shuffle tree adds the lanes' sums (the CTA-tile form
+//     for d > 1024 sums 32 dimensions per chunk and then the chunks); the square
+//     root halves the relative error and adds u (u = 2^-24).
+// k_boundary, one CTA per query set (k' = min(k, candidates)):
+//   1. tau = the k'-th smallest hi; the band B = {lo <= tau} holds every candidate
+//      that can be among the k' nearest;
+//   2. the direct FP32 Hausdorff value H32 of every member of B over all pairs, one
+//      warp per member (lanes over the dimensions, the query set staged in shared
+//      memory, coalesced 16-byte row loads, shuffle sums);
+//   3. S = the members whose interval H32 (1 +- eta) reaches the k'-th smallest H32,
+//      sorted by (H32, id); neighbours in S whose intervals overlap at or above rank
+//      k' are re-scored in FP64 the same way (one warp each);
+//   4. S ordered by (value, id); the first k' are the result.
 // Members of B get their exact FP32 (or FP64) value as their candidate distance;
 // the others keep the refine's value.  Returned distances are within eta (relative)
-// of the FP64 Hausdorff value, or its FP32 rounding where FP64 decided.
+// of the FP64 Hausdorff value, or are its FP32 rounding where FP64 decided.
+// S is held in shared memory with room for max(256, 4 k) candidates; more near-ties
+// than that at the k-th set a device status bit.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -43,11 +50,13 @@ namespace bvss {
 
 namespace {
 
-constexpr int kBT = 256;          // threads of every boundary kernel (16 x 16 pair grid)
-constexpr int kTile = 32;         // query vectors x rows per pair tile
+constexpr int kBT = 256;          // threads of the boundary kernel
+constexpr int kBW = kBT / 32;     // its warps
+constexpr int kTile = 32;         // CTA-tile form: query vectors x rows per pair tile
 constexpr int kTP = kTile + 1;    // padded smem row
 constexpr int kMaxS = 4096;       // candidates that may tie with the k-th (sorted in smem)
-constexpr int kExactCTAs = 8;     // CTAs per query set in k_band_exact
+constexpr int kWarpMaxD = 1024;   // warp form up to this dimension (8 float4 per lane)
+constexpr int kHausSmem = 2 * kTile * kTP + BVSS_MAX_QSET + kTile + 2;   // CTA-tile T's
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
 
@@ -106,16 +115,23 @@ __device__ T haus_exact(const float *__restrict__ Q, int mq, const float *__rest
                 qs[0] = (T)x.x; qs[1] = (T)x.y; qs[2] = (T)x.z; qs[3] = (T)x.w;
                 vs[0] = (T)y.x; vs[1] = (T)y.y; vs[2] = (T)y.z; vs[3] = (T)y.w;
                 __syncthreads();
+                // each chunk of 32 dimensions is summed on its own, then added: the
+                // rounding bound grows with 32 + d/32 terms instead of d
+                T part[2][2] = {{0, 0}, {0, 0}};
 #pragma unroll 8
                 for (int kk = 0; kk < kTile; ++kk) {
                     const T q0 = Qs[tx * kTP + kk], q1 = Qs[(tx + 16) * kTP + kk];
                     const T w0 = Vs[ty * kTP + kk], w1 = Vs[(ty + 16) * kTP + kk];
                     const T d00 = q0 - w0, d01 = q0 - w1, d10 = q1 - w0, d11 = q1 - w1;
-                    acc[0][0] = fma(d00, d00, acc[0][0]);
-                    acc[0][1] = fma(d01, d01, acc[0][1]);
-                    acc[1][0] = fma(d10, d10, acc[1][0]);
-                    acc[1][1] = fma(d11, d11, acc[1][1]);
+                    part[0][0] = fma(d00, d00, part[0][0]);
+                    part[0][1] = fma(d01, d01, part[0][1]);
+                    part[1][0] = fma(d10, d10, part[1][0]);
+                    part[1][1] = fma(d11, d11, part[1][1]);
                 }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) acc[i][j] += part[i][j];
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -149,8 +165,9 @@ __device__ T haus_exact(const float *__restrict__ Q, int mq, const float *__rest
     return root(h2);
 }
 
-// k-th smallest (1-based) of the n keys in shared memory, by the whole CTA: radix
-// select over four 8-bit digits.  hist: 256 ints; sh: 2 ints.
+// k-th smallest (1-based, 1 <= k <= n) of the n keys in shared memory, by the whole
+// CTA: radix select over four 8-bit digits, the digit found with a block-wide scan.
+// sh: kBW + 3 ints.
 __device__ uint32_t block_kth(const uint32_t *keys, int n, int k, int *hist, int *sh) {
     uint32_t prefix = 0, mask = 0;
     for (int shift = 24; shift >= 0; shift -= 8) {
@@ -161,29 +178,29 @@ __device__ uint32_t block_kth(const uint32_t *keys, int n, int k, int *hist, int
             if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int cum = 0, sel = 255;
-            for (int b = 0; b < 256; ++b) {
-                if (cum + hist[b] >= k) {
-                    sel = b;
-                    break;
-                }
-                cum += hist[b];
-            }
-            sh[0] = sel;
-            sh[1] = k - cum;
+        // kBT == 256: one bin per thread
+        const int c = hist[threadIdx.x];
+        int tot;
+        const int before = block_excl_scan<kBT>(c, sh, &tot);
+        if (before < k && before + c >= k) {
+            sh[kBW + 1] = threadIdx.x;
+            sh[kBW + 2] = k - before;
         }
         __syncthreads();
-        prefix |= (uint32_t)sh[0] << shift;
+        prefix |= (uint32_t)sh[kBW + 1] << shift;
         mask |= 0xFFu << shift;
-        k = sh[1];
+        k = sh[kBW + 2];
         __syncthreads();
     }
     return prefix;
 }
 
-// eta: relative error bound of a direct FP32 distance in d dimensions
+// relative error bound of a direct FP32 distance summed in one chain over d dimensions
 __device__ __forceinline__ float eta_of(int d) { return (float)(d + 4) * 5.9604645e-8f; }
+// the same for this stage's own FP32 distances (warp and CTA-tile forms)
+__device__ __forceinline__ float eta_exact(int d) {
+    return (float)(40 + (d + 31) / 32) * 5.9604645e-8f;
+}
 
 // A query vector's norm and the norm of its rounding error in the refine's copy:
 // form 1 BF16 (round to nearest), form 2 FP8 E4M3 with the vector's own scale
@@ -223,164 +240,371 @@ __device__ void query_round_err(const float *x, int d, int form, float &norm, fl
     err = __fmul_ru(__fsqrt_ru(e), up);
 }
 
-// per query set: every candidate's interval, tau and the band (ascending candidate slot)
-__global__ void __launch_bounds__(kBT)
-k_band_sel(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int d, int form,
-           const float *__restrict__ stats, float *__restrict__ cand_dist,
-           const longlong2 *__restrict__ pair, const int32_t *__restrict__ thr, int C, int k,
-           int32_t *__restrict__ band, int32_t *__restrict__ band_n) {
-    extern __shared__ uint32_t bsm[];
-    uint32_t *hik = bsm;                                      // C keys: bits of hi
-    float *lov = reinterpret_cast<float *>(bsm + C);          // C values: lo
+// NJ: float4 of a row per lane (dimensions 4 lane + 128 j, j < NJ): d <= 128 NJ
+constexpr int kNI = BVSS_MAX_QSET / 32;   // query vectors per lane (row-minimum owners)
+
+// one database row into the lane's registers: dimensions 4 lane + 128 j
+template <int NJ>
+__device__ __forceinline__ void load_row(const float *__restrict__ v, int d, float4 (&r)[NJ]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = 4 * lane + 128 * j;
+        if (k < d) r[j] = *reinterpret_cast<const float4 *>(v + k);
+    }
+}
+
+// |q_a - v|^2 for the four query vectors a0 .. a0 + 3 (those below mq) and the row in r,
+// each lane summing its dimensions in FP32 and a shuffle tree adding the lanes: four
+// independent chains, so their latencies overlap.  Warp-uniform results.
+template <int NJ>
+__device__ __forceinline__ void pair4_sq(const float *Q, int a0, int mq, int d,
+                                         const float4 (&r)[NJ], float (&s)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) s[g] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = 4 * lane + 128 * j;
+        if (k < d) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (a0 + g < mq) {
+                    const float4 x = *reinterpret_cast<const float4 *>(Q + (int64_t)(a0 + g) * d + k);
+                    float t = x.x - r[j].x;
+                    s[g] = fmaf(t, t, s[g]);
+                    t = x.y - r[j].y;
+                    s[g] = fmaf(t, t, s[g]);
+                    t = x.z - r[j].z;
+                    s[g] = fmaf(t, t, s[g]);
+                    t = x.w - r[j].w;
+                    s[g] = fmaf(t, t, s[g]);
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int g = 0; g < 4; ++g) s[g] += __shfl_xor_sync(0xffffffffu, s[g], o);
+}
+
+// The same for one query vector in FP64 (each difference and square in double).
+template <int NJ>
+__device__ __forceinline__ double pair_sq64(const float *q, int d, const float4 (&r)[NJ]) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = 4 * lane + 128 * j;
+        if (k < d) {
+            const float4 x = *reinterpret_cast<const float4 *>(q + k);
+            double t = (double)x.x - (double)r[j].x;
+            s = fma(t, t, s);
+            t = (double)x.y - (double)r[j].y;
+            s = fma(t, t, s);
+            t = (double)x.z - (double)r[j].z;
+            s = fma(t, t, s);
+            t = (double)x.w - (double)r[j].w;
+            s = fma(t, t, s);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__device__ __forceinline__ float warp_max(float m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
+// One FP32 pass of a warp over V's rows against Q (mq x d, row stride d): the row
+// minima of the squared distances of query vectors 32 i + lane go to rm[i] (owner
+// lanes), the return value is the largest column minimum.  The next row's loads are in
+// flight while a row is scored.  d % 4 == 0, d <= kWarpMaxD, 1 <= mq <= BVSS_MAX_QSET.
+template <int NJ>
+__device__ float warp_scan32(const float *Q, int mq, const float *__restrict__ V, int mv, int d,
+                             float (&rm)[kNI]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < kNI; ++i) rm[i] = inf_f();
+    float cmax = 0.0f;
+    float4 rn[NJ];
+    load_row<NJ>(V, d, rn);
+    for (int b = 0; b < mv; ++b) {
+        float4 r[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) r[j] = rn[j];
+        if (b + 1 < mv) load_row<NJ>(V + (int64_t)(b + 1) * d, d, rn);
+        float cmin = inf_f();
+#pragma unroll
+        for (int i = 0; i < kNI; ++i)
+            for (int l = 0; l < 32; l += 4) {
+                const int a0 = 32 * i + l;
+                if (a0 >= mq) break;   // uniform over the warp
+                float s[4];
+                pair4_sq<NJ>(Q, a0, mq, d, r, s);
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    if (a0 + g < mq) {
+                        cmin = fminf(cmin, s[g]);
+                        if (lane == l + g) rm[i] = fminf(rm[i], s[g]);
+                    }
+            }
+        cmax = fmaxf(cmax, cmin);
+    }
+    return cmax;
+}
+
+// the largest row minimum over the valid query vectors
+__device__ __forceinline__ float rows_max(const float (&rm)[kNI], int mq) {
+    const int lane = threadIdx.x & 31;
+    float m = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kNI; ++i)
+        if (32 * i + lane < mq) m = fmaxf(m, rm[i]);
+    return warp_max(m);
+}
+
+// Hausdorff distance (Def. 4) of Q and V in FP32 by one warp (warp-uniform).
+template <int NJ>
+__device__ float warp_haus32(const float *Q, int mq, const float *__restrict__ V, int mv, int d) {
+    float rm[kNI];
+    const float cmax = warp_scan32<NJ>(Q, mq, V, mv, d, rm);
+    return sqrtf(fmaxf(cmax, rows_max(rm, mq)));
+}
+
+// Hausdorff distance of Q and V decided in FP64 on the pairs that can attain it.  With
+// the FP32 squared distances s' within a factor (1 +- e) of the true s: a row (query
+// vector) whose FP32 minimum is below H'^2 (1 - e) / (1 + e) cannot attain the maximum,
+// nor a column (row of V) likewise, and inside a row or column only pairs with
+// s' (1 - e) <= min' (1 + e) can be its minimum.  A first FP32 pass gives the row
+// minima and H'^2, a second one recomputes every pair, and the pairs that pass both
+// tests are re-scored in FP64; the maximum over the surviving rows and columns of their
+// FP64 minima is H^2.
+template <int NJ>
+__device__ __noinline__ double warp_haus64(const float *Q, int mq, const float *__restrict__ V,
+                                           int mv, int d) {
+    const int lane = threadIdx.x & 31;
+    float rm[kNI];
+    const float c32 = warp_scan32<NJ>(Q, mq, V, mv, d, rm);
+    const float h2 = fmaxf(c32, rows_max(rm, mq));
+    const float e = 2.0f * eta_exact(d);
+    const float lo_reach = __fdiv_rd(__fmul_rd(h2, 1.0f - e), 1.0f + e);
+    double rm64[kNI];
+#pragma unroll
+    for (int i = 0; i < kNI; ++i) rm64[i] = __longlong_as_double(0x7ff0000000000000ll);
+    double best = 0.0;
+    float4 r[NJ];
+    for (int b = 0; b < mv; ++b) {
+        load_row<NJ>(V + (int64_t)b * d, d, r);
+        float sv[kNI];
+        float cmin = inf_f();
+#pragma unroll
+        for (int i = 0; i < kNI; ++i) {
+            sv[i] = inf_f();
+            for (int l = 0; l < 32; l += 4) {
+                const int a0 = 32 * i + l;
+                if (a0 >= mq) break;
+                float s[4];
+                pair4_sq<NJ>(Q, a0, mq, d, r, s);
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    if (a0 + g < mq) {
+                        cmin = fminf(cmin, s[g]);
+                        if (lane == l + g) sv[i] = s[g];
+                    }
+            }
+        }
+        const bool col_rel = cmin >= lo_reach;
+        const float col_cut = __fmul_ru(cmin, 1.0f + e);
+        double cm64 = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+        for (int i = 0; i < kNI; ++i)
+            for (int l = 0; l < 32; ++l) {
+                const int a = 32 * i + l;
+                if (a >= mq) break;
+                const float sa = __shfl_sync(0xffffffffu, sv[i], l);
+                const float ra = __shfl_sync(0xffffffffu, rm[i], l);
+                const float sl = __fmul_rd(sa, 1.0f - e);
+                const bool row_pair = ra >= lo_reach && sl <= __fmul_ru(ra, 1.0f + e);
+                const bool col_pair = col_rel && sl <= col_cut;
+                if (row_pair || col_pair) {   // uniform over the warp
+                    const double s64 = pair_sq64<NJ>(Q + (int64_t)a * d, d, r);
+                    if (row_pair && lane == l) rm64[i] = fmin(rm64[i], s64);
+                    if (col_pair) cm64 = fmin(cm64, s64);
+                }
+            }
+        if (col_rel) best = fmax(best, cm64);
+    }
+    // rows that can attain the maximum hold a finite FP64 minimum (their own arg-min pair
+    // passed both tests); the others are left out
+    double m = best;
+#pragma unroll
+    for (int i = 0; i < kNI; ++i)
+        if (32 * i + lane < mq && rm[i] >= lo_reach) m = fmax(m, rm64[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return sqrt(m);
+}
+
+// S's room: max(256, 4 k) rounded up to a power of two, at most kMaxS
+__host__ __device__ inline int s_cap(int k) {
+    int c = 256;
+    while (c < 4 * k && c < kMaxS) c <<= 1;
+    return c;
+}
+
+// Bytes of k_boundary's dynamic shared memory: the CTA-tile form's doubles (d >
+// kWarpMaxD only), S's values, keys and slots, the staged query set (q_floats), and
+// per candidate its hi key (then a band slot) and its lo (then the band's exact values).
+__host__ __device__ inline size_t boundary_smem(int C, int k, int q_floats, bool tiles) {
+    return (tiles ? sizeof(double) * kHausSmem : 0) +
+           (sizeof(double) + sizeof(unsigned long long) + sizeof(int)) * s_cap(k) +
+           sizeof(float) * (size_t)q_floats + 2 * sizeof(uint32_t) * (size_t)C;
+}
+
+// NJ: the warp form's float4 per lane and row (d <= 128 NJ); NJ = 0: the CTA-tile form
+template <int NJ>
+__global__ void __launch_bounds__(kBT, NJ >= 8 ? 1 : 2)
+k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int d, int form,
+           const float *__restrict__ stats, const float *__restrict__ vec,
+           const int64_t *__restrict__ set_off, const int32_t *__restrict__ cand,
+           const int32_t *__restrict__ thr, int C, int k, const longlong2 *__restrict__ pair,
+           float *__restrict__ cand_dist, int64_t *__restrict__ out_ids,
+           float *__restrict__ out_dist, int *__restrict__ err, int q_floats) {
+    constexpr bool tiles = NJ == 0;
+    constexpr int NJW = NJ > 0 ? NJ : 1;   // the warp form's width (unused when tiles)
+    extern __shared__ __align__(16) unsigned char bsm[];
+    const int cap = s_cap(k);
+    double *hsm = reinterpret_cast<double *>(bsm);
+    double *sval = hsm + (tiles ? kHausSmem : 0);
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(sval + cap);
+    float *Qs = reinterpret_cast<float *>(skey + cap);
+    uint32_t *hik = reinterpret_cast<uint32_t *>(Qs + q_floats);
+    float *lov = reinterpret_cast<float *>(hik + C);
+    int *mem = reinterpret_cast<int *>(hik);   // the band's slots, once tau is known
+    int *sslot = reinterpret_cast<int *>(lov + C);
     __shared__ int hist[256];
-    __shared__ int sh[kBT / 32 + 2];
-    __shared__ float qst[2];                                  // max norm, max rounding error
+    __shared__ int sh[kBW + 3];
+    __shared__ float qst[2];   // largest norm of a rounded query vector, largest rounding error
     const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_sel = thr[q * 4 + 3];
+    const int kp = k < n_sel ? k : n_sel;
     float *cd = cand_dist + (int64_t)q * C;
+    const int32_t *cq = cand + (int64_t)q * C;
     for (int j = n_sel + tid; j < C; j += kBT) cd[j] = inf_f();
-    if (n_sel <= 0) {
-        if (tid == 0) band_n[q] = 0;
-        return;
+    for (int t = kp + tid; t < k; t += kBT) {
+        out_ids[(int64_t)q * k + t] = -1;
+        out_dist[(int64_t)q * k + t] = inf_f();
+    }
+    if (kp <= 0) return;   // uniform over the CTA
+    const int64_t a0 = qoff[q];
+    const int mq = (int)(qoff[q + 1] - a0);
+    const float *Q = qvec + a0 * d;
+    if (mq * d <= q_floats) {
+        for (int e = tid; e < mq * d / 4; e += kBT)
+            reinterpret_cast<float4 *>(Qs)[e] = reinterpret_cast<const float4 *>(Q)[e];
+        Q = Qs;
     }
     if (tid < 2) qst[tid] = 0.0f;
     __syncthreads();
-    const int64_t a0 = qoff[q];
-    const int mq = (int)(qoff[q + 1] - a0);
-    for (int a = warp; a < mq; a += kBT / 32) {
-        float nrm, err;
-        query_round_err(qvec + (a0 + a) * d, d, form, nrm, err);
+    // ---- 1. intervals, tau and the band ----------------------------------------------
+    for (int a = warp; a < mq; a += kBW) {
+        float nrm, er;
+        query_round_err(Q + (int64_t)a * d, d, form, nrm, er);
         if (lane == 0) {
-            smem_max(&qst[0], __fadd_ru(nrm, err));   // norm of the rounded vector, at most
-            smem_max(&qst[1], err);
+            smem_max(&qst[0], __fadd_ru(nrm, er));
+            smem_max(&qst[1], er);
         }
     }
     __syncthreads();
-    const float eta = eta_of(d);
-    const float eV = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
-    const float nsum = __fadd_ru(qst[0], __fadd_ru(stats[0], eV));
-    // GEMM-form squared-distance error bound (d + 8) 2^-23 (N_Q + N_V)^2
-    const float D = __fmul_ru((float)(d + 8) * 1.1920929e-7f, __fmul_ru(nsum, nsum));
-    const float e = __fadd_ru(qst[1], eV);
-    const longlong2 *pq = pair + (int64_t)q * C;
-    for (int j = tid; j < n_sel; j += kBT) {
-        float lo, hi;
-        if (form == 0) {
-            const float r = cd[j];
-            const float rl = __fmul_rd(r, 1.0f - eta), rh = __fmul_ru(r, 1.0f + 2.0f * eta);
-            const float D2 = __fmul_ru(2.0f, D);
-            lo = __fsqrt_rd(fmaxf(__fsub_rd(__fmul_rd(rl, rl), D2), 0.0f));
-            hi = __fsqrt_ru(__fadd_ru(__fmul_ru(rh, rh), D2));
-        } else {
-            const float h2 = __uint_as_float((uint32_t)((unsigned long long)pq[j].x >> 32));
-            lo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(h2, D), 0.0f)), e), 0.0f);
-            hi = __fadd_ru(__fsqrt_ru(__fadd_ru(h2, D)), e);
+    {
+        const float eta_d = eta_of(d);
+        const float eV = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
+        const float nsum = __fadd_ru(qst[0], __fadd_ru(stats[0], eV));
+        // GEMM-form squared-distance error bound (d + 8) 2^-23 (N_Q + N_V)^2
+        const float D = __fmul_ru((float)(d + 8) * 1.1920929e-7f, __fmul_ru(nsum, nsum));
+        const float e = __fadd_ru(qst[1], eV);
+        const longlong2 *pq = pair + (int64_t)q * C;
+        for (int j = tid; j < n_sel; j += kBT) {
+            float lo, hi;
+            if (form == 0) {
+                const float r = cd[j];
+                const float rl = __fmul_rd(r, 1.0f - eta_d), rh = __fmul_ru(r, 1.0f + 2.0f * eta_d);
+                const float D2 = __fmul_ru(2.0f, D);
+                lo = __fsqrt_rd(fmaxf(__fsub_rd(__fmul_rd(rl, rl), D2), 0.0f));
+                hi = __fsqrt_ru(__fadd_ru(__fmul_ru(rh, rh), D2));
+            } else {
+                const float h2 = __uint_as_float((uint32_t)((unsigned long long)pq[j].x >> 32));
+                lo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(h2, D), 0.0f)), e), 0.0f);
+                hi = __fadd_ru(__fsqrt_ru(__fadd_ru(h2, D)), e);
+            }
+            hik[j] = __float_as_uint(hi);   // non-negative: bit order is value order
+            lov[j] = lo;
         }
-        hik[j] = __float_as_uint(hi);   // non-negative: bit order is value order
-        lov[j] = lo;
     }
     __syncthreads();
-    const int kp = k < n_sel ? k : n_sel;
     const float tau = __uint_as_float(block_kth(hik, n_sel, kp, hist, sh));
-    // the band, in slot order
-    int base = 0;
+    int nb = 0;   // mem[] overwrites hik[] from here on (block_kth has returned)
     for (int j0 = 0; j0 < n_sel; j0 += kBT) {
         const int j = j0 + tid;
         const int in = j < n_sel && lov[j] <= tau;
         int tot;
         const int pos = block_excl_scan<kBT>(in, sh, &tot);
-        if (in) band[(int64_t)q * C + base + pos] = j;
-        base += tot;
+        if (in) mem[nb + pos] = j;
+        nb += tot;
     }
-    if (tid == 0) band_n[q] = base;
-}
-
-// direct FP32 Hausdorff value of every band member
-__global__ void __launch_bounds__(kBT)
-k_band_exact(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-             const float *__restrict__ vec, const int64_t *__restrict__ set_off, int d,
-             const int32_t *__restrict__ cand, int C, const int32_t *__restrict__ band,
-             const int32_t *__restrict__ band_n, float *__restrict__ cand_dist) {
-    __shared__ float sm[2 * kTile * kTP + BVSS_MAX_QSET + kTile + 2];
-    const int q = blockIdx.y;
-    const int nb = band_n[q];
-    const int64_t a0 = qoff[q];
-    const int mq = (int)(qoff[q + 1] - a0);
-    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
-        const int j = band[(int64_t)q * C + t];
-        const int64_t id = cand[(int64_t)q * C + j];
-        const int64_t r0 = set_off[id];
-        const int mv = (int)(set_off[id + 1] - r0);
-        const float h = haus_exact<float>(qvec + a0 * d, mq, vec + r0 * d, mv, d, sm);
-        if (threadIdx.x == 0) cand_dist[(int64_t)q * C + j] = h;
-    }
-}
-
-// Bytes of k_band_order's dynamic shared memory: the FP64 pair tiles, S's values
-// (double), sort keys (uint64) and slots (int), and one radix-select key per candidate.
-__host__ __device__ inline size_t order_smem(int C) {
-    return sizeof(double) * (2 * kTile * kTP + BVSS_MAX_QSET + kTile + 2) +
-           (sizeof(double) + sizeof(unsigned long long) + sizeof(int)) * kMaxS +
-           sizeof(uint32_t) * (size_t)C;
-}
-
-// per query set: S, FP64 where FP32 cannot order, the k' smallest (value, id)
-__global__ void __launch_bounds__(kBT)
-k_band_order(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-             const float *__restrict__ vec, const int64_t *__restrict__ set_off, int d,
-             const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int k,
-             const int32_t *__restrict__ band, const int32_t *__restrict__ band_n,
-             float *__restrict__ cand_dist, int64_t *__restrict__ out_ids,
-             float *__restrict__ out_dist, int *__restrict__ err) {
-    extern __shared__ double osm[];
-    double *hsm = osm;                                        // haus_exact<double> tiles
-    double *sval = hsm + (2 * kTile * kTP + BVSS_MAX_QSET + kTile + 2);
-    unsigned long long *skey = reinterpret_cast<unsigned long long *>(sval + kMaxS);
-    int *sslot = reinterpret_cast<int *>(skey + kMaxS);
-    uint32_t *keys = reinterpret_cast<uint32_t *>(sslot + kMaxS);
-    __shared__ int hist[256];
-    __shared__ int sh[kBT / 32 + 2];
-    const int q = blockIdx.x, tid = threadIdx.x;
-    const int n_sel = thr[q * 4 + 3];
-    const int kp = k < n_sel ? k : n_sel;
-    for (int t = kp + tid; t < k; t += kBT) {
-        out_ids[(int64_t)q * k + t] = -1;
-        out_dist[(int64_t)q * k + t] = inf_f();
-    }
-    if (kp <= 0) return;
-    const int nb = band_n[q];
-    const int32_t *bq = band + (int64_t)q * C;
-    const int32_t *cq = cand + (int64_t)q * C;
-    float *cd = cand_dist + (int64_t)q * C;
-    for (int t = tid; t < nb; t += kBT) keys[t] = __float_as_uint(cd[bq[t]]);
     __syncthreads();
-    const float vk = __uint_as_float(block_kth(keys, nb, kp, hist, sh));
-    const float eta = eta_of(d);
+    // ---- 2. the direct FP32 Hausdorff value of every band member -----------------------
+    if (!tiles) {
+        for (int t = warp; t < nb; t += kBW) {
+            const int j = mem[t];
+            const int64_t r0 = set_off[cq[j]];
+            const float h = warp_haus32<NJW>(Q, mq, vec + r0 * d, (int)(set_off[cq[j] + 1] - r0), d);
+            if (lane == 0) {
+                lov[t] = h;
+                cd[j] = h;
+            }
+        }
+    } else {
+        float *fsm = reinterpret_cast<float *>(hsm);
+        for (int t = 0; t < nb; ++t) {
+            const int j = mem[t];
+            const int64_t r0 = set_off[cq[j]];
+            const float h = haus_exact<float>(Q, mq, vec + r0 * d,
+                                              (int)(set_off[cq[j] + 1] - r0), d, fsm);
+            if (tid == 0) {
+                lov[t] = h;
+                cd[j] = h;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- 3. S: the members that can reach rank k', sorted by (H32, id) ----------------
+    // the exact values are non-negative: their bits order as they do
+    const float vk =
+        __uint_as_float(block_kth(reinterpret_cast<const uint32_t *>(lov), nb, kp, hist, sh));
+    const float eta = eta_exact(d);
     const float reach = __fmul_ru(vk, 1.0f + eta);
-    // S: members whose interval reaches the k'-th value, in band order
     int ns = 0;
     for (int t0 = 0; t0 < nb; t0 += kBT) {
         const int t = t0 + tid;
-        float h = 0.0f;
-        int in = 0;
-        if (t < nb) {
-            h = __uint_as_float(keys[t]);
-            in = __fmul_rd(h, 1.0f - eta) <= reach;
-        }
+        const int in = t < nb && __fmul_rd(lov[t], 1.0f - eta) <= reach;
         int tot;
         const int pos = block_excl_scan<kBT>(in, sh, &tot);
-        if (in && ns + pos < kMaxS) {
-            skey[ns + pos] = ((unsigned long long)__float_as_uint(h) << 32) |
-                             (uint32_t)cq[bq[t]];
-            sslot[ns + pos] = bq[t];
+        if (in && ns + pos < cap) {
+            skey[ns + pos] = ((unsigned long long)__float_as_uint(lov[t]) << 32) |
+                             (uint32_t)cq[mem[t]];
+            sslot[ns + pos] = mem[t];
         }
         ns += tot;
     }
-    if (ns > kMaxS) {
+    if (ns > cap) {
         if (tid == 0) atomicOr(err, kErrBandOverflow);
-        ns = kMaxS;
+        ns = cap;
     }
-    // sort S by (H32, id): bitonic over the next power of two, padded with the largest key
     int np = 1;
     while (np < ns) np <<= 1;
     for (int t = ns + tid; t < np; t += kBT) {
@@ -398,15 +622,15 @@ k_band_order(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     if ((a > b) == asc) {
                         skey[t] = b;
                         skey[u] = a;
-                        const int s = sslot[t];
+                        const int sl = sslot[t];
                         sslot[t] = sslot[u];
-                        sslot[u] = s;
+                        sslot[u] = sl;
                     }
                 }
             }
             __syncthreads();
         }
-    // neighbours that FP32 cannot order, at or above rank k': mark both (slot bit 30)
+    // neighbours that FP32 cannot order, at or above rank k': both marked (slot bit 30)
     for (int t = tid; t < ns; t += kBT) sval[t] = (double)__uint_as_float((uint32_t)(skey[t] >> 32));
     __syncthreads();
     for (int t = tid; t + 1 < ns && t < kp; t += kBT) {
@@ -418,25 +642,39 @@ k_band_order(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         }
     }
     __syncthreads();
-    const int64_t a0 = qoff[q];
-    const int mq = (int)(qoff[q + 1] - a0);
-    for (int t = 0; t < ns; ++t) {
-        const int sl = sslot[t];   // uniform over the CTA
-        if (!(sl & (1 << 30))) continue;
-        const int j = sl & 0x3fffffff;
-        const int64_t id = cq[j];
-        const int64_t r0 = set_off[id];
-        const double h = haus_exact<double>(qvec + a0 * d, mq, vec + r0 * d,
-                                            (int)(set_off[id + 1] - r0), d, hsm);
-        if (tid == 0) {
-            sval[t] = h;
-            cd[j] = (float)h;
+    // ---- FP64 for the marked members: the u-th marked one on warp u mod kBW --------------
+    if (!tiles) {
+        int u = 0;
+        for (int t = 0; t < ns; ++t) {
+            const int sl = sslot[t];
+            if (!(sl & (1 << 30))) continue;
+            if (u++ % kBW != warp) continue;
+            const int j = sl & 0x3fffffff;
+            const int64_t r0 = set_off[cq[j]];
+            const double h = warp_haus64<NJW>(Q, mq, vec + r0 * d, (int)(set_off[cq[j] + 1] - r0), d);
+            if (lane == 0) {
+                sval[t] = h;
+                cd[j] = (float)h;
+            }
+        }
+    } else {
+        for (int t = 0; t < ns; ++t) {
+            const int sl = sslot[t];
+            if (!(sl & (1 << 30))) continue;
+            const int j = sl & 0x3fffffff;
+            const int64_t r0 = set_off[cq[j]];
+            const double h = haus_exact<double>(Q, mq, vec + r0 * d,
+                                                (int)(set_off[cq[j] + 1] - r0), d, hsm);
+            if (tid == 0) {
+                sval[t] = h;
+                cd[j] = (float)h;
+            }
         }
     }
     __syncthreads();
+    // ---- 4. order by (value, id): FP64 reorders only inside runs of overlapping
+    // neighbours, so an insertion sort does no work elsewhere ------------------------------
     if (tid == 0) {
-        // FP64 reorders only inside runs of overlapping neighbours: insertion sort by
-        // (value, id) does no work elsewhere
         for (int t = 1; t < ns; ++t) {
             const double v = sval[t];
             const unsigned long long kk = skey[t];
@@ -460,30 +698,31 @@ k_band_order(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
 
 }  // namespace
 
-size_t band_workspace_ints(int64_t n_q, int C) { return (size_t)n_q * C + (size_t)n_q; }
+// query floats staged in shared memory when the batch's largest query set fits this
+constexpr int kQStageFloats = 16384;   // 64 KB
+constexpr size_t kSmemLimit = 232448;    // 227 KB opt-in per CTA
 
-cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int d, int form,
-                             const float *stats, const float *vec, const int64_t *set_off,
-                             const int32_t *cand, const int32_t *thr, int C, int k,
-                             const longlong2 *pair, float *cand_dist, int32_t *band,
+cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int max_mq, int d,
+                             int form, const float *stats, const float *vec,
+                             const int64_t *set_off, const int32_t *cand, const int32_t *thr,
+                             int C, int k, const longlong2 *pair, float *cand_dist,
                              int64_t *out_ids, float *out_dist, int *err, cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
-    if (C > BVSS_MAX_C || form < 0 || form > 2 || d % 4 != 0) return cudaErrorInvalidValue;
-    int32_t *band_n = band + (size_t)n_q * C;
-    const size_t sel_smem = 2 * sizeof(uint32_t) * (size_t)C;
-    cudaError_t e = cudaFuncSetAttribute(k_band_sel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sel_smem);
+    if (C > BVSS_MAX_C || k < 1 || k > BVSS_MAX_K || form < 0 || form > 2 || d % 4 != 0 ||
+        max_mq < 1 || max_mq > BVSS_MAX_QSET)
+        return cudaErrorInvalidValue;
+    int q_floats = max_mq * d <= kQStageFloats ? max_mq * d : 0;
+    const bool tiles = d > kWarpMaxD;
+    if (boundary_smem(C, k, q_floats, tiles) > kSmemLimit) q_floats = 0;   // read in place
+    const size_t smem = boundary_smem(C, k, q_floats, tiles);
+    if (smem > kSmemLimit) return cudaErrorInvalidValue;
+    auto kern = tiles ? k_boundary<0> : d <= 128 ? k_boundary<1> : d <= 256 ? k_boundary<2>
+              : d <= 512 ? k_boundary<4> : k_boundary<8>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_band_sel<<<n_q, kBT, sel_smem, st>>>(qvec, qoff, d, form, stats, cand_dist, pair, thr, C,
-                                           k, band, band_n);
-    k_band_exact<<<dim3(kExactCTAs, n_q), kBT, 0, st>>>(qvec, qoff, vec, set_off, d, cand, C,
-                                                        band, band_n, cand_dist);
-    const size_t ord_smem = order_smem(C);
-    e = cudaFuncSetAttribute(k_band_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ord_smem);
-    if (e != cudaSuccess) return e;
-    k_band_order<<<n_q, kBT, ord_smem, st>>>(qvec, qoff, vec, set_off, d, cand, thr, C, k, band,
-                                             band_n, cand_dist, out_ids, out_dist, err);
+    kern<<<n_q, kBT, smem, st>>>(qvec, qoff, d, form, stats, vec, set_off, cand, thr, C, k, pair,
+                                 cand_dist, out_ids, out_dist, err, q_floats);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,6 @@ struct Workspace {
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
-    int32_t *band = nullptr;      // boundary band slots and counts      band_workspace_ints
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
     float *out_dist = nullptr;
     int cap_k = 0;
@@ -212,16 +211,15 @@ cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, cons
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------
 // form: the refine that ran (0 FP32, 1 BF16 tensor cores, 2 FP8 tensor cores); stats: the
-// index's rstat; pair: the MMA forms' records (value in the high word of .x); band:
-// band_workspace_ints(n_q, C) ints of scratch.  Band members' cand_dist become their exact
-// values; cand_dist[q][n_sel..C) is padded with +inf; results as launch_topk.
-size_t band_workspace_ints(int64_t n_q, int C);
-cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int d, int form,
-                             const float *stats, const float *vec, const int64_t *set_off,
-                             const int32_t *cand, const int32_t *thr, int C, int k,
-                             const longlong2 *pair, float *cand_dist, int32_t *band,
+// index's rstat; pair: the MMA forms' records (value in the high word of .x); max_mq: the
+// batch's largest query set.  Band members' cand_dist become their exact values;
+// cand_dist[q][n_sel..C) is padded with +inf; results as launch_topk.
+cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int max_mq, int d,
+                             int form, const float *stats, const float *vec,
+                             const int64_t *set_off, const int32_t *cand, const int32_t *thr,
+                             int C, int k, const longlong2 *pair, float *cand_dist,
                              int64_t *out_ids, float *out_dist, int *err, cudaStream_t st);
-constexpr int kBandKernels = 3;
+constexpr int kBandKernels = 1;
 // rstat of an index (x16 / x8 may be null: their entries stay 0)
 cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,
                                const uint8_t *x8, const float *sc8, float *stats,

@@ -82,3 +82,19 @@ def test_committed_traffic_entries_name_existing_sources(bench):
     for name, t in bench.TRAFFIC.items():
         assert os.path.exists(os.path.join(bench.ROOT, t["source"])), name
         assert len(t["sha256"]) == 64 and t["bytes_per_unit"] > 0
+
+
+def test_fp64_recall_decides_with_the_oracle(bench, orc):
+    """Recall against the k smallest FP64 Hausdorff distances of the pooled lists."""
+    rng = np.random.default_rng(5)
+    sets = [rng.standard_normal((3, 8)).astype(np.float32) for _ in range(30)]
+    Q = rng.standard_normal((2, 8)).astype(np.float32)
+    truth = sorted(range(30), key=lambda i: (orc.haus(Q, sets[i]), i))
+    qoff = np.array([0, 2])
+    gt = np.array([truth[:6]])            # the ground truth's longer list
+    r, dist = bench.fp64_recall(np.array([truth[:4]]), gt, Q, qoff, lambda i: sets[i], 4)
+    assert r == 1.0
+    assert np.allclose(dist[0], [orc.haus(Q, sets[i]) for i in truth[:4]])
+    got = np.array([[truth[0], truth[1], truth[5], -1]])
+    r, dist = bench.fp64_recall(got, gt, Q, qoff, lambda i: sets[i], 4)
+    assert r == 0.5 and np.isinf(dist[0, 3])

@@ -6,7 +6,7 @@ boundary stage re-scores, directly in FP32 over all pairs, every candidate
 whose error interval reaches the k-th smallest upper bound, and in FP64 the
 candidates that FP32 cannot order at the top k.  So every form must return
 the oracle's ids (FP64 Hausdorff, ties by id) exactly, with distances within
-the stated (d + 4) 2^-24 relative bound of the oracle's FP64 values.
+the stated (36 + ceil(d / 32)) 2^-24 relative bound of the oracle's FP64 values.
 """
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ def bv():
 
 
 def _eta(d):
-    return (d + 4) * 2.0 ** -24
+    return (36 + -(-d // 32)) * 2.0 ** -24
 
 
 def _check(bv, orc, w, L, k, C, A, M, forms=FORMS):
