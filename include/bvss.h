@@ -107,13 +107,19 @@ typedef struct bvss_params {
                                query vectors are scaled and rounded to E4M3 the same way, the
                                squared distances are |q|^2 + |v|^2 - 2 s_q s_v (q8 . v8) of the
                                scaled values, and each candidate's distance is the FP32 distance
-                               of the pair that attains its Hausdorff value there.  Approximate:
-                               FP8 rounding (relative error up to 2^-4 per value) can pick another
-                               pair, so a distance can be off by about twice the rounding error
-                               of the vectors involved.  The top k are still exact as in
-                               bvss_query, through a boundary band that this error widens.  Batches
-                               with a query set of more than 32 vectors use the BF16 copy if the
-                               index has one, else the FP32 refine */
+                               of the pair that attains its Hausdorff value there (the trace's
+                               cand_dist outside the boundary band).  FP8 rounding (up to 2^-4
+                               relative per value) moves a distance by up to e_q + e_v, the
+                               norms of the two vectors' rounding errors; a band that wide holds
+                               nearly every candidate, so by default the band takes 3 standard
+                               deviations of the rounding model instead (independent zero-mean
+                               errors per value: sqrt(e_q^2 + e_v^2) / sqrt(d) per distance) and
+                               the top k are approximate; returned distances are still exact
+                               values (as in bvss_query) of the returned sets.  Batches with a
+                               query set of more than 32 vectors use the BF16 copy if the index
+                               has one, else the FP32 refine */
+#define BVSS_SEARCH_FP8_EXACT 16  /* with BVSS_SEARCH_FP8: the band from the rigorous bound, so
+                                     the top k are exact as in bvss_query */
 
 typedef struct bvss_search {
     int32_t k;      /* results per query set, 1..BVSS_MAX_K */
@@ -121,7 +127,7 @@ typedef struct bvss_search {
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
     int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2,
-                       BVSS_SEARCH_FP8 */
+                       BVSS_SEARCH_FP8, BVSS_SEARCH_FP8_EXACT */
     int32_t reserved;
 } bvss_search;
 
@@ -170,7 +176,8 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
  * C_Q / S_Q / P, first-layer gate (count >= M at one of the A positions),
  * the min(C, |F1|) smallest (Hamming, id) pairs, the Hausdorff distance
  * (Def. 4) of those candidates, then the k smallest (distance, id).
- * The k results are exact for every refine form: each candidate's refine value
+ * The k results are exact for every refine form (the FP8 form: with
+ * BVSS_SEARCH_FP8_EXACT): each candidate's refine value
  * comes with a rigorous error bound (rounding of the stored copy, FP32
  * accumulation); every candidate whose interval reaches the k-th smallest upper
  * bound is re-scored directly in FP32 over all pairs, and candidates that FP32

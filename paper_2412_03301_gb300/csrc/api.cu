@@ -324,7 +324,8 @@ int check_search(const bvss_index *ix, const bvss_search *s) {
     if ((s->flags & BVSS_SEARCH_ALG2) == 0 && (s->A < 1 || s->A > L || s->A > BVSS_MAX_A))
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
-    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2 | BVSS_SEARCH_FP8))
+    if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2 | BVSS_SEARCH_FP8 |
+                     BVSS_SEARCH_FP8_EXACT))
         return fail(BVSS_EINVAL, "unknown search flags");
     if ((s->flags & BVSS_SEARCH_FAST) && !ix->vec16)
         return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
@@ -439,7 +440,7 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     // line 23: the k smallest (distance, id), decided exactly around the k-th
     BVSS_CU(launch_band_topk(qv, b.qoff, nb, b.max_mq, d, form, ix->rstat, ix->vec, ix->set_off,
                              w.cand, w.thr, C, k, w.pair, w.cand_dist, b.ids, b.dist, ix->err,
-                             st));
+                             (s->flags & BVSS_SEARCH_FP8_EXACT) != 0, st));
     n += kBandKernels;
     *launches += n;
     return BVSS_OK;

@@ -10,6 +10,8 @@
 //     is off by at most D = (d + 8) 2^-23 (N_Q + N_V)^2 (N = largest norm), so the
 //     GEMM-form Hausdorff value is within D of H^2 and r^2 within 2D of it:
 //     lo = sqrt(r^2 - 2D) (1 - eta_d), hi = sqrt(r^2 + 2D) (1 + 2 eta_d).
+//   (The FP8 form by default replaces e by a stated tolerance, below: its rigorous
+//   band would hold nearly every candidate.)
 //   BF16 / FP8 forms: the GEMM-form Hausdorff value h of the rounded copies, packed
 //     into the pair record by the refine.  Rounding moves a vector x by e_x = |x - x'|
 //     and every pair distance by at most e_q + e_v (triangle inequality), so the
@@ -202,10 +204,24 @@ __device__ __forceinline__ float eta_exact(int d) {
     return (float)(40 + (d + 31) / 32) * 5.9604645e-8f;
 }
 
+// Binary digits below the point that x needs: x = integer * 2^-g for this g and no
+// smaller one (0 for integers and zero; subnormals report 200, beyond any usable grid).
+__device__ __forceinline__ int frac_bits(float x) {
+    const uint32_t u = __float_as_uint(x) & 0x7fffffffu;
+    if (u == 0) return 0;
+    const int ex = (int)(u >> 23);
+    if (ex == 0) return 200;
+    const uint32_t mant = (u & 0x7fffffu) | 0x800000u;   // x = mant * 2^(ex - 150)
+    const int g = 150 - ex - (__ffs(mant) - 1);
+    return g > 0 ? g : 0;
+}
+
 // A query vector's norm and the norm of its rounding error in the refine's copy:
 // form 1 BF16 (round to nearest), form 2 FP8 E4M3 with the vector's own scale
 // (largest magnitude -> 448, round to nearest, saturating), form 0 none.  One warp.
-__device__ void query_round_err(const float *x, int d, int form, float &norm, float &err) {
+// gbits: the largest frac_bits of its values.
+__device__ void query_round_err(const float *x, int d, int form, float &norm, float &err,
+                                int &gbits) {
     const int lane = threadIdx.x & 31;
     float mx = 0.0f;
     if (form == 2) {
@@ -216,8 +232,10 @@ __device__ void query_round_err(const float *x, int d, int form, float &norm, fl
     const float sc = mx > 0.0f ? mx / 448.0f : 1.0f;
     const float inv = 1.0f / sc;
     float s = 0.0f, e = 0.0f;
+    int g = 0;
     for (int k = lane; k < d; k += 32) {
         const float v = x[k];
+        g = max(g, frac_bits(v));
         float r = v;
         if (form == 1) {
             r = __bfloat162float(__float2bfloat16_rn(v));
@@ -238,6 +256,7 @@ __device__ void query_round_err(const float *x, int d, int form, float &norm, fl
     const float up = 1.0f + 2.0f * eta_of(d);
     norm = __fmul_ru(__fsqrt_ru(s), up);
     err = __fmul_ru(__fsqrt_ru(e), up);
+    gbits = __reduce_max_sync(0xffffffffu, (unsigned)g);
 }
 
 // NJ: float4 of a row per lane (dimensions 4 lane + 128 j, j < NJ): d <= 128 NJ
@@ -473,7 +492,7 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
            const int64_t *__restrict__ set_off, const int32_t *__restrict__ cand,
            const int32_t *__restrict__ thr, int C, int k, const longlong2 *__restrict__ pair,
            float *__restrict__ cand_dist, int64_t *__restrict__ out_ids,
-           float *__restrict__ out_dist, int *__restrict__ err, int q_floats) {
+           float *__restrict__ out_dist, int *__restrict__ err, int q_floats, int exact_band) {
     constexpr bool tiles = NJ == 0;
     constexpr int NJW = NJ > 0 ? NJ : 1;   // the warp form's width (unused when tiles)
     extern __shared__ __align__(16) unsigned char bsm[];
@@ -488,7 +507,8 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     int *sslot = reinterpret_cast<int *>(lov + C);
     __shared__ int hist[256];
     __shared__ int sh[kBW + 3];
-    __shared__ float qst[2];   // largest norm of a rounded query vector, largest rounding error
+    // largest norm of a rounded query vector, largest rounding error, largest frac_bits
+    __shared__ float qst[3];
     const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_sel = thr[q * 4 + 3];
     const int kp = k < n_sel ? k : n_sel;
@@ -508,29 +528,60 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
             reinterpret_cast<float4 *>(Qs)[e] = reinterpret_cast<const float4 *>(Q)[e];
         Q = Qs;
     }
-    if (tid < 2) qst[tid] = 0.0f;
+    if (tid < 3) qst[tid] = 0.0f;
     __syncthreads();
     // ---- 1. intervals, tau and the band ----------------------------------------------
     for (int a = warp; a < mq; a += kBW) {
         float nrm, er;
-        query_round_err(Q + (int64_t)a * d, d, form, nrm, er);
+        int gb;
+        query_round_err(Q + (int64_t)a * d, d, form, nrm, er, gb);
         if (lane == 0) {
             smem_max(&qst[0], __fadd_ru(nrm, er));
             smem_max(&qst[1], er);
+            smem_max(&qst[2], (float)gb);
         }
     }
     __syncthreads();
+    // Exactness certificate: with every value a multiple of 2^-g, every product, partial
+    // sum, norm and difference of the GEMM form and of the re-scored pair is a multiple of
+    // 2^-2g no larger than (N_Q + N_V)^2 in magnitude.  Below 2^(22 - 2g) FP32 holds each
+    // one exactly, in any order of accumulation, so the refine's value is the exact
+    // Hausdorff value up to its final square root, and two such square roots are equal
+    // only when the exact values are.  (The BF16 copy must be lossless, e = 0; the FP8
+    // copy's scaling is never exact.)
+    bool cert;
+    {
+        const float eV0 = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
+        const float ns0 = __fadd_ru(qst[0], __fadd_ru(stats[0], eV0));
+        const int g = (int)fmaxf(qst[2], stats[3]);
+        cert = form != 2 && qst[1] == 0.0f && eV0 == 0.0f && g <= 10 &&
+               __fmul_ru(ns0, ns0) < ldexpf(1.0f, 22 - 2 * g);
+    }
     {
         const float eta_d = eta_of(d);
         const float eV = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
         const float nsum = __fadd_ru(qst[0], __fadd_ru(stats[0], eV));
         // GEMM-form squared-distance error bound (d + 8) 2^-23 (N_Q + N_V)^2
         const float D = __fmul_ru((float)(d + 8) * 1.1920929e-7f, __fmul_ru(nsum, nsum));
-        const float e = __fadd_ru(qst[1], eV);
+        // the rounding's effect on a distance: at most e_q + e_v (rigorous); for the FP8
+        // form by default 3 standard deviations of the rounding model, in which the
+        // per-value errors are independent and zero-mean, so a pair distance moves by
+        // about sqrt(e_q^2 + e_v^2) / sqrt(d)
+        const float e = form == 2 && !exact_band
+                            ? __fmul_ru(3.0f, __fdiv_ru(__fsqrt_ru(__fadd_ru(
+                                  __fmul_ru(qst[1], qst[1]), __fmul_ru(eV, eV))), sqrtf((float)d) *
+                                  (1.0f - 1e-6f)))
+                            : __fadd_ru(qst[1], eV);
         const longlong2 *pq = pair + (int64_t)q * C;
         for (int j = tid; j < n_sel; j += kBT) {
             float lo, hi;
-            if (form == 0) {
+            if (cert) {   // exact up to the square root's rounding
+                const float v = form == 0 ? cd[j]
+                                          : sqrtf(__uint_as_float(
+                                                (uint32_t)((unsigned long long)pq[j].x >> 32)));
+                lo = __fmul_rd(v, 1.0f - 1.1920929e-7f);
+                hi = __fmul_ru(v, 1.0f + 1.1920929e-7f);
+            } else if (form == 0) {
                 const float r = cd[j];
                 const float rl = __fmul_rd(r, 1.0f - eta_d), rh = __fmul_ru(r, 1.0f + 2.0f * eta_d);
                 const float D2 = __fmul_ru(2.0f, D);
@@ -558,7 +609,17 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     }
     __syncthreads();
     // ---- 2. the direct FP32 Hausdorff value of every band member -----------------------
-    if (!tiles) {
+    if (cert) {   // the refine's value is already exact (up to the square root's rounding)
+        const longlong2 *pq = pair + (int64_t)q * C;
+        for (int t = tid; t < nb; t += kBT) {
+            const int j = mem[t];
+            const float h = form == 0 ? cd[j]
+                                      : sqrtf(__uint_as_float(
+                                            (uint32_t)((unsigned long long)pq[j].x >> 32)));
+            lov[t] = h;
+            cd[j] = h;
+        }
+    } else if (!tiles) {
         for (int t = warp; t < nb; t += kBW) {
             const int j = mem[t];
             const int64_t r0 = set_off[cq[j]];
@@ -586,7 +647,7 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     // the exact values are non-negative: their bits order as they do
     const float vk =
         __uint_as_float(block_kth(reinterpret_cast<const uint32_t *>(lov), nb, kp, hist, sh));
-    const float eta = eta_exact(d);
+    const float eta = cert ? 0.0f : eta_exact(d);   // certified values: equal iff equal
     const float reach = __fmul_ru(vk, 1.0f + eta);
     int ns = 0;
     for (int t0 = 0; t0 < nb; t0 += kBT) {
@@ -643,7 +704,9 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     }
     __syncthreads();
     // ---- FP64 for the marked members: the u-th marked one on warp u mod kBW --------------
-    if (!tiles) {
+    // (certified values are marked only when exactly equal: no FP64, the id decides)
+    if (cert) {
+    } else if (!tiles) {
         int u = 0;
         for (int t = 0; t < ns; ++t) {
             const int sl = sslot[t];
@@ -698,22 +761,22 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
 
 }  // namespace
 
-// query floats staged in shared memory when the batch's largest query set fits this
-constexpr int kQStageFloats = 16384;   // 64 KB
 constexpr size_t kSmemLimit = 232448;    // 227 KB opt-in per CTA
 
 cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int max_mq, int d,
                              int form, const float *stats, const float *vec,
                              const int64_t *set_off, const int32_t *cand, const int32_t *thr,
                              int C, int k, const longlong2 *pair, float *cand_dist,
-                             int64_t *out_ids, float *out_dist, int *err, cudaStream_t st) {
+                             int64_t *out_ids, float *out_dist, int *err, int exact_band,
+                             cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
     if (C > BVSS_MAX_C || k < 1 || k > BVSS_MAX_K || form < 0 || form > 2 || d % 4 != 0 ||
         max_mq < 1 || max_mq > BVSS_MAX_QSET)
         return cudaErrorInvalidValue;
-    int q_floats = max_mq * d <= kQStageFloats ? max_mq * d : 0;
+    // the query set in shared memory whenever it fits beside the rest (else read in place)
+    int q_floats = max_mq * d;
     const bool tiles = d > kWarpMaxD;
-    if (boundary_smem(C, k, q_floats, tiles) > kSmemLimit) q_floats = 0;   // read in place
+    if (boundary_smem(C, k, q_floats, tiles) > kSmemLimit) q_floats = 0;
     const size_t smem = boundary_smem(C, k, q_floats, tiles);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     auto kern = tiles ? k_boundary<0> : d <= 128 ? k_boundary<1> : d <= 256 ? k_boundary<2>
@@ -722,12 +785,13 @@ cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, in
                                          (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<n_q, kBT, smem, st>>>(qvec, qoff, d, form, stats, vec, set_off, cand, thr, C, k, pair,
-                                 cand_dist, out_ids, out_dist, err, q_floats);
+                                 cand_dist, out_ids, out_dist, err, q_floats, exact_band);
     return cudaGetLastError();
 }
 
 // The largest vector norm of the database and the largest rounding-error norm of its
-// BF16 and FP8 copies (stats[0..2]), each rounded up, read from the stored copies.
+// BF16 and FP8 copies (stats[0..2]), each rounded up, read from the stored copies, and
+// the largest frac_bits of its values (stats[3]).
 __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
                               const __nv_bfloat16 *__restrict__ x16,
                               const uint8_t *__restrict__ x8, const float *__restrict__ sc8,
@@ -736,12 +800,14 @@ __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const float up = 1.0f + 2.0f * eta_of(d);
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+    int g = 0;
     for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
          v += warps) {
         float s = 0.0f, e16 = 0.0f, e8 = 0.0f;
         const float sc = x8 ? sc8[v] : 1.0f;
         for (int k = lane; k < d; k += 32) {
             const float a = x[v * d + k];
+            g = max(g, frac_bits(a));
             s = fmaf(a, a, s);
             if (x16) {
                 const float b = __bfloat162float(x16[v * d + k]);
@@ -763,7 +829,9 @@ __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
         m1 = fmaxf(m1, __fmul_ru(__fsqrt_ru(e16), up));
         m2 = fmaxf(m2, __fmul_ru(__fsqrt_ru(e8), up));
     }
+    g = (int)__reduce_max_sync(0xffffffffu, (unsigned)g);
     if (lane == 0) {
+        atomicMax(reinterpret_cast<unsigned *>(&stats[3]), __float_as_uint((float)g));
         atomicMax(reinterpret_cast<unsigned *>(&stats[0]), __float_as_uint(m0));
         atomicMax(reinterpret_cast<unsigned *>(&stats[1]), __float_as_uint(m1));
         atomicMax(reinterpret_cast<unsigned *>(&stats[2]), __float_as_uint(m2));

@@ -212,13 +212,15 @@ cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------
 // form: the refine that ran (0 FP32, 1 BF16 tensor cores, 2 FP8 tensor cores); stats: the
 // index's rstat; pair: the MMA forms' records (value in the high word of .x); max_mq: the
-// batch's largest query set.  Band members' cand_dist become their exact values;
+// batch's largest query set; exact_band: the FP8 form's band from its rigorous bound
+// (else from its 3-sigma tolerance).  Band members' cand_dist become their exact values;
 // cand_dist[q][n_sel..C) is padded with +inf; results as launch_topk.
 cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int max_mq, int d,
                              int form, const float *stats, const float *vec,
                              const int64_t *set_off, const int32_t *cand, const int32_t *thr,
                              int C, int k, const longlong2 *pair, float *cand_dist,
-                             int64_t *out_ids, float *out_dist, int *err, cudaStream_t st);
+                             int64_t *out_ids, float *out_dist, int *err, int exact_band,
+                             cudaStream_t st);
 constexpr int kBandKernels = 1;
 // rstat of an index (x16 / x8 may be null: their entries stay 0)
 cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,

@@ -4,7 +4,8 @@ Off the 2^-8 grid the BF16 and FP8 copies round the vectors and FP32 GEMM-form
 sums round too, so each form's candidate values are approximate.  The
 boundary stage re-scores, directly in FP32 over all pairs, every candidate
 whose error interval reaches the k-th smallest upper bound, and in FP64 the
-candidates that FP32 cannot order at the top k.  So every form must return
+candidates that FP32 cannot order at the top k.  So every form (the FP8 form
+with its rigorous band, BVSS_SEARCH_FP8_EXACT) must return
 the oracle's ids (FP64 Hausdorff, ties by id) exactly, with distances within
 the stated (36 + ceil(d / 32)) 2^-24 relative bound of the oracle's FP64 values.
 """
@@ -16,7 +17,7 @@ from paper_2412_03301_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
 
-FORMS = (dict(), dict(fast=True), dict(fp8=True))
+FORMS = (dict(), dict(fast=True), dict(fp8=True, fp8_exact=True))
 
 
 @pytest.fixture(scope="module")
@@ -90,3 +91,17 @@ def test_fp64_orders_what_fp32_cannot(bv, orc):
     r = orc.query(orc.Index(vec, w["offsets"], w["proj"], 8), qv, k=3, C=n, A=3, M=0)
     assert r["ids"].tolist() == [1, 2, 0]
     _check(bv, orc, w, 8, 3, n, 3, 0)
+
+
+@pytest.mark.parametrize("bits,scale", [(8, 1.0), (10, 0.9), (8, 8.0), (6, 12.0)])
+def test_grid_certificate_and_its_limits(bv, orc, bits, scale):
+    """Values on a 2^-bits grid: where (N_Q + N_V)^2 < 2^(22 - 2 bits) the stage certifies
+    the refine's arithmetic exact and only selects; beyond it (norms of 8 on the 2^-8 grid,
+    12 on 2^-6) it re-scores the band.  Every case must give the oracle's top k."""
+    w = datagen.workload(n_sets=1200, size_lo=2, size_hi=14, d=128, n_components=32,
+                         n_queries=10, q_lo=2, q_hi=14, m=1024, fanin=8, seed=90 + bits,
+                         grid=False)
+    g = 2.0 ** bits
+    for key in ("vectors", "q_vectors"):
+        w[key] = (torch.round(w[key].double() * scale * g) / g).float()
+    _check(bv, orc, w, 16, 10, 200, 3, 1)

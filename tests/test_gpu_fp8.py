@@ -8,13 +8,16 @@ pairwise distance then moves by at most e(q) + e(v) (triangle inequality),
 and the Hausdorff value of Def. 4 by at most the largest of those over the
 pairs (max and min are 1-Lipschitz).  The kernel keeps the pair that attains
 the rounded Hausdorff value and reports that pair's FP32 distance, so a
-reported distance is within 2 eps of the candidate's true Hausdorff distance,
-eps = max e(q) + max e(v) plus the FP32 rounding of the GEMM form; and a
-returned set's true distance is within 4 eps of the true k-th smallest among
-the same candidates (the candidates themselves are exact: scan and select do
-not depend on the refine).  The tests check exactly those two statements
-against the FP64 oracle, and that batches the FP8 copy does not take fall
-back to the exact forms.
+candidate's value is within 2 eps of its true Hausdorff distance, eps = max
+e(q) + max e(v) plus the FP32 rounding of the GEMM form.  The boundary stage
+then re-scores exactly the candidates within its band of the k-th value (by
+default a 3-sigma tolerance, with BVSS_SEARCH_FP8_EXACT the rigorous bound),
+so a returned distance is the exact value of its set and a returned set's true
+distance is within 4 eps of the true k-th smallest among the same candidates
+(the candidates themselves are exact: scan and select do not depend on the
+refine).  The tests check those statements against the FP64 oracle, that the
+exact band returns the oracle's ids, and that batches the FP8 copy does not
+take fall back to the exact forms.
 """
 import numpy as np
 import pytest
@@ -73,9 +76,22 @@ def test_fp8_distances_and_ranks_within_the_bound(bv, orc, case):
             rows = slice(int(off[sid]), int(off[sid + 1]))
             eps = eq + ev[rows].max() + GEMM_SLACK
             assert abs(dist[q][j] - true_d[j]) <= 2 * eps + 1e-5 * true_d[j], (q, j)
+            # the boundary stage returns the set's exact value
+            assert abs(dist[q][j] - true_d[j]) <= (40 + 4) * 2.0 ** -24 * true_d[j], (q, j)
             # near-optimal: within 4 eps of the true k-th smallest over the same candidates
             assert true_d[j] <= r["dist"][n - 1] + 4 * eps + 1e-5, (q, j)
         assert np.all(np.diff(dist[q][:n]) >= 0)
+
+
+def test_fp8_exact_band_returns_the_oracle_top_k(bv, orc, case):
+    w, ix, oix, _ = case
+    qv, qo = w["q_vectors"], w["q_offsets"]
+    ids, dist = bv.bvss_query(ix, qv.cuda(), qo, k=10, C=300, fp8=True, fp8_exact=True)
+    for q in range(qo.shape[0] - 1):
+        r = orc.query(oix, qv[qo[q]:qo[q + 1]].numpy(), k=10, C=300, A=3, M=1)
+        assert ids[q].tolist() == r["ids"].tolist(), q
+        fin = np.isfinite(r["dist"])
+        np.testing.assert_allclose(dist[q].cpu().numpy()[fin], r["dist"][fin], rtol=3e-6)
 
 
 def test_fp8_falls_back_for_wide_query_sets(bv, orc, case):
