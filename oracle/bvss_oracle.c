@@ -26,6 +26,11 @@
  *                       between per-vector codes in place of the norm
  *   orc_alg2_scores     Alg. 2 lines 6-8 (Haus^H against every set)
  *   orc_alg2_select     Alg. 2 line 9 (the c smallest d_H)
+ *   orc_dense_encode    Def. 7 with a learned dense W (BioHash in place of
+ *                       FlyHash): BF16 layer, then WTA
+ *   orc_soft_pair,      the training of that W on neighbour pairs: soft-code
+ *   orc_learn_step      loss and gradient, and one normalized step (the
+ *                       update magnitude of the BioHash iteration analysis)
  *
  * Readings where the paper is silent (the same readings the GPU path uses):
  *   - activations a_j are FP32 sums taken in the order of W's row, starting
@@ -528,5 +533,201 @@ int orc_alg2_select(const int32_t *score, int64_t n_sets, int32_t c, int32_t *ou
     qsort(out_ids, (size_t)n, sizeof(int32_t), orc_i32_cmp);
     *n_out = n;
     free(pr);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Learned projection (the paper's BioHash in place of FlyHash, Def. 7: */
+/* h = WTA(W v) with W learned).  Readings, as in the GPU path:        */
+/*   - the layer is BF16: a = bf16(W) bf16(x), each BF16 value the     */
+/*     round-to-nearest-even of the FP32 one; here summed exactly      */
+/*     in FP64 (exact for weights and inputs on the 2^-8 grid);        */
+/*   - WTA keeps the L largest activations, ties to the lower index;   */
+/*   - training: a logistic loss on the overlap of soft codes, the     */
+/*     WTA threshold held fixed in the gradient, then a normalized     */
+/*     gradient step (its largest entry is the step size, the update   */
+/*     magnitude M_t of the paper's BioHash iteration analysis), rows  */
+/*     rescaled to a fixed norm and the forward weights rounded to     */
+/*     the 2^-8 grid.                                                  */
+/* ------------------------------------------------------------------ */
+
+/* round-to-nearest-even of an FP32 value to BF16 (8 significant bits), */
+/* from the IEEE 754 binary32 layout; finite inputs                      */
+float orc_bf16(float x) {
+    uint32_t u;
+    memcpy(&u, &x, sizeof u);
+    const uint32_t lsb = (u >> 16) & 1u;
+    const uint32_t rounded = u + 0x7FFFu + lsb;   /* carries into the exponent when due */
+    uint32_t r = rounded & 0xFFFF0000u;
+    float y;
+    memcpy(&y, &r, sizeof y);
+    return y;
+}
+
+typedef struct {
+    double a;
+    int32_t j;
+} orc_dact;
+
+static int orc_dact_cmp(const void *pa, const void *pb) {
+    const orc_dact *x = (const orc_dact *)pa;
+    const orc_dact *y = (const orc_dact *)pb;
+    if (x->a > y->a) return -1;
+    if (x->a < y->a) return 1;
+    if (x->j < y->j) return -1;
+    if (x->j > y->j) return 1;
+    return 0;
+}
+
+/* a[j] = sum_k bf16(w[j][k]) bf16(x[k]) for n vectors (act: n x m, may be NULL), */
+/* then WTA: pos (n x L, ascending) and mask (n x m/32) as orc_encode           */
+int orc_dense_encode(const float *x, int64_t n, int32_t d, const float *w, int32_t m,
+                     int32_t L, uint16_t *pos, uint32_t *mask, double *act) {
+    if (n < 0 || d < 1 || m < 1 || L < 1 || L > m) return ORC_EINVAL;
+    orc_dact *buf = (orc_dact *)malloc(sizeof(orc_dact) * (size_t)m);
+    uint16_t *sel = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)L);
+    if (!buf || !sel) {
+        free(buf);
+        free(sel);
+        return ORC_ENOMEM;
+    }
+    const int32_t words = (m + 31) / 32;
+    for (int64_t v = 0; v < n; ++v) {
+        const float *xv = x + v * d;
+        for (int32_t j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int32_t k = 0; k < d; ++k)
+                s += (double)orc_bf16(w[(int64_t)j * d + k]) * (double)orc_bf16(xv[k]);
+            buf[j].a = s;
+            buf[j].j = j;
+            if (act) act[v * m + j] = s;
+        }
+        qsort(buf, (size_t)m, sizeof(orc_dact), orc_dact_cmp);
+        for (int32_t t = 0; t < L; ++t) sel[t] = (uint16_t)buf[t].j;
+        qsort(sel, (size_t)L, sizeof(uint16_t), orc_u16_cmp);
+        if (pos)
+            for (int32_t t = 0; t < L; ++t) pos[v * L + t] = sel[t];
+        if (mask) {
+            uint32_t *mv = mask + v * words;
+            for (int32_t w2 = 0; w2 < words; ++w2) mv[w2] = 0u;
+            for (int32_t t = 0; t < L; ++t) mv[sel[t] >> 5] |= 1u << (sel[t] & 31);
+        }
+    }
+    free(buf);
+    free(sel);
+    return ORC_OK;
+}
+
+/* the WTA threshold of one activation vector: midway between its L-th and */
+/* (L+1)-th largest values (L < m)                                         */
+double orc_wta_threshold(const double *a, int32_t m, int32_t L) {
+    double *s = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!s) return 0.0;
+    for (int32_t j = 0; j < m; ++j) s[j] = a[j];
+    /* partial selection sort of the L + 1 largest (m is small in the tests) */
+    for (int32_t t = 0; t <= L && t < m; ++t) {
+        int32_t b = t;
+        for (int32_t j = t + 1; j < m; ++j)
+            if (s[j] > s[b]) b = j;
+        const double tmp = s[t];
+        s[t] = s[b];
+        s[b] = tmp;
+    }
+    const double th = 0.5 * (s[L - 1] + s[L]);
+    free(s);
+    return th;
+}
+
+static double orc_sigmoid(double z) {
+    return z >= 0.0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+}
+
+/* Loss of one pair and its gradient in the activations, the thresholds th_x, th_y held */
+/* fixed: soft codes c_j = sigmoid((a_j - th) / T), overlap o = (1/L) sum_j c_j(x) c_j(y), */
+/* logit z = s (o - mu), loss = log(1 + exp(-z)) for a positive pair (y = 1) and        */
+/* log(1 + exp(z)) for a negative one.  gx, gy (m each) receive d loss / d a.            */
+double orc_soft_pair(const double *ax, const double *ay, int32_t m, int32_t L, double T,
+                     double s, double mu, int32_t y, double th_x, double th_y, double *gx,
+                     double *gy) {
+    double o = 0.0;
+    for (int32_t j = 0; j < m; ++j)
+        o += orc_sigmoid((ax[j] - th_x) / T) * orc_sigmoid((ay[j] - th_y) / T);
+    o /= (double)L;
+    const double sg = y ? 1.0 : -1.0;
+    const double z = sg * s * (o - mu);
+    /* log(1 + exp(-z)), evaluated without overflow */
+    const double loss = z >= 0.0 ? log1p(exp(-z)) : -z + log1p(exp(z));
+    const double dl_do = -sg * s * orc_sigmoid(-z);
+    for (int32_t j = 0; j < m; ++j) {
+        const double cx = orc_sigmoid((ax[j] - th_x) / T);
+        const double cy = orc_sigmoid((ay[j] - th_y) / T);
+        if (gx) gx[j] = dl_do * (cy / L) * cx * (1.0 - cx) / T;
+        if (gy) gy[j] = dl_do * (cx / L) * cy * (1.0 - cy) / T;
+    }
+    return loss;
+}
+
+/* a weight's forward value: the nearest multiple of 2^-8 (ties to even), clamped to */
+/* [-1, 1], so that BF16 holds it exactly                                            */
+double orc_quant_weight(double w) {
+    double q = nearbyint(w * 256.0) / 256.0;
+    if (q > 1.0) q = 1.0;
+    if (q < -1.0) q = -1.0;
+    return q;
+}
+
+/* One training step over a batch of n pairs (x_i, y_i, label_i):                     */
+/*   forward with the quantized weights wq = quant(w): a = wq bf16(x);              */
+/*   d w = (1/n) sum_i g_x,i bf16(x_i)^T + g_y,i bf16(y_i)^T (orc_soft_pair);        */
+/*   w' = w - eta dw / max|dw|, then every row rescaled to norm row_norm;            */
+/*   wq' = quant(w').  w, w_out: m x d FP64; wq_out: m x d; loss_out: the mean loss. */
+int orc_learn_step(const double *w, const float *xs, const float *ys, const uint8_t *labels,
+                   int64_t n, int32_t m, int32_t d, int32_t L, double T, double s, double mu,
+                   double eta, double row_norm, double *w_out, float *wq_out, double *dw_out,
+                   double *loss_out) {
+    if (n < 1 || m < 2 || d < 1 || L < 1 || L >= m) return ORC_EINVAL;
+    const size_t md = (size_t)m * d;
+    float *wq = (float *)malloc(sizeof(float) * md);
+    double *dw = (double *)calloc(md, sizeof(double));
+    double *ax = (double *)malloc(sizeof(double) * (size_t)m);
+    double *ay = (double *)malloc(sizeof(double) * (size_t)m);
+    double *gx = (double *)malloc(sizeof(double) * (size_t)m);
+    double *gy = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!wq || !dw || !ax || !ay || !gx || !gy) {
+        free(wq); free(dw); free(ax); free(ay); free(gx); free(gy);
+        return ORC_ENOMEM;
+    }
+    for (size_t e = 0; e < md; ++e) wq[e] = (float)orc_quant_weight(w[e]);
+    double loss = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float *x = xs + i * d, *yv = ys + i * d;
+        orc_dense_encode(x, 1, d, wq, m, L, NULL, NULL, ax);
+        orc_dense_encode(yv, 1, d, wq, m, L, NULL, NULL, ay);
+        const double tx = orc_wta_threshold(ax, m, L), ty = orc_wta_threshold(ay, m, L);
+        loss += orc_soft_pair(ax, ay, m, L, T, s, mu, labels[i], tx, ty, gx, gy);
+        for (int32_t j = 0; j < m; ++j)
+            for (int32_t k = 0; k < d; ++k)
+                dw[(size_t)j * d + k] +=
+                    (gx[j] * (double)orc_bf16(x[k]) + gy[j] * (double)orc_bf16(yv[k])) / (double)n;
+    }
+    double mx = 0.0;
+    for (size_t e = 0; e < md; ++e) mx = fabs(dw[e]) > mx ? fabs(dw[e]) : mx;
+    for (int32_t j = 0; j < m; ++j) {
+        double nn = 0.0;
+        for (int32_t k = 0; k < d; ++k) {
+            const size_t e = (size_t)j * d + k;
+            w_out[e] = w[e] - (mx > 0.0 ? eta * dw[e] / mx : 0.0);
+            nn += w_out[e] * w_out[e];
+        }
+        nn = sqrt(nn);
+        for (int32_t k = 0; k < d; ++k) {
+            const size_t e = (size_t)j * d + k;
+            if (nn > 0.0) w_out[e] *= row_norm / nn;
+            wq_out[e] = (float)orc_quant_weight(w_out[e]);
+        }
+    }
+    if (dw_out) memcpy(dw_out, dw, sizeof(double) * md);
+    *loss_out = loss / (double)n;
+    free(wq); free(dw); free(ax); free(ay); free(gx); free(gy);
     return ORC_OK;
 }

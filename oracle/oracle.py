@@ -20,6 +20,8 @@ Each wrapper names the passage of the paper it follows:
 * ``refine_topk``     Alg. 6 lines 19-23
 * ``bruteforce_topk`` exact top-k of Def. 5 (ground truth)
 * ``query``           the whole of Alg. 6 for one query set
+* ``dense_encode``    Def. 7 with a learned BF16 dense layer (BioHash)
+* ``soft_pair``, ``learn_step``  training that layer on neighbour pairs
 
 Every function is pinned by ``tests/test_oracle_*.py`` against worked
 examples printed in the paper, closed forms, invariants and brute force.
@@ -79,6 +81,13 @@ def _load():
         "orc_haus_h": (i32, [P, i64, P, i64, i32]),
         "orc_alg2_scores": (ctypes.c_int, [P, i64, P, P, i64, i32, P]),
         "orc_alg2_select": (ctypes.c_int, [P, i64, i32, P, P]),
+        "orc_bf16": (ctypes.c_float, [ctypes.c_float]),
+        "orc_dense_encode": (ctypes.c_int, [P, i64, i32, P, i32, i32, P, P, P]),
+        "orc_wta_threshold": (dbl, [P, i32, i32]),
+        "orc_soft_pair": (dbl, [P, P, i32, i32, dbl, dbl, dbl, i32, dbl, dbl, P, P]),
+        "orc_quant_weight": (dbl, [dbl]),
+        "orc_learn_step": (ctypes.c_int, [P, P, P, P, i64, i32, i32, i32, dbl, dbl, dbl, dbl,
+                                          dbl, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -338,6 +347,68 @@ def query_alg2(index: Index, Q, k, C):
     ids, dist, cand_dist = refine_topk(Q, index.vectors, index.set_off, cand, k)
     return dict(qpos=qpos, qmask=qmask, score=score, cand=cand, cand_dist=cand_dist, ids=ids,
                 dist=dist)
+
+
+# ---- learned projection (BioHash in place of FlyHash, Def. 7) ----------------------
+def bf16(x):
+    """Round-to-nearest-even BF16 value of each FP32 value."""
+    f = _load().orc_bf16
+    return np.array([f(float(v)) for v in np.asarray(x, np.float32).ravel()],
+                    np.float32).reshape(np.shape(x))
+
+
+def dense_encode(x, w, L, return_act=False):
+    """Codes of a BF16 dense layer: a = bf16(w) bf16(x) exactly, then WTA top-L."""
+    lib = _load()
+    x = _c(x, np.float32)
+    w = _c(w, np.float32)
+    n, d = x.shape
+    m = w.shape[0]
+    pos = np.zeros((n, L), np.uint16)
+    mask = np.zeros((n, (m + 31) // 32), np.uint32)
+    act = np.zeros((n, m), np.float64) if return_act else None
+    _check(lib.orc_dense_encode(_p(x), n, d, _p(w), m, L, _p(pos), _p(mask), _p(act)),
+           "dense_encode")
+    return (pos, mask, act) if return_act else (pos, mask)
+
+
+def wta_threshold(a, L):
+    a = _c(a, np.float64)
+    return float(_load().orc_wta_threshold(_p(a), a.shape[0], L))
+
+
+def soft_pair(ax, ay, L, T, s, mu, y, th_x, th_y):
+    """(loss, d loss / d ax, d loss / d ay) of one pair, thresholds fixed."""
+    ax = _c(ax, np.float64)
+    ay = _c(ay, np.float64)
+    gx = np.zeros_like(ax)
+    gy = np.zeros_like(ay)
+    loss = _load().orc_soft_pair(_p(ax), _p(ay), ax.shape[0], L, T, s, mu, int(y), th_x, th_y,
+                                 _p(gx), _p(gy))
+    return loss, gx, gy
+
+
+def quant_weight(w):
+    f = _load().orc_quant_weight
+    return np.vectorize(lambda v: f(float(v)))(np.asarray(w, np.float64))
+
+
+def learn_step(w, xs, ys, labels, L, T, s, mu, eta, row_norm):
+    """One training step; returns (w', wq', dw, mean loss)."""
+    lib = _load()
+    w = _c(w, np.float64)
+    xs = _c(xs, np.float32)
+    ys = _c(ys, np.float32)
+    labels = _c(labels, np.uint8)
+    m, d = w.shape
+    w_out = np.zeros_like(w)
+    wq = np.zeros((m, d), np.float32)
+    dw = np.zeros_like(w)
+    loss = ctypes.c_double()
+    _check(lib.orc_learn_step(_p(w), _p(xs), _p(ys), _p(labels), xs.shape[0], m, d, L, T, s,
+                              mu, eta, row_norm, _p(w_out), _p(wq), _p(dw),
+                              ctypes.byref(loss)), "learn_step")
+    return w_out, wq, dw, loss.value
 
 
 if __name__ == "__main__":
