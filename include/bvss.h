@@ -364,6 +364,89 @@ int bvss_select_noalloc(const uint16_t *h, int64_t n_sets, int64_t h_stride, int
                         int32_t n_queries, int32_t C, int32_t *cand, int32_t *n_cand,
                         void *stream);
 
+/*
+ * The learned projection.  The paper's own runs use BioHash, a learned W in
+ * h = WTA(W v) (Def. 7; the BioHash discussion beside it and the appendix on
+ * its iteration), in place of FlyHash's random sparse binary W.  Here W is a
+ * dense BF16 layer (m x d), run on the tensor cores, and is trained on
+ * neighbour pairs that the exact refine itself produces; FlyHash stays the
+ * fallback (bvss_build).  Readings: the layer computes a = bf16(W) bf16(x)
+ * with FP32 accumulation (bf16: round to nearest even), which is exact for
+ * weights and inputs on the 2^-8 grid with norms far below 2^8, so the codes
+ * then equal those of an exact layer; WTA ties go to the lower index.
+ */
+
+/* bvss_build with the learned dense projection in place of FlyHash.
+ *   w       host or device, m x d FP32 row-major (m = params->m, d = params->d),
+ *           rounded to BF16 for the layer; the caller keeps ownership
+ *   params  as bvss_build; fanin is not used (bvss_index_info reports 0); needs
+ *           d % 64 == 0 and m % 128 == 0
+ * Everything else (vectors, offsets, flags, errors) as bvss_build.  Queries on
+ * the index (bvss_query, plans, bvss_encode) encode with the same layer. */
+int bvss_build_dense(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+                     const float *w, const bvss_params *params, void *stream, bvss_index **out);
+
+/* Activations of the dense layer, a = W x, for n vectors on the tensor cores.
+ *   x_bf16  device, n x d BF16 row-major (16-byte aligned)
+ *   w_bf16  device, m x d BF16 row-major (16-byte aligned)
+ *   act     device, n rows of ld_act FP32 (16-byte aligned): act[i][j] = w_j . x_i
+ * d % 64 == 0, m % 128 == 0, ld_act >= m, ld_act % 4 == 0.  Asynchronous; a
+ * bounded wait inside that gives up is reported by bvss_learn_sync.  Errors:
+ * EINVAL, ECUDA. */
+int bvss_dense_forward(const void *x_bf16, int64_t n, int32_t d, const void *w_bf16, int32_t m,
+                       float *act, int64_t ld_act, void *stream);
+
+/* Waits for `stream`, then reports BVSS_ETIMEOUT (and clears it) if a dense-layer
+ * kernel's bounded wait gave up since the last call, BVSS_ECUDA on a CUDA error. */
+int bvss_learn_sync(void *stream);
+
+/* Training loss of n neighbour pairs and its gradient in the activations.  For pair i
+ * with activations a = act_x[i], b = act_y[i] (m values each, rows ld_act apart) and
+ * label y = labels[i] (1: neighbours, 0: not): thresholds t_a, t_b midway between the
+ * L-th and (L+1)-th largest values; soft codes c_j = sigmoid((a_j - t) / temperature);
+ * overlap o = (1/L) sum_j c_j(a) c_j(b); loss = log(1 + exp(-z)) with z = +-scale (o -
+ * margin), + for y = 1.  g_x[i], g_y[i] (device, rows ld_g apart) receive d loss / d a
+ * and d loss / d b with the thresholds held fixed; *loss_sum (device) is incremented by
+ * the sum of the n losses.  All pointers device memory.  Errors: EINVAL, ECUDA. */
+int bvss_learn_pair_grad(const float *act_x, const float *act_y, int64_t ld_act,
+                         const uint8_t *labels, int64_t n, int32_t m, int32_t L,
+                         float temperature, float scale, float margin, float *g_x, float *g_y,
+                         int64_t ld_g, double *loss_sum, void *stream);
+
+/* The layer's weight gradient: dw (device, m x d FP32) = (1/n) sum_i g_x[i] x_i^T +
+ * g_y[i] y_i^T, with g_x, g_y as bvss_learn_pair_grad writes them and x_bf16, y_bf16
+ * (device, n x d BF16) the pairs' vectors.  m and d multiples of 64. */
+int bvss_learn_weight_grad(const float *g_x, const float *g_y, int64_t ld_g, const void *x_bf16,
+                           const void *y_bf16, int64_t n, int32_t m, int32_t d, float *dw,
+                           void *stream);
+
+/* One normalized gradient step: w (device, m x d FP32, updated in place) <- w - eta dw /
+ * max|dw| (so eta is the largest entry of the update, the update magnitude M_t of the
+ * paper's BioHash iteration analysis), then every row rescaled to norm row_norm;
+ * wq_bf16 (device, m x d BF16) receives the forward weights: w rounded to the nearest
+ * multiple of 2^-8 (ties to even), clamped to [-1, 1].  *absmax (device) receives
+ * max|dw|.  Errors: EINVAL, ECUDA. */
+int bvss_learn_update(float *w, const float *dw, int32_t m, int32_t d, float eta, float row_norm,
+                      float *absmax, void *wq_bf16, void *stream);
+
+/* BF16 copy (round to nearest even) of n x d FP32 values; both device memory. */
+int bvss_to_bf16(const float *x, int64_t n, int32_t d, void *out, void *stream);
+
+/* BF16 copies of the index's database vectors rows[0..n) (device int64, global rows
+ * in set order) into out (device, n x d BF16); an id outside [0, n_vectors) gives a
+ * row of zeros. */
+int bvss_index_rows_bf16(const bvss_index *ix, const int64_t *rows, int64_t n, void *out,
+                         void *stream);
+
+/* For mining training pairs from the refine's neighbours: rows (device, Vq x k int64)
+ * [a][t] = the global row of the database vector nearest to query vector a (direct
+ * FP32 distance, ties to the lower row) in set sets[q][t], q the query set holding a;
+ * -1 for a set id outside [0, n_sets).  q_vectors device (Vq x d FP32), q_offsets host
+ * (as bvss_query), sets device (n_queries x k int64).  Synchronises `stream`. */
+int bvss_nearest_rows(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+                      int64_t n_queries, const int64_t *sets, int32_t k, int64_t *rows,
+                      void *stream);
+
 /* Release an index and all its device memory (NULL is a no-op).  Work that
  * uses the index must have finished. */
 void bvss_free(bvss_index *ix);

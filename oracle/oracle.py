@@ -271,13 +271,17 @@ def bruteforce_topk(Q, vectors, set_off, k):
 class Index:
     """The oracle's index: codes, sketches, counts and inverted lists."""
 
-    def __init__(self, vectors, set_off, proj, L, threads=1):
+    def __init__(self, vectors, set_off, proj, L, threads=1, dense_w=None):
         self.vectors = _c(vectors, np.float32)
         self.set_off = _c(set_off, np.int64)
-        self.proj = _c(proj, np.uint16)
-        self.m = self.proj.shape[0]
+        self.dense_w = None if dense_w is None else _c(dense_w, np.float32)
+        self.proj = None if proj is None else _c(proj, np.uint16)
+        self.m = (self.proj if self.dense_w is None else self.dense_w).shape[0]
         self.L = L
-        if threads > 1:
+        if self.dense_w is not None:
+            # the learned dense projection in place of FlyHash
+            self.pos, self.mask = dense_encode(self.vectors, self.dense_w, L)
+        elif threads > 1:
             # the vectors are encoded independently (Alg. 1 line 4): chunks on host
             # threads (the C calls release the GIL), the same codes as one call
             from concurrent.futures import ThreadPoolExecutor
@@ -300,9 +304,15 @@ class Index:
         return self.set_off.shape[0] - 1
 
 
+def _codes(index: Index, Q):
+    if index.dense_w is not None:
+        return dense_encode(Q, index.dense_w, index.L)
+    return encode(Q, index.proj, index.L)
+
+
 def query(index: Index, Q, k, C, A, M):
     """Alg. 6 for one query set; returns every intermediate as a dict."""
-    qpos, qmask = encode(Q, index.proj, index.L)
+    qpos, qmask = _codes(index, Q)
     cq, sq, plist = query_filters(qpos, index.m, A)
     gate = index.inv.gate(plist, M)
     h = hamming(sq, index.sketch, gate, m=index.m)
@@ -341,7 +351,7 @@ def alg2_select(score, c):
 
 def query_alg2(index: Index, Q, k, C):
     """Alg. 2 (plain BioVSS) for one query set; returns every intermediate."""
-    qpos, qmask = encode(Q, index.proj, index.L)
+    qpos, qmask = _codes(index, Q)
     score = alg2_scores(qmask, index.mask, index.set_off, index.m)
     cand = alg2_select(score, C)
     ids, dist, cand_dist = refine_topk(Q, index.vectors, index.set_off, cand, k)

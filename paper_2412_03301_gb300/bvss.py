@@ -83,6 +83,20 @@ SYMBOLS = {
     "bvss_plan_free": (None, [_vp]),
     "bvss_free": (None, [_vp]),
     "bvss_last_error": (ctypes.c_char_p, []),
+    "bvss_build_dense": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, ctypes.POINTER(bvss_params),
+                                        _vp, ctypes.POINTER(_vp)]),
+    "bvss_dense_forward": (ctypes.c_int, [_vp, _c_i64, _c_i32, _vp, _c_i32, _vp, _c_i64, _vp]),
+    "bvss_learn_sync": (ctypes.c_int, [_vp]),
+    "bvss_learn_pair_grad": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _c_i64, _c_i32, _c_i32,
+                                            ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                            _vp, _vp, _c_i64, _vp, _vp]),
+    "bvss_learn_weight_grad": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp, _c_i64, _c_i32,
+                                              _c_i32, _vp, _vp]),
+    "bvss_learn_update": (ctypes.c_int, [_vp, _vp, _c_i32, _c_i32, ctypes.c_float,
+                                         ctypes.c_float, _vp, _vp, _vp]),
+    "bvss_to_bf16": (ctypes.c_int, [_vp, _c_i64, _c_i32, _vp, _vp]),
+    "bvss_index_rows_bf16": (ctypes.c_int, [_vp, _vp, _c_i64, _vp, _vp]),
+    "bvss_nearest_rows": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _vp, _c_i32, _vp, _vp]),
 }
 
 _lib = None
@@ -418,6 +432,100 @@ def bvss_profile_read(ix: Index, reset: bool = True):
     _check(load().bvss_profile_read(ix.handle, ms, ctypes.byref(nb), ctypes.byref(nl),
                                     1 if reset else 0))
     return dict(zip(STAGES, list(ms))), nb.value, nl.value
+
+
+# ---- the learned projection (BioHash in place of FlyHash, Def. 7) --------------------
+def bvss_build_dense(vectors: torch.Tensor, set_offsets, w: torch.Tensor, *, wta_l: int,
+                     bf16: bool = False, fp8: bool = False, stream=None) -> Index:
+    """Build an index whose codes come from the dense layer w (m, d) float32 (any device)."""
+    lib = load()
+    assert vectors.dtype == torch.float32 and vectors.is_contiguous()
+    assert w.dtype == torch.float32 and w.is_contiguous()
+    off, off_p = _host_i64(set_offsets)
+    p = bvss_params(d=vectors.shape[1], m=w.shape[0], fanin=0, wta_l=wta_l,
+                    flags=(BVSS_BUILD_BF16 if bf16 else 0) | (BVSS_BUILD_FP8 if fp8 else 0))
+    h = ctypes.c_void_p()
+    dev = vectors.device if vectors.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _check(lib.bvss_build_dense(_dptr(vectors), off_p, off.shape[0] - 1, _dptr(w),
+                                    ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+    return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
+
+
+def bvss_to_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    _check(load().bvss_to_bf16(_dptr(x), x.shape[0], x.shape[1], _dptr(out), _stream(stream)))
+    return out
+
+
+def bvss_dense_forward(x_bf16: torch.Tensor, w_bf16: torch.Tensor, out=None, stream=None):
+    """Activations (n, m) float32 of the BF16 layer on the tensor cores."""
+    n, d = x_bf16.shape
+    m = w_bf16.shape[0]
+    if out is None:
+        out = torch.empty((n, m), dtype=torch.float32, device=x_bf16.device)
+    _check(load().bvss_dense_forward(_dptr(x_bf16), n, d, _dptr(w_bf16), m, _dptr(out),
+                                     out.stride(0), _stream(stream)))
+    return out
+
+
+def bvss_learn_sync(stream=None):
+    _check(load().bvss_learn_sync(_stream(stream)))
+
+
+def bvss_learn_pair_grad(act_x, act_y, labels, L, temperature, scale, margin, g_x=None,
+                         g_y=None, loss_sum=None, stream=None):
+    """(g_x, g_y, loss_sum): the pairs' loss gradients in their activations."""
+    n, m = act_x.shape
+    g_x = torch.empty_like(act_x) if g_x is None else g_x
+    g_y = torch.empty_like(act_y) if g_y is None else g_y
+    if loss_sum is None:
+        loss_sum = torch.zeros(1, dtype=torch.float64, device=act_x.device)
+    _check(load().bvss_learn_pair_grad(_dptr(act_x), _dptr(act_y), act_x.stride(0),
+                                       _dptr(labels), n, m, L, temperature, scale, margin,
+                                       _dptr(g_x), _dptr(g_y), g_x.stride(0), _dptr(loss_sum),
+                                       _stream(stream)))
+    return g_x, g_y, loss_sum
+
+
+def bvss_learn_weight_grad(g_x, g_y, x_bf16, y_bf16, out=None, stream=None):
+    n, m = g_x.shape
+    d = x_bf16.shape[1]
+    out = torch.empty((m, d), dtype=torch.float32, device=g_x.device) if out is None else out
+    _check(load().bvss_learn_weight_grad(_dptr(g_x), _dptr(g_y), g_x.stride(0), _dptr(x_bf16),
+                                         _dptr(y_bf16), n, m, d, _dptr(out), _stream(stream)))
+    return out
+
+
+def bvss_learn_update(w, dw, eta, row_norm, wq_bf16=None, absmax=None, stream=None):
+    """In place: w <- rows rescaled to row_norm of w - eta dw / max|dw|; returns
+    (wq_bf16, absmax)."""
+    m, d = w.shape
+    wq_bf16 = torch.empty((m, d), dtype=torch.bfloat16, device=w.device) if wq_bf16 is None \
+        else wq_bf16
+    absmax = torch.empty(1, dtype=torch.float32, device=w.device) if absmax is None else absmax
+    _check(load().bvss_learn_update(_dptr(w), _dptr(dw), m, d, eta, row_norm, _dptr(absmax),
+                                    _dptr(wq_bf16), _stream(stream)))
+    return wq_bf16, absmax
+
+
+def bvss_index_rows_bf16(ix: Index, rows: torch.Tensor, out=None, stream=None):
+    n = rows.shape[0]
+    out = torch.empty((n, ix.d), dtype=torch.bfloat16, device=ix.device) if out is None else out
+    _check(load().bvss_index_rows_bf16(ix.handle, _dptr(rows), n, _dptr(out), _stream(stream)))
+    return out
+
+
+def bvss_nearest_rows(ix: Index, q_vectors: torch.Tensor, q_offsets, sets: torch.Tensor,
+                      stream=None):
+    """(Vq, k) int64 global rows: each query vector's nearest vector in each of its query
+    set's k neighbour sets."""
+    off, off_p = _host_i64(q_offsets)
+    nq, k = sets.shape
+    rows = torch.empty((int(off[-1]), k), dtype=torch.int64, device=ix.device)
+    _check(load().bvss_nearest_rows(ix.handle, _dptr(q_vectors), off_p, nq, _dptr(sets), k,
+                                    _dptr(rows), _stream(stream)))
+    return rows
 
 
 def bvss_free(ix: Index):

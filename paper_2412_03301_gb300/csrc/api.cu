@@ -90,6 +90,8 @@ void free_workspace(Workspace &w) {
     dfree(w.cand);
     dfree(w.cand_dist);
     dfree(w.pair);
+    dfree(w.enc_x);
+    dfree(w.enc_act);
     dfree(w.out_ids);
     dfree(w.out_dist);
     w = Workspace();
@@ -105,6 +107,7 @@ void free_index(bvss_index *ix) {
     dfree(ix->vscale8);
     dfree(ix->vnorm8);
     dfree(ix->rstat);
+    dfree(ix->wproj16);
     dfree(ix->set_off);
     dfree(ix->proj);
     dfree(ix->codes);
@@ -217,6 +220,10 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
     if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
+    if (ix->wproj16) {
+        BVSS_CU(dalloc(&w.enc_x, (size_t)kEncChunk * d));
+        BVSS_CU(dalloc(&w.enc_act, (size_t)kEncChunk * m));
+    }
     if (need_out) {
         BVSS_CU(dalloc(&w.out_ids, (size_t)nq * k));
         BVSS_CU(dalloc(&w.out_dist, (size_t)nq * k));
@@ -314,6 +321,31 @@ struct Knobs {
     int stages = 0;     // tensor-core refine: depth of the copy ring (0: the most that fit)
 };
 
+// Codes (Def. 7) of n vectors x (device FP32) with the index's projection: the sparse
+// binary FlyHash W, or the learned dense layer -- blocks of kEncChunk vectors rounded to
+// BF16, their activations on the tensor cores (launch_dense_gemm), then WTA.  xb / act:
+// kEncChunk x d BF16 and kEncChunk x m FP32 of scratch (dense layer only).  n_dev: the
+// count, read on the device (the dense layer then encodes all n rows).  Counts launches.
+int encode_vectors(const bvss_index *ix, const float *x, int64_t n, uint16_t *pos,
+                   uint32_t *mask, __nv_bfloat16 *xb, float *act, cudaStream_t st,
+                   const int64_t *n_dev, int64_t *launches) {
+    const int d = ix->p.d, m = ix->p.m, L = ix->p.wta_l;
+    if (!ix->wproj16) {
+        BVSS_CU(launch_encode(x, n, d, ix->proj, m, ix->p.fanin, L, pos, mask, st, n_dev));
+        if (launches) ++*launches;
+        return BVSS_OK;
+    }
+    for (int64_t v0 = 0; v0 < n; v0 += kEncChunk) {
+        const int64_t nb = n - v0 < kEncChunk ? n - v0 : kEncChunk;
+        BVSS_CU(launch_rows_bf16(x + v0 * d, d, nullptr, nb, xb, st));
+        BVSS_CU(launch_dense_gemm(xb, nb, d, ix->wproj16, m, act, m, ix->err, st));
+        BVSS_CU(launch_encode_dense(act, nb, m, m, L, pos ? pos + v0 * L : nullptr,
+                                    mask ? mask + v0 * (m / 32) : nullptr, st));
+        if (launches) *launches += 3;
+    }
+    return BVSS_OK;
+}
+
 int check_search(const bvss_index *ix, const bvss_search *s) {
     if (!s) return fail(BVSS_EINVAL, "search parameters are NULL");
     const int L = ix->p.wta_l;
@@ -375,9 +407,9 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     if (ev) BVSS_CU(cudaEventRecord(ev[0], st));
     // Alg. 6 lines 1-4 (Alg. 2 lines 2-5: the codes only)
     if (b.enc_n > 0) {
-        BVSS_CU(launch_encode(qv, b.enc_n, d, ix->proj, m, ix->p.fanin, L, w.qpos, nullptr, st,
-                              b.enc_n_dev));
-        ++n;
+        const int rc = encode_vectors(ix, qv, b.enc_n, w.qpos, nullptr, w.enc_x, w.enc_act, st,
+                                      b.enc_n_dev, &n);
+        if (rc) return rc;
     }
     if (!alg2) {
         BVSS_CU(launch_query_prep(w.qpos, b.qoff, nb, m, L, A, w.sq, w.plist, b.cq_trace, st));
@@ -623,9 +655,10 @@ int plan_enqueue(bvss_plan *p, cudaStream_t st, int64_t *launches) {
     k_plan_offsets<<<1, 1024, 0, st>>>(p->qoff_in, p->n_q, p->max_qset, p->max_v, p->qoff,
                                        ix->err);
     BVSS_CU(cudaGetLastError());
-    BVSS_CU(launch_encode(p->qv, p->max_v, ix->p.d, ix->proj, ix->p.m, ix->p.fanin,
-                          ix->p.wta_l, p->w.qpos, nullptr, st, p->qoff + p->n_q));
-    *launches = 2;
+    *launches = 1;
+    const int rc0 = encode_vectors(ix, p->qv, p->max_v, p->w.qpos, nullptr, p->w.enc_x,
+                                   p->w.enc_act, st, p->qoff + p->n_q, launches);
+    if (rc0) return rc0;
     const int64_t QB = p->w.cap_q;
     for (int64_t b0 = 0; b0 < p->n_q; b0 += QB) {
         Batch b;
@@ -699,22 +732,30 @@ int record_error(int code, const char *fmt, ...) {
 
 }  // namespace bvss
 
-extern "C" {
+namespace {
 
-int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
-               const uint16_t *proj, const bvss_params *params, void *stream,
+// bvss_build (proj: the sparse binary FlyHash projection) and bvss_build_dense (w: the
+// learned dense layer, m x d FP32, host or device, rounded to BF16)
+int build_impl(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+               const uint16_t *proj, const float *w, const bvss_params *params, void *stream,
                bvss_index **out) {
     if (!out) return fail(BVSS_EINVAL, "out is NULL");
     *out = nullptr;
-    int rc = check_params(params);
+    if (!params) return fail(BVSS_EINVAL, "params is NULL");
+    bvss_params p = *params;
+    if (w) p.fanin = 1;   // not used by the dense layer; checked as the smallest fan-in
+    int rc = check_params(&p);
     if (rc) return rc;
+    if (w && (p.d % 64 != 0 || p.m % 128 != 0))
+        return fail(BVSS_EINVAL, "the dense projection needs d %% 64 == 0 and m %% 128 == 0 "
+                                 "(d = %d, m = %d)", p.d, p.m);
+    if (w) p.fanin = 0;
     if (n_sets < 1 || n_sets > 0x7fffffffLL)
         return fail(BVSS_EINVAL, "n_sets = %lld: need 1 <= n_sets < 2^31", (long long)n_sets);
-    if (!vectors || !proj) return fail(BVSS_EINVAL, "vectors or proj is NULL");
+    if (!vectors || (!proj && !w)) return fail(BVSS_EINVAL, "vectors or projection is NULL");
     rc = check_offsets(set_offsets, n_sets, 0, "database");
     if (rc) return rc;
-    const bvss_params p = *params;
-    for (int j = 0; j < p.m; ++j) {
+    for (int j = 0; j < p.m && proj; ++j) {
         const uint16_t *row = proj + (int64_t)j * p.fanin;
         for (int t = 0; t < p.fanin; ++t) {
             if (row[t] >= p.d) return fail(BVSS_EINVAL, "proj[%d][%d] = %d >= d", j, t, row[t]);
@@ -736,7 +777,8 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         BVSS_CU(dalloc(&ix->vec, (size_t)nv * p.d));
         BVSS_CU(dalloc(&ix->vnorm, (size_t)nv));
         BVSS_CU(dalloc(&ix->set_off, (size_t)n_sets + 1));
-        BVSS_CU(dalloc(&ix->proj, (size_t)p.m * p.fanin));
+        if (proj) BVSS_CU(dalloc(&ix->proj, (size_t)p.m * p.fanin));
+        if (w) BVSS_CU(dalloc(&ix->wproj16, (size_t)p.m * p.d));
         BVSS_CU(dalloc(&ix->codes, (size_t)nv * p.wta_l));
         BVSS_CU(dalloc(&ix->sketch, (size_t)n_sets * ix->W));
         BVSS_CU(dalloc(&ix->spop, (size_t)n_sets));
@@ -752,8 +794,25 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         BVSS_CU(cudaMemcpyAsync(ix->vec, vectors, sizeof(float) * (size_t)nv * p.d, kind, st));
         BVSS_CU(cudaMemcpyAsync(ix->set_off, set_offsets, sizeof(int64_t) * (size_t)(n_sets + 1),
                                 cudaMemcpyHostToDevice, st));
-        BVSS_CU(cudaMemcpyAsync(ix->proj, proj, sizeof(uint16_t) * (size_t)p.m * p.fanin,
-                                cudaMemcpyHostToDevice, st));
+        if (proj)
+            BVSS_CU(cudaMemcpyAsync(ix->proj, proj, sizeof(uint16_t) * (size_t)p.m * p.fanin,
+                                    cudaMemcpyHostToDevice, st));
+        if (w) {
+            // the layer's weights in BF16 (round to nearest even), from host or device
+            float *wd = nullptr;
+            const float *wsrc = w;
+            if (!is_device_ptr(w)) {
+                BVSS_CU(dalloc(&wd, (size_t)p.m * p.d));
+                BVSS_CU(cudaMemcpyAsync(wd, w, sizeof(float) * (size_t)p.m * p.d,
+                                        cudaMemcpyHostToDevice, st));
+                wsrc = wd;
+            }
+            BVSS_CU(launch_rows_bf16(wsrc, p.d, nullptr, p.m, ix->wproj16, st));
+            if (wd) {
+                BVSS_CU(cudaStreamSynchronize(st));
+                dfree(wd);
+            }
+        }
         BVSS_CU(cudaMemsetAsync(ix->flag, 0, sizeof(int), st));
         BVSS_CU(launch_check_finite(ix->vec, nv * p.d, ix->flag, st));
         int bad = 0;
@@ -776,8 +835,23 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
         BVSS_CU(dalloc(&ix->rstat, 4));
         BVSS_CU(launch_round_stats(ix->vec, nv, p.d, ix->vec16, ix->vec8, ix->vscale8, ix->rstat,
                                    st));
-        BVSS_CU(launch_encode(ix->vec, nv, p.d, ix->proj, p.m, p.fanin, p.wta_l, ix->codes,
-                              nullptr, st));
+        {
+            // Alg. 1: codes of every database vector (the dense layer in blocks)
+            __nv_bfloat16 *xb = nullptr;
+            float *act = nullptr;
+            if (w) {
+                BVSS_CU(dalloc(&xb, (size_t)kEncChunk * p.d));
+                BVSS_CU(dalloc(&act, (size_t)kEncChunk * p.m));
+            }
+            const int r2 = encode_vectors(ix, ix->vec, nv, ix->codes, nullptr, xb, act, st,
+                                          nullptr, nullptr);
+            if (w) {
+                cudaStreamSynchronize(st);
+                dfree(xb);
+                dfree(act);
+            }
+            if (r2) return r2;
+        }
         BVSS_CU(launch_build_filters(ix->codes, ix->set_off, n_sets, p.m, p.wta_l, ix->sketch,
                                      ix->count, st));
         BVSS_CU(launch_sketch_pop(ix->sketch, n_sets, ix->W, ix->spop, st));
@@ -794,6 +868,24 @@ int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
     }
     *out = ix;
     return BVSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bvss_build(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+               const uint16_t *proj, const bvss_params *params, void *stream,
+               bvss_index **out) {
+    if (!proj) return fail(BVSS_EINVAL, "proj is NULL");
+    return build_impl(vectors, set_offsets, n_sets, proj, nullptr, params, stream, out);
+}
+
+int bvss_build_dense(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
+                     const float *w, const bvss_params *params, void *stream,
+                     bvss_index **out) {
+    if (!w) return fail(BVSS_EINVAL, "w is NULL");
+    return build_impl(vectors, set_offsets, n_sets, nullptr, w, params, stream, out);
 }
 
 int bvss_query(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
@@ -820,8 +912,67 @@ int bvss_encode(const bvss_index *ix, const float *x, int64_t n, uint16_t *pos, 
         return fail(BVSS_EINVAL, "pos / mask must be device memory");
     int rc = check_device(ix);
     if (rc) return rc;
-    BVSS_CU(launch_encode(x, n, ix->p.d, ix->proj, ix->p.m, ix->p.fanin, ix->p.wta_l, pos, mask,
-                          reinterpret_cast<cudaStream_t>(stream)));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    __nv_bfloat16 *xb = nullptr;
+    float *act = nullptr;
+    if (ix->wproj16) {   // a block of scratch for the dense layer
+        BVSS_CU(dalloc(&xb, (size_t)kEncChunk * ix->p.d));
+        rc = dalloc(&act, (size_t)kEncChunk * ix->p.m) == cudaSuccess
+                 ? BVSS_OK : fail(BVSS_ENOMEM, "bvss_encode: scratch allocation failed");
+        if (rc) {
+            dfree(xb);
+            return rc;
+        }
+    }
+    rc = encode_vectors(ix, x, n, pos, mask, xb, act, st, nullptr, nullptr);
+    if (ix->wproj16) {
+        cudaStreamSynchronize(st);
+        dfree(xb);
+        dfree(act);
+    }
+    return rc;
+}
+
+int bvss_nearest_rows(const bvss_index *ix, const float *q_vectors, const int64_t *q_offsets,
+                      int64_t n_queries, const int64_t *sets, int32_t k, int64_t *rows,
+                      void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (n_queries < 0 || n_queries > 0x7fffffffLL || k < 1)
+        return fail(BVSS_EINVAL, "bvss_nearest_rows: need 0 <= n_queries < 2^31 and k >= 1");
+    if (n_queries == 0) return BVSS_OK;
+    if (!q_vectors || !sets || !rows || !is_device_ptr(q_vectors) || !is_device_ptr(sets) ||
+        !is_device_ptr(rows))
+        return fail(BVSS_EINVAL, "bvss_nearest_rows: vectors, sets and rows must be device "
+                                 "memory");
+    int rc = check_offsets(q_offsets, n_queries, BVSS_MAX_QSET, "query");
+    if (rc) return rc;
+    rc = check_device(ix);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int64_t *qoff = nullptr;
+    BVSS_CU(dalloc(&qoff, (size_t)n_queries + 1));
+    cudaError_t e = cudaMemcpyAsync(qoff, q_offsets, sizeof(int64_t) * (size_t)(n_queries + 1),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_nearest(q_vectors, qoff, (int)n_queries, ix->p.d, ix->vec, ix->set_off,
+                           ix->n_sets, sets, k, rows, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(qoff);
+    if (e != cudaSuccess) return fail(BVSS_ECUDA, "bvss_nearest_rows: %s", cudaGetErrorString(e));
+    return BVSS_OK;
+}
+
+int bvss_index_rows_bf16(const bvss_index *ix, const int64_t *rows, int64_t n, void *out,
+                         void *stream) {
+    if (!ix) return fail(BVSS_EINVAL, "index is NULL");
+    if (n < 0) return fail(BVSS_EINVAL, "n < 0");
+    if (n == 0) return BVSS_OK;
+    if (!rows || !out || !is_device_ptr(rows) || !is_device_ptr(out))
+        return fail(BVSS_EINVAL, "bvss_index_rows_bf16: rows and out must be device memory");
+    int rc = check_device(ix);
+    if (rc) return rc;
+    BVSS_CU(launch_rows_bf16(ix->vec, ix->p.d, rows, n, static_cast<__nv_bfloat16 *>(out),
+                             reinterpret_cast<cudaStream_t>(stream), ix->n_vec));
     return BVSS_OK;
 }
 

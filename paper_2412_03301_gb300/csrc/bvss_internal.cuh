@@ -48,6 +48,8 @@ struct Workspace {
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
+    __nv_bfloat16 *enc_x = nullptr;  // dense projection: a block of query vectors in BF16
+    float *enc_act = nullptr;        //   and their activations (kEncChunk x d, x m)
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
     float *out_dist = nullptr;
     int cap_k = 0;
@@ -69,7 +71,10 @@ struct bvss_index {
     float *vscale8 = nullptr;         // its per-vector scales
     float *vnorm8 = nullptr;          // squared norms of the scaled FP8 values
     float *rstat = nullptr;           // [0] largest norm, [1] / [2] largest rounding-error
-                                      // norm of the BF16 / FP8 copy (rounded up)
+                                      // norm of the BF16 / FP8 copy (rounded up), [3] the
+                                      // largest frac_bits of the values
+    __nv_bfloat16 *wproj16 = nullptr; // learned dense projection (m x d BF16), or null for
+                                      // the sparse binary FlyHash projection proj
     int64_t *set_off = nullptr;  // n_sets + 1
     uint16_t *proj = nullptr;    // m x F
     uint16_t *codes = nullptr;   // n_vec x L, ascending positions
@@ -99,11 +104,29 @@ struct bvss_index {
 namespace bvss {
 
 // ---- encode.cu --------------------------------------------------------------
+constexpr int64_t kEncChunk = 4096;   // vectors per block of the dense projection
 // FlyHash (Def. 7): pos[v] = ascending L winners, mask[v] = code bits.  With n_dev,
 // the count is min(n, *n_dev) read on the device (n is then the capacity).
 cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj,
                           int m, int F, int L, uint16_t *pos, uint32_t *mask,
                           cudaStream_t st, const int64_t *n_dev = nullptr);
+// WTA of dense activations act (n x m, row stride lda) into codes, as launch_encode
+cudaError_t launch_encode_dense(const float *act, int64_t n, int64_t lda, int m, int L,
+                                uint16_t *pos, uint32_t *mask, cudaStream_t st,
+                                const int64_t *n_dev = nullptr);
+// ---- dense.cu: the learned projection's BF16 layer on the tensor cores -----------------
+// D (n x m, row stride ldd) = X (n x d) W^T (W: m x d), BF16 in, FP32 out; d % 64 == 0,
+// m % 128 == 0; a bounded wait that gives up sets bit 4 of *err
+cudaError_t launch_dense_gemm(const __nv_bfloat16 *X, int64_t n, int d, const __nv_bfloat16 *W,
+                              int m, float *D, int64_t ldd, int *err, cudaStream_t st);
+// BF16 copies of FP32 rows: rows null -> rows 0..n-1, else the listed rows of the n_src
+// rows of x (ids outside [0, n_src) give zero rows)
+cudaError_t launch_rows_bf16(const float *x, int d, const int64_t *rows, int64_t n,
+                             __nv_bfloat16 *out, cudaStream_t st, int64_t n_src = 0);
+// rows[a][t]: the row nearest to query vector a in set sets[q][t] of its query set q
+cudaError_t launch_nearest(const float *qvec, const int64_t *qoff, int n_q, int d,
+                           const float *vec, const int64_t *set_off, int64_t n_sets,
+                           const int64_t *sets, int k, int64_t *rows, cudaStream_t st);
 // Alg. 6 lines 1-4 for n_q query sets (codes qpos, offsets qoff relative to qpos).
 cudaError_t launch_query_prep(const uint16_t *qpos, const int64_t *qoff, int n_q,
                               int m, int L, int A, uint32_t *sq, uint16_t *plist,

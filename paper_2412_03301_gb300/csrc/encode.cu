@@ -47,7 +47,8 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_dev, int d,
          int dpad, int rep, const uint16_t *__restrict__ proj, int m, int F, int L,
-         uint16_t *__restrict__ pos, uint32_t *__restrict__ mask) {
+         uint16_t *__restrict__ pos, uint32_t *__restrict__ mask,
+         const float *__restrict__ act, int64_t lda) {
     extern __shared__ uint32_t sm[];
     // rep (a power of two <= 32) copies of the vector, interleaved: value k of copy c
     // at xs[k * rep + c].  Lane l reads copy l % rep, so lanes l and l' can only meet in
@@ -66,6 +67,12 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
     const int W = m >> 5;
     if (n_dev && *n_dev < n) n = *n_dev;   // the vector count, when it lives on the device
     for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
+      if (act) {
+        // activations of a dense layer, computed elsewhere (the learned projection)
+        const float *av = act + v * lda;
+        for (int j = tid; j < m; j += THREADS) key[j] = order_key(av[j]);
+        __syncthreads();
+      } else {
         const float *xv = x + v * (int64_t)d;
         const int rs = __ffs(rep) - 1;
         float *x0 = reinterpret_cast<float *>(key);    // plain copy, until the keys are written
@@ -112,6 +119,7 @@ k_encode(const float *__restrict__ x, int64_t n, const int64_t *__restrict__ n_d
                 key[j] = order_key(a);
             }
         }
+      }
 
         // exact L-th largest key: radix select, most significant digit first
         uint32_t prefix = 0, pmask = 0;
@@ -297,7 +305,25 @@ cudaError_t launch_encode(const float *x, int64_t n, int d, const uint16_t *proj
     if (e != cudaSuccess) return e;
     const int64_t grid = n < (int64_t)1 << 30 ? n : (int64_t)1 << 30;
     kern<<<(unsigned)grid, wide ? kEncWide : kEncThreads, smem, st>>>(x, n, n_dev, d, dpad, rep,
-                                                                      proj, m, F, L, pos, mask);
+                                                                      proj, m, F, L, pos, mask,
+                                                                      nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_dense(const float *act, int64_t n, int64_t lda, int m, int L,
+                                uint16_t *pos, uint32_t *mask, cudaStream_t st,
+                                const int64_t *n_dev) {
+    if (n <= 0) return cudaSuccess;
+    // the keys, histogram and code words only (no copies of the vector)
+    const size_t smem = sizeof(uint32_t) * ((size_t)m + 2048 + 2 * (m / 32));
+    const bool wide = m % kEncWide == 0;
+    auto kern = wide ? k_encode<kEncWide> : k_encode<kEncThreads>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = n < (int64_t)1 << 30 ? n : (int64_t)1 << 30;
+    kern<<<(unsigned)grid, wide ? kEncWide : kEncThreads, smem, st>>>(
+        nullptr, n, n_dev, 0, 0, 1, nullptr, m, 0, L, pos, mask, act, lda);
     return cudaGetLastError();
 }
 
