@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--alg2-queries", type=int, default=100,
                     help="query sets for the plain BioVSS search (Alg. 2) line; 0 skips it")
+    ap.add_argument("--learned", type=int, default=1,
+                    help="1: also train the learned projection and compare it with FlyHash")
+    ap.add_argument("--learned-train-queries", type=int, default=20000)
+    ap.add_argument("--learned-pairs", type=int, default=2_000_000)
     ap.add_argument("--offgrid", type=int, default=1,
                     help="1: also time the three refine forms on the large workload off the "
                          "2^-8 grid and check them against the FP64 oracle")
@@ -214,6 +218,76 @@ def true_d2_of(vec, vnorm, qvec, qoff, offsets, qids, ids):
             D.clamp_(min=0)
             out[j, c] = float(torch.maximum(D.min(1).values.max(), D.min(0).values.max()))
     return out
+
+
+# --------------------------------------------------------------------------
+# the learned projection (BioHash in place of FlyHash): trained on mined pairs
+# --------------------------------------------------------------------------
+def learned_line(args, dev, stream, ix, w, c, qids, gt_ids, gt_d2, vec, vnorm):
+    """Train the dense layer on pairs mined from the exact refine's neighbours of
+    20,000 training query sets (1M positives, 1M hard negatives, 5 epochs of 10k-pair
+    batches), build the learned index, and compare recall@10 and query sets/s with the
+    random FlyHash index at several candidate budgets C (BF16 fast form both)."""
+    from paper_2412_03301_gb300 import bvss, datagen, learn
+    off, qv, qo = w["offsets"], w["q_vectors"], w["q_offsets"]
+    nq = qo.shape[0] - 1
+    ts = datagen.set_sizes(args.learned_train_queries, c["q_lo"], c["q_hi"], 777 + args.seed)
+    mix = datagen.Mixture(c["d"], c["n_components"], args.seed, device=dev)
+    tq = mix.draw_sets(ts, 778 + args.seed)
+    to = datagen.offsets_from_sizes(ts)
+    t0 = time.perf_counter()
+    pairs = learn.mine_pairs(ix, tq, to, k=c["k"], C=c["C"], n_pos=args.learned_pairs // 2,
+                             n_neg=args.learned_pairs // 2, seed=5 + args.seed, hard=50)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    w0 = learn.flyhash_dense(w["proj"], c["d"])
+    wl, wq, hist = learn.train(ix, tq, pairs, w0, L=c["L"], epochs=5, batch=10_000,
+                               seed=args.seed)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    lix = bvss.bvss_build_dense(w["vectors"], off, wq.float().contiguous(), wta_l=c["L"],
+                                bf16=True)
+    torch.cuda.synchronize(dev)
+    t3 = time.perf_counter()
+    out_ids = torch.empty((nq, c["k"]), dtype=torch.int64, device=dev)
+    out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
+    nr = len(qids)
+
+    def measure(index, C):
+        kw = dict(k=c["k"], C=C, A=c["A"], M=c["M"], fast=True)
+        for _ in range(max(1, args.warmup)):
+            bvss.bvss_query(index, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kw)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(2, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(reps):
+            bvss.bvss_query(index, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        got = out_ids[:nr].cpu().numpy()
+        d2 = true_d2_of(vec, vnorm, qv, qo, off, qids, got)
+        r = recall_at_k(got, gt_ids, gt_d2, d2, c["k"])
+        return {"C": C, "value": nq / (ms / 1e3), "ms_per_step": ms, "recall_at_10": r[0],
+                "recall_at_10_ties": r[1]}
+
+    budgets = (500, 750, 1000, 1250, 1500, 1750, 2000)
+    learned = [measure(lix, C) for C in budgets]
+    flyhash = [measure(ix, C) for C in budgets]
+    lix.close()
+    return {"train_query_sets": int(ts.shape[0]), "pairs": int(pairs[0].shape[0]),
+            "hard_negatives": "nearest vector in a set ranked 11-50 by the exact refine",
+            "epochs": 5, "batch": 10_000, "steps": len(hist), "mine_s": t1 - t0,
+            "train_s": t2 - t1, "build_s": t3 - t2,
+            "loss_first": hist[0][0], "loss_last": hist[-1][0],
+            "update_magnitude_first": hist[0][1], "update_magnitude_last": hist[-1][1],
+            "grad_absmax_first": hist[0][2], "grad_absmax_last": hist[-1][2],
+            "recall_queries": nr, "learned": learned, "flyhash": flyhash,
+            "form": "BF16 dense 384->4096 layer on the tensor cores (tcgen05), WTA top-64; "
+                    "BF16 fast refine"}
 
 
 # --------------------------------------------------------------------------
@@ -719,6 +793,10 @@ def run_ours(args, rank, world, local_rank):
             rec["alg2"] = dict(zip(("recall_at_10", "recall_at_10_ties"),
                                    recall_at_k(got2, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(),
                                                d2_2, c["k"])))
+        if args.learned and args.workload == "large":
+            rec["learned_projection"] = learned_line(args, dev, stream, ix, w, c, qids,
+                                                     gt_ids.cpu().numpy(), gt_d2.cpu().numpy(),
+                                                     vec, vnorm)
         del vnorm, set_of_row
 
     # CPU baseline sample (rank 0): copy the sample before freeing the database
@@ -854,6 +932,29 @@ def run_ours(args, rank, world, local_rank):
                "parts_s": {"query_filters": float(parts[0]), "scan_scaled": float(parts[1]),
                            "refine_scaled": float(parts[2])}}
 
+    # the learned projection against the plain FP32 random-FlyHash form at equal recall:
+    # the smallest budget at which the learned fast form reaches the recall the FlyHash
+    # indexes reach at the workload's own C
+    learned = rec.pop("learned_projection", None) if rec else None
+    if learned:
+        target = max(r["recall_at_10_ties"] for r in learned["flyhash"] if r["C"] == c["C"])
+        ok = [r for r in learned["learned"] if r["recall_at_10_ties"] >= target]
+        best = min(ok, key=lambda r: r["C"]) if ok else None
+        learned["equal_recall"] = {
+            "target_recall_at_10_ties": target, "target": "FlyHash at C=%d" % c["C"],
+            "learned_C": best["C"] if best else None,
+            "learned_value": best["value"] if best else None,
+            "plain_fp32_flyhash_value": world * nq / (ms_plain / 1e3),
+            "learned_over_plain": best["value"] / (world * nq / (ms_plain / 1e3)) if best
+            else None}
+        # the metric's own operating point: the fastest budget with recall@10 >= 0.95
+        for name in ("learned", "flyhash"):
+            ok95 = [r for r in learned[name] if r["recall_at_10_ties"] >= 0.95]
+            b95 = max(ok95, key=lambda r: r["value"]) if ok95 else None
+            learned[name + "_at_0.95"] = ({"C": b95["C"], "value": b95["value"],
+                                          "recall_at_10_ties": b95["recall_at_10_ties"]}
+                                         if b95 else None)
+
     # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
     roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok)
     ix.close()
@@ -886,6 +987,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "alg2": alg2,
         "fp8": fp8,
+        "learned": learned,
         "offgrid": offgrid,
         "serving": serving,
         "clocks": clk,

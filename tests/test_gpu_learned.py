@@ -200,3 +200,30 @@ def test_index_rows_in_bf16(bv):
     out = bv.bvss_index_rows_bf16(ix, rows).cpu()
     want = w["vectors"][[0, 5, ix.n_vectors - 1]].to(torch.bfloat16)
     assert torch.equal(out[:3], want) and torch.all(out[3:] == 0)
+
+
+def test_training_pipeline_small(bv, orc):
+    """Mine pairs with the library's refine, train two epochs, build the learned index:
+    the loss falls, the first step's update magnitude is eta0, the forward weights stay
+    on the 2^-8 grid, and the trained layer's codes equal the oracle's."""
+    from paper_2412_03301_gb300 import learn
+    w = datagen.workload(n_sets=2000, size_lo=2, size_hi=10, d=128, n_components=32,
+                         n_queries=4, q_lo=2, q_hi=8, m=1024, fanin=8, seed=21)
+    ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=16, bf16=True)
+    ts = datagen.set_sizes(300, 2, 8, 22)
+    tq = datagen.Mixture(128, 32, 21).draw_sets(ts, 23).cuda()
+    pairs = learn.mine_pairs(ix, tq, datagen.offsets_from_sizes(ts), k=5, C=200, n_pos=3000,
+                             n_neg=3000, seed=24, hard=20)
+    assert int(pairs[2].sum()) == 3000 and pairs[0].shape[0] == 6000
+    wl, wq, hist = learn.train(ix, tq, pairs, learn.flyhash_dense(w["proj"], 128), L=16,
+                               epochs=2, batch=1000, eta0=0.002)
+    assert len(hist) == 12 and hist[0][1] == pytest.approx(0.002)
+    assert np.mean([h[0] for h in hist[-3:]]) < np.mean([h[0] for h in hist[:3]])
+    q = wq.float().cpu().numpy()
+    assert np.all(q * 256 == np.round(q * 256)) and np.abs(q).max() <= 1.0
+    np.testing.assert_allclose(wl.norm(dim=1).cpu().numpy(), 8 ** 0.5, rtol=1e-5)
+    lix = bv.bvss_build_dense(w["vectors"].cuda(), w["offsets"], wq.float().contiguous(),
+                              wta_l=16)
+    got = bv.bvss_get_codes(lix, 0, lix.n_vectors).cpu().numpy().view(np.uint16)
+    want, _ = orc.dense_encode(w["vectors"].numpy(), q, 16)
+    assert np.array_equal(got, want)
