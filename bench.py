@@ -62,6 +62,9 @@ def parse():
                     help="1: also time the three refine forms on the large workload off the "
                          "2^-8 grid and check them against the FP64 oracle")
     ap.add_argument("--offgrid-recall-queries", type=int, default=100)
+    ap.add_argument("--fp8-high-d", type=int, default=1,
+                    help="1: also run every refine form at the FP8 load (500k sets, d = 1024)")
+    ap.add_argument("--fp8-recall-queries", type=int, default=100)
     ap.add_argument("--serving-queries", type=int, default=4096,
                     help="query sets per pass of the batched serving line (200k Zipf-sized "
                          "sets, d=768, one graph launch per pass); 0 skips it")
@@ -396,6 +399,104 @@ def offgrid_line(args, dev, stream):
 
 
 # --------------------------------------------------------------------------
+# the FP8 refine at its own load: 500k Zipf-sized sets at d = 1024, C = 4000
+# --------------------------------------------------------------------------
+def fp8_high_d_line(args, dev, stream):
+    """datagen.FP8_HIGH_D: every refine form on the same 2000 query sets (C = 4000):
+    query sets/s, the FP8 refine's HBM fraction, ids against the exact FP32 form, recall@10
+    decided in FP64 and every returned distance against the oracle's FP64 value on the
+    first query sets."""
+    from paper_2412_03301_gb300 import bvss, datagen
+    c = dict(datagen.FP8_HIGH_D)
+    c["A"], c["M"] = 3, 1
+    w = datagen.workload(n_sets=c["n_sets"], size_lo=c["size_lo"], size_hi=c["size_hi"],
+                         d=c["d"], n_components=c["n_components"], n_queries=c["n_queries"],
+                         q_lo=c["q_lo"], q_hi=c["q_hi"], m=c["m"], fanin=c["fanin"],
+                         seed=args.seed + 11, device=dev, size_dist="zipf", q_dist="zipf")
+    off, qv, qo = w["offsets"], w["q_vectors"], w["q_offsets"]
+    nq = qo.shape[0] - 1
+    t0 = time.perf_counter()
+    ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=True, fp8=True)
+    torch.cuda.synchronize(dev)
+    build_s = time.perf_counter() - t0
+    kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"])
+    tr = bvss.bvss_query_trace(ix, qv, qo, **kw)
+    torch.cuda.synchronize(dev)
+    sizes = torch.from_numpy(np.diff(off)).to(dev)
+    cand = tr["cand"]
+    cand_rows = int(sizes[cand.clamp(min=0).to(torch.int64)].masked_fill(cand < 0, 0).sum())
+    del tr, cand
+    out_ids = torch.empty((nq, c["k"]), dtype=torch.int64, device=dev)
+    out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
+    hbm, basis = measured_peaks()
+    forms, res = {}, {}
+    for name, f in (("plain", {}), ("fast", {"fast": True}), ("fp8", {"fp8": True}),
+                    ("fp8_exact", {"fp8": True, "fp8_exact": True})):
+        bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw, **f)
+        torch.cuda.synchronize(dev)
+        bvss.bvss_profile_enable(ix, True)
+        bvss.bvss_profile_read(ix, reset=True)
+        reps = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
+                            **kw, **f)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st, _, nl = bvss.bvss_profile_read(ix, reset=True)
+        bvss.bvss_profile_enable(ix, False)
+        bvss.bvss_sync(ix, stream)
+        ms = e0.elapsed_time(e1) / reps
+        stages = {k_: v / reps for k_, v in st.items()}
+        res[name] = (out_ids.cpu().numpy().copy(), out_dist.cpu().numpy().astype(np.float64))
+        forms[name] = {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                       "stages_ms_per_step": stages, "gpu_launches_per_step": nl // reps}
+        row_bytes = {"plain": 4, "fast": 2, "fp8": 1, "fp8_exact": 1}[name] * c["d"]
+        ach = cand_rows * row_bytes / (stages["refine"] / 1e3) / 1e9
+        forms[name]["refine_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm,
+                                          "unit": "GB/s", "frac": ach / hbm,
+                                          "peak_basis": basis,
+                                          "algorithmic_bytes": cand_rows * row_bytes}
+    ids_p = res["plain"][0]
+    same = {n_: int((res[n_][0] == ids_p).all(axis=1).sum()) for n_ in res if n_ != "plain"}
+    nr = min(args.fp8_recall_queries, nq)
+    vec = w["vectors"]
+    vnorm = (vec * vec).sum(1)
+    sor = torch.repeat_interleave(torch.arange(c["n_sets"], device=dev), sizes)
+    gt_ids, _ = exact_topk(vec, vnorm, sor, c["n_sets"], qv, qo, list(range(nr)), c["k"] + 5)
+    gt_ids = gt_ids.cpu().numpy()
+    del vnorm, sor
+    qvec_h = qv[:int(qo[nr])].cpu().numpy()
+    cache = {}
+
+    def vec_of(i):
+        if i not in cache:
+            cache[i] = vec[int(off[i]):int(off[i + 1])].cpu().numpy()
+        return cache[i]
+
+    for name in res:
+        ids, dist = res[name][0][:nr], res[name][1][:nr]
+        r, d64 = fp64_recall(ids, gt_ids, qvec_h, qo, vec_of, c["k"])
+        ok = np.isfinite(d64)
+        rel = np.abs(dist[ok] - d64[ok]) / np.maximum(d64[ok], 1e-30)
+        forms[name].update({"recall_at_10_fp64": r, "dist_rel_err_max": float(rel.max()),
+                            "dist_rel_err_mean": float(rel.mean())})
+    ix.close()
+    del w
+    torch.cuda.empty_cache()
+    return {"workload": "N=%d sets of Zipf 4-64 vectors (%d vectors), d=%d FP32 (grid 2^-8), "
+                        "%d-component mixture; FlyHash m=%d F=%d L=%d; %d query sets of Zipf "
+                        "4-64; A=%d M=%d C=%d k=%d" % (c["n_sets"], int(off[-1]), c["d"],
+                                                      c["n_components"], c["m"], c["fanin"],
+                                                      c["L"], nq, c["A"], c["M"], c["C"],
+                                                      c["k"]),
+            "build_s": build_s, "candidate_rows_per_step": cand_rows, "forms": forms,
+            "same_ids_as_plain": same, "query_sets": nq, "recall_queries": nr,
+            "dist_rel_err_bound_exact": (36 + -(-c["d"] // 32)) * 2.0 ** -24}
+
+
+# --------------------------------------------------------------------------
 # batched serving line: a query plan (one CUDA graph launch per pass)
 # --------------------------------------------------------------------------
 def serving_line(args, dev, stream):
@@ -725,7 +826,7 @@ def run_ours(args, rank, world, local_rank):
     w["q_vectors"], w["q_offsets"] = shard.replica_queries(w, c, args.seed, rank, device=dev)
     off = w["offsets"]
     t0 = time.perf_counter()
-    fp8_ok = c["d"] % 128 == 0 and c["q_hi"] <= 32
+    fp8_ok = c["d"] % 128 == 0 and c["q_hi"] <= 64
     ix = bvss.bvss_build(w["vectors"], off, w["proj"], wta_l=c["L"], bf16=c["d"] % 64 == 0,
                          fp8=fp8_ok)
     fast_ok = c["d"] % 64 == 0
@@ -768,7 +869,7 @@ def run_ours(args, rank, world, local_rank):
         got_d2 = true_d2_of(vec, vnorm, qv, qoff, off, qids, got)
         rs, rt = recall_at_k(got, gt_ids.cpu().numpy(), gt_d2.cpu().numpy(), got_d2, c["k"])
         rec = {"recall_at_10": rs, "recall_at_10_ties": rt, "queries": len(qids)}
-        if c["d"] % 128 == 0 and c["q_hi"] <= 32:
+        if c["d"] % 128 == 0 and c["q_hi"] <= 64:
             # FP8 refine: recall and the error of each returned distance against the
             # exact (FP32 GEMM-form on grid values) Hausdorff distance of the same set
             nr = len(qids)
@@ -963,6 +1064,8 @@ def run_ours(args, rank, world, local_rank):
                if args.offgrid and args.workload == "large" and rank == 0 else None)
     serving = (serving_line(args, dev, stream)
                if args.serving_queries > 0 and args.workload == "large" else None)
+    fp8_high_d = (fp8_high_d_line(args, dev, stream)
+                  if args.fp8_high_d and args.workload == "large" and rank == 0 else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -990,6 +1093,7 @@ def run_ours(args, rank, world, local_rank):
         "learned": learned,
         "offgrid": offgrid,
         "serving": serving,
+        "fp8_high_d": fp8_high_d,
         "clocks": clk,
         "build_s": build_s,
         "work": {"gated_pairs_per_step": gated_pairs, "candidates_per_step": sum_cand,

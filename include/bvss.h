@@ -115,9 +115,8 @@ typedef struct bvss_params {
                                deviations of the rounding model instead (independent zero-mean
                                errors per value: sqrt(e_q^2 + e_v^2) / sqrt(d) per distance) and
                                the top k are approximate; returned distances are still exact
-                               values (as in bvss_query) of the returned sets.  Batches with a
-                               query set of more than 32 vectors use the BF16 copy if the index
-                               has one, else the FP32 refine */
+                               values (as in bvss_query) of the returned sets.  Query sets of up
+                               to 64 vectors; batches with a larger one use the FP32 refine */
 #define BVSS_SEARCH_FP8_EXACT 16  /* with BVSS_SEARCH_FP8: the band from the rigorous bound, so
                                      the top k are exact as in bvss_query */
 

@@ -204,9 +204,8 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
                               const float *vec, const float *vnorm, const int64_t *set_off,
                               int d, const int32_t *cand, const int32_t *thr, int C,
                               float *cand_dist, int *err, cudaStream_t st);
-// refine_mma.cu: the same on the tensor cores from BF16 vectors (query sets <= 64) or
-// FP8 vectors (query sets <= 32)
-// f8: the FP8 copy (query sets <= 32, d % 128 == 0) instead of the BF16 one
+// refine_mma.cu: the same on the tensor cores from BF16 or FP8 vectors (query sets <= 64)
+// f8: the FP8 copy (d % 128 == 0) instead of the BF16 one
 bool refine_mma_supported(int d, int max_mq, bool f8 = false);
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st);

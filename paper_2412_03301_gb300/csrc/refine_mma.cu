@@ -576,10 +576,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
             float qreg[MQ];
 #pragma unroll
             for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
-            // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1
-            float qs2[F8 ? MQ : 1];
+            // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1.  The
+            // 64-wide FP8 instance reads the scales from shared memory (broadcast) to stay
+            // within its registers
+            constexpr bool kQsReg = F8 && MQ == 32;
+            float qs2[kQsReg ? MQ : 1];
 #pragma unroll
-            for (int a = 0; a < (F8 ? MQ : 1); ++a) qs2[a] = F8 ? 2.0f * qsc[a] : 2.0f;
+            for (int a = 0; a < (kQsReg ? MQ : 1); ++a) qs2[a] = kQsReg ? 2.0f * qsc[a] : 2.0f;
             const int r = warp * 32 + lane;
             bool ok = true;
             for (int t = 0; t < n_tiles; ++t) {
@@ -623,7 +626,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                             for (int i = 0; i < 4; ++i) {
                                 const int a = c4 * 4 + i;
                                 // qreg is +inf past the query, which keeps those entries out
-                                const float w2 = F8 ? qs2[F8 ? a : 0] * m.sc : 2.0f;
+                                const float w2 =
+                                    F8 ? (kQsReg ? qs2[kQsReg ? a : 0] : 2.0f * qsc[a]) * m.sc
+                                       : 2.0f;
                                 const float d2 =
                                     fmaxf(qreg[a] + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
                                 x[i] = d2;
@@ -802,7 +807,7 @@ inline int mq_for(int max_mq) { return max_mq <= 32 ? 32 : 64; }
 inline int kblocks(int d, bool f8) { return f8 ? d / 128 : d / 64; }
 
 bool refine_mma_supported(int d, int max_mq, bool f8) {
-    if (max_mq < 1 || max_mq > (f8 ? 32 : kMaxQ)) return false;
+    if (max_mq < 1 || max_mq > kMaxQ) return false;
     if (f8 ? (d % 128 != 0 || d < 128) : (d % kKB != 0 || d < kKB)) return false;
     return pick_stages(kblocks(d, f8), mq_for(max_mq)) > 0;
 }
@@ -848,7 +853,7 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
     const Layout Lo = make_layout(kblocks(d, f8), ns, MQ);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
-    const auto kern = f8 ? k_refine_mma<32, true>
+    const auto kern = f8 ? (MQ == 32 ? k_refine_mma<32, true> : k_refine_mma<64, true>)
                          : (MQ == 32 ? k_refine_mma<32, false> : k_refine_mma<64, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;

@@ -124,12 +124,14 @@ class Mixture:
 def workload(n_sets: int, size_lo: int, size_hi: int, d: int, n_components: int,
              n_queries: int, q_lo: int, q_hi: int, m: int, fanin: int,
              seed: int = 0, device="cpu", sigma: float = 0.5, tau: float = 0.5,
-             group: int = 16, grid: bool = True, size_dist: str = "uniform"):
+             group: int = 16, grid: bool = True, size_dist: str = "uniform",
+             q_dist: str = "uniform"):
     """A database, its query sets and the FlyHash projection, all seeded.
 
     seed -> database, seed + 1 -> queries, seed + 2 -> projection.  Database set
     sizes are uniform or (size_dist="zipf") truncated Zipf with exponent 1 on
-    [size_lo, size_hi]; query set sizes are uniform on [q_lo, q_hi].
+    [size_lo, size_hi]; query set sizes are uniform on [q_lo, q_hi] or (q_dist="zipf")
+    truncated Zipf on it.
     Returns a dict of vectors / offsets (torch on ``device``; offsets also
     as numpy) and the projection (numpy uint16).
     """
@@ -140,7 +142,12 @@ def workload(n_sets: int, size_lo: int, size_hi: int, d: int, n_components: int,
         sizes = set_sizes(n_sets, size_lo, size_hi, seed * 1000 + 11)
     else:
         raise ValueError("size_dist must be 'uniform' or 'zipf'")
-    qsizes = set_sizes(n_queries, q_lo, q_hi, seed * 1000 + 12)
+    if q_dist == "zipf":
+        qsizes = zipf_sizes(n_queries, q_lo, q_hi, seed * 1000 + 12)
+    elif q_dist == "uniform":
+        qsizes = set_sizes(n_queries, q_lo, q_hi, seed * 1000 + 12)
+    else:
+        raise ValueError("q_dist must be 'uniform' or 'zipf'")
     vec = mix.draw_sets(sizes, seed * 1000 + 21, sigma=sigma, grid=grid)
     qvec = mix.draw_sets(qsizes, seed * 1000 + 22, sigma=sigma, grid=grid)
     proj = projection(d, m, fanin, seed + 2)
@@ -159,3 +166,10 @@ LARGE = dict(n_sets=1_000_000, size_lo=8, size_hi=32, d=384, n_components=4096,
 SERVING = dict(n_sets=200_000, size_lo=1, size_hi=128, d=768, n_components=4096,
                n_queries=4096, q_lo=1, q_hi=64, m=4096, fanin=8, L=64, C=2000, k=10,
                size_dist="zipf")
+# The FP8 refine's load at high dimension: 500k sets of Zipf sizes 4-64, d = 1024, a
+# 16,384-component mixture, 2000 query sets, C = 4000.  The load names neither m, F, L,
+# A, M nor the query sets' sizes: m, F, L come from LARGE and the query sets follow the
+# database's size law.
+FP8_HIGH_D = dict(n_sets=500_000, size_lo=4, size_hi=64, d=1024, n_components=16384,
+                  n_queries=2000, q_lo=4, q_hi=64, m=4096, fanin=8, L=64, C=4000, k=10,
+                  size_dist="zipf", q_dist="zipf")

@@ -94,10 +94,27 @@ def test_fp8_exact_band_returns_the_oracle_top_k(bv, orc, case):
         np.testing.assert_allclose(dist[q].cpu().numpy()[fin], r["dist"][fin], rtol=3e-6)
 
 
-def test_fp8_falls_back_for_wide_query_sets(bv, orc, case):
-    # query sets of more than 32 vectors take the BF16 copy: exact again
+def test_fp8_64_wide_with_the_exact_band(bv, orc, case):
+    # query sets of 33-64 vectors take the 64-wide FP8 instance; with the rigorous band
+    # the ids are the oracle's
     w, ix, oix, _ = case
-    sizes = datagen.set_sizes(5, 33, 48, 71)
+    sizes = datagen.set_sizes(6, 33, 64, 73)
+    qv = datagen.Mixture(128, 32, 61).draw_sets(sizes, 74)
+    qo = datagen.offsets_from_sizes(sizes)
+    ids, dist = bv.bvss_query(ix, qv.cuda(), qo, k=8, C=200, fp8=True, fp8_exact=True)
+    ids8, _ = bv.bvss_query(ix, qv.cuda(), qo, k=8, C=200, fp8=True)
+    for q in range(6):
+        r = orc.query(oix, qv[qo[q]:qo[q + 1]].numpy(), k=8, C=200, A=3, M=1)
+        assert ids[q].tolist() == r["ids"].tolist()
+        np.testing.assert_allclose(dist[q].cpu().numpy(), r["dist"], rtol=3e-6)
+        # the default band: approximate, but every returned set is among the candidates
+        assert set(ids8[q].tolist()) <= set(r["cand"].tolist())
+
+
+def test_fp8_falls_back_for_wide_query_sets(bv, orc, case):
+    # query sets of more than 64 vectors take the FP32 refine: exact again
+    w, ix, oix, _ = case
+    sizes = datagen.set_sizes(5, 65, 80, 71)
     qv = datagen.Mixture(128, 32, 61).draw_sets(sizes, 72)
     qo = datagen.offsets_from_sizes(sizes)
     ids, dist = bv.bvss_query(ix, qv.cuda(), qo, k=5, C=100, fp8=True)
