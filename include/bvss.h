@@ -84,9 +84,9 @@ typedef struct bvss_params {
 /* Search parameters of Alg. 6 (Theta's A, M, c = T) and Def. 5's k. */
 /* bvss_search.flags */
 #define BVSS_SEARCH_FAST 1  /* refine on the tensor cores: squared distances in the GEMM form
-                               from BF16 vectors with FP32 accumulation (tcgen05), the pair that
-                               attains each Hausdorff value re-scored in FP32 (the trace's
-                               cand_dist outside the boundary band).  The top k are exact as in
+                               from BF16 vectors with FP32 accumulation (tcgen05); outside the
+                               boundary band the trace's cand_dist is that value (the square
+                               root of the GEMM-form Hausdorff value of the BF16 copies).  The top k are exact as in
                                bvss_query; the band is wider by the copy's rounding error (zero
                                for inputs on the 2^-8 grid).  Needs an index built with
                                BVSS_BUILD_BF16; batches with a query set of more than 64 vectors
@@ -106,9 +106,8 @@ typedef struct bvss_params {
 #define BVSS_SEARCH_FP8 8   /* refine on the tensor cores from the FP8 copy (BVSS_BUILD_FP8): the
                                query vectors are scaled and rounded to E4M3 the same way, the
                                squared distances are |q|^2 + |v|^2 - 2 s_q s_v (q8 . v8) of the
-                               scaled values, and each candidate's distance is the FP32 distance
-                               of the pair that attains its Hausdorff value there (the trace's
-                               cand_dist outside the boundary band).  FP8 rounding (up to 2^-4
+                               scaled values (the trace's cand_dist outside the boundary band
+                               is the resulting Hausdorff value).  FP8 rounding (up to 2^-4
                                relative per value) moves a distance by up to e_q + e_v, the
                                norms of the two vectors' rounding errors; a band that wide holds
                                nearly every candidate, so by default the band takes 3 standard
@@ -308,8 +307,8 @@ void bvss_plan_free(bvss_plan *p);
 #define BVSS_STAGE_SCAN 2     /* sketch Hamming over all sets (line 12) */
 #define BVSS_STAGE_SELECT 3   /* the C smallest (Hamming, id) (lines 10-18) */
 #define BVSS_STAGE_REFINE 4   /* Hausdorff of the candidates (lines 19-22) */
-#define BVSS_STAGE_RESCORE 5  /* FP32 distance of each candidate's critical pair
-                                 (BVSS_SEARCH_FAST only; 0 otherwise) */
+#define BVSS_STAGE_RESCORE 5  /* empty (the boundary stage, within BVSS_STAGE_TOPK, reads the
+                                 tensor-core refine's values directly); kept for the layout */
 #define BVSS_STAGE_TOPK 6     /* boundary re-score and the k smallest (distance, id)
                                  (line 23; see bvss_query) */
 #define BVSS_N_STAGES 7

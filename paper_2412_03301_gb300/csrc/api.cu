@@ -463,11 +463,8 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
                               w.cand, w.thr, C, w.cand_dist, st));
     ++n;
     if (ev) BVSS_CU(cudaEventRecord(ev[5], st));
-    if (mma) {
-        BVSS_CU(launch_rescore(qv, b.qoff, nb, ix->vec, ix->n_vec, d, w.thr, C, w.pair,
-                               w.cand_dist, st));
-        ++n;
-    }
+    // (the re-score stage is empty: the boundary stage reads the tensor-core refine's
+    // values from its pair records)
     if (ev) BVSS_CU(cudaEventRecord(ev[6], st));
     // line 23: the k smallest (distance, id), decided exactly around the k-th
     BVSS_CU(launch_band_topk(qv, b.qoff, nb, b.max_mq, d, form, ix->rstat, ix->vec, ix->set_off,

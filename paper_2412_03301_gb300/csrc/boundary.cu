@@ -592,6 +592,8 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
                 lo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(h2, D), 0.0f)), e), 0.0f);
                 hi = __fadd_ru(__fsqrt_ru(__fadd_ru(h2, D)), e);
             }
+            if (form != 0) cd[j] = sqrtf(__uint_as_float(
+                                       (uint32_t)((unsigned long long)pq[j].x >> 32)));
             hik[j] = __float_as_uint(hi);   // non-negative: bit order is value order
             lov[j] = lo;
         }

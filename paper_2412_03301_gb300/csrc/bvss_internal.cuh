@@ -212,8 +212,8 @@ cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, f
 // FP8 E4M3 copy with one scale per vector and the squared norms of the scaled values
 cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *scale,
                           float *norm, cudaStream_t st);
-// records each candidate's critical (query vector, row) pair; launch_rescore then
-// writes its FP32 distance as the candidate's distance.  vecb: the BF16 copy, or with
+// records each candidate's attaining (query vector, row) pair and, in the high word of
+// pair.x, its squared Hausdorff value over the stored copies (read by the boundary stage).  vecb: the BF16 copy, or with
 // f8 the FP8 copy and its per-vector scales vscale; vnorm: squared norms of the stored
 // values.  cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy
 // ring (4 up to the most that fit; otherwise, and for 0, the most that fit).
@@ -226,9 +226,6 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
 int refine_mma_stages(int d, int max_mq, bool f8 = false);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
 int refine_mma_ring(int d, int max_mq, int stages, bool f8 = false);
-cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
-                           int64_t n_vec, int d, const int32_t *thr, int C,
-                           const longlong2 *pair, float *cand_dist, cudaStream_t st);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------

@@ -37,9 +37,9 @@
 //              Hausdorff value, which is recorded.  The one candidate that runs
 //              past the end of a tile carries its state in shared memory to the
 //              next tile (double-buffered), so no atomics are needed.
-// k_rescore then computes each pair's distance directly in FP32 from the
-// original vectors (one warp per candidate) and writes the square root as the
-// candidate's distance.
+// The record holds the pair (query vector, global row of the database vector) and, in
+// the high word of its first field, the candidate's squared Hausdorff value over the
+// stored copies; the boundary stage (boundary.cu) takes it from there.
 // Every wait gives up after 2 s (or when another role gave up), sets the error
 // word and lets all roles reach tear-down, where TMEM is released.
 #include <cuda_bf16.h>
@@ -681,52 +681,6 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// distance of each candidate's recorded pair, directly in FP32; one warp per
-// candidate.  The pair holds the database vector's global row, so the row's loads
-// follow a single dependent load; all of them are issued before the first use.
-__global__ void __launch_bounds__(256)
-k_rescore(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
-          const float *__restrict__ vec, int64_t n_vec, const int32_t *__restrict__ thr,
-          const longlong2 *__restrict__ pair, int C, int d, float *__restrict__ cand_dist) {
-    const int q = blockIdx.y;
-    const int n_sel = thr[q * 4 + 3];
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (c >= n_sel) return;
-    const longlong2 pr = pair[(int64_t)q * C + c];
-    // keep the pair inside the arrays whatever they hold
-    const int64_t a0 = qoff[q], mq = qoff[q + 1] - a0;
-    const int64_t qa = a0 + min(max((long long)(int32_t)(uint32_t)pr.x, 0ll), (long long)mq - 1);
-    const int64_t row = min(max(pr.y, 0ll), (long long)n_vec - 1);
-    const float4 *x4 = reinterpret_cast<const float4 *>(qvec + qa * d);
-    const float4 *y4 = reinterpret_cast<const float4 *>(vec + row * d);
-    const int n4 = d / 4;
-    float s = 0.0f;
-    for (int k0 = 0; k0 < n4; k0 += 32 * 4) {
-        float4 x[4], y[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + 32 * i + lane;
-            x[i] = k < n4 ? x4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-            y[i] = k < n4 ? y4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float u = x[i].x - y[i].x;
-            s = fmaf(u, u, s);
-            u = x[i].y - y[i].y;
-            s = fmaf(u, u, s);
-            u = x[i].z - y[i].z;
-            s = fmaf(u, u, s);
-            u = x[i].w - y[i].w;
-            s = fmaf(u, u, s);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) cand_dist[(int64_t)q * C + c] = sqrtf(s);
-}
-
 // FP32 -> BF16 copy of the vectors and the squared norms of the BF16 values
 __global__ void k_to_bf16(const float *__restrict__ x, int64_t n, int d,
                           __nv_bfloat16 *__restrict__ y, float *__restrict__ norm) {
@@ -860,15 +814,6 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
     kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(
         qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
         thr, C, cpc, pair, err);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rescore(const float *qvec, const int64_t *qoff, int n_q, const float *vec,
-                           int64_t n_vec, int d, const int32_t *thr, int C,
-                           const longlong2 *pair, float *cand_dist, cudaStream_t st) {
-    if (n_q <= 0) return cudaSuccess;
-    k_rescore<<<dim3((C + 7) / 8, n_q), 256, 0, st>>>(qvec, qoff, vec, n_vec, thr, pair, C, d,
-                                                       cand_dist);
     return cudaGetLastError();
 }
 
