@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--serving-queries", type=int, default=4096,
                     help="query sets per pass of the batched serving line (200k Zipf-sized "
                          "sets, d=768, one graph launch per pass); 0 skips it")
+    ap.add_argument("--serving-recall-queries", type=int, default=500)
     ap.add_argument("--cpu-sample-sets", type=int, default=10000)
     ap.add_argument("--cpu-sample-queries", type=int, default=32,
                     help="query sets of the all-core oracle sample (a quarter of them, at "
@@ -546,12 +547,12 @@ def serving_line(args, dev, stream):
     torch.cuda.synchronize(dev)
     ms_query = e0.elapsed_time(e1) / max(2, args.steps // 4)
     rec = None
-    if args.recall_queries > 0:
+    if args.serving_recall_queries > 0:
         vec = w["vectors"]
         vnorm = (vec * vec).sum(1)
         set_of_row = torch.repeat_interleave(torch.arange(c["n_sets"], device=dev),
                                              torch.from_numpy(np.diff(off)).to(dev))
-        qids = list(range(min(50, nq)))
+        qids = list(range(min(args.serving_recall_queries, nq)))
         gt_ids, gt_d2 = exact_topk(vec, vnorm, set_of_row, c["n_sets"], qv, qo, qids, c["k"])
         got = ids_plan[qids].cpu().numpy()
         got_d2 = true_d2_of(vec, vnorm, qv, qo, off, qids, got)
@@ -567,7 +568,9 @@ def serving_line(args, dev, stream):
                           c["n_components"], c["m"], c["fanin"], c["L"], nq, c["q_lo"],
                           c["q_hi"], c["A"], c["M"], c["C"], c["k"]),
            "form": "one CUDA graph launch per pass (bvss_plan), tensor-core scan and BF16 "
-                   "tensor-core refine (64-wide), FP32 re-score of the critical pair",
+                   "tensor-core refine (query sets of <= 32 vectors on the 32-wide instance, "
+                   "the wider ones on the 64-wide one, unless the tuner drops the split), "
+                   "boundary re-score for the exact top-k",
            "tuned": plan.info(), "untuned": dict(knobs_default, ms_per_step=ms_default),
            "tune_s": tune_s,
            "bvss_query_ms_per_step": ms_query, "same_ids_as_bvss_query": bool(torch.equal(ids_plan, ids_q)),

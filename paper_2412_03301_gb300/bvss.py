@@ -283,15 +283,17 @@ class Plan:
         return ms.value
 
     def info(self):
-        kn = (_c_i32 * 4)()
+        kn = (_c_i32 * 6)()
         nl = _c_i64()
         _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
         return dict(scan={1: "tensor", 2: "popcount", 0: "alg2"}[kn[0]], cand_cta=kn[1],
-                    stages=kn[2], mq=kn[3], launches=nl.value)
+                    stages=kn[2], mq=kn[3], width_split=kn[4], batch=kn[5],
+                    launches=nl.value)
 
-    def set_knobs(self, scan=0, cand_cta=0, stages=0):
-        """Pin the tuner's choices (0 = default); scan 1 = tensor-core, 2 = popcount."""
-        kn = (_c_i32 * 3)(scan, cand_cta, stages)
+    def set_knobs(self, scan=0, cand_cta=0, stages=0, bucket=0, batch=0):
+        """Pin the tuner's choices (0 = default); scan 1 = tensor-core, 2 = popcount;
+        bucket 2 = no width split; batch = query sets per internal batch."""
+        kn = (_c_i32 * 5)(scan, cand_cta, stages, bucket, batch)
         _check(load().bvss_plan_set_knobs(self.handle, kn))
 
     def close(self):

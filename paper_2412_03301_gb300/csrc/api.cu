@@ -72,6 +72,14 @@ int64_t batch_cap(const bvss_index *ix) {
     return qb;
 }
 
+// a plan's largest internal batch: up to 4096 query sets, score matrix within 4 GiB
+int64_t plan_batch_cap(const bvss_index *ix) {
+    int64_t qb = ((int64_t)1 << 31) / h_stride(ix);
+    if (qb > 4096) qb = 4096;
+    if (qb < 1) qb = 1;
+    return qb;
+}
+
 void free_workspace(Workspace &w) {
     dfree(w.qvec);
     dfree(w.qoff);
@@ -90,6 +98,7 @@ void free_workspace(Workspace &w) {
     dfree(w.cand);
     dfree(w.cand_dist);
     dfree(w.pair);
+    dfree(w.wlist);
     dfree(w.enc_x);
     dfree(w.enc_act);
     dfree(w.out_ids);
@@ -219,6 +228,7 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand, (size_t)nq * C));
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
+    BVSS_CU(dalloc(&w.wlist, (size_t)2 * nq + 2));
     if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
     if (ix->wproj16) {
         BVSS_CU(dalloc(&w.enc_x, (size_t)kEncChunk * d));
@@ -319,6 +329,10 @@ struct Knobs {
     int scan = 0;       // 1: tensor-core sketch scan, 2: popcount scan, 0: by the search flags
     int cand_cta = 0;   // tensor-core refine: candidates per CTA (0: 512)
     int stages = 0;     // tensor-core refine: depth of the copy ring (0: the most that fit)
+    int bucket = 0;     // tensor-core refine of a batch holding query sets over 32 vectors:
+                        // 0 the sets of at most 32 on the 32-wide instance and the others on
+                        // the 64-wide one, 2 all on the 64-wide one
+    int batch = 0;      // query plans: query sets per internal batch (0: the default cap)
 };
 
 // Codes (Def. 7) of n vectors x (device FP32) with the index's projection: the sparse
@@ -449,10 +463,20 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     // the FP8 copy for query sets it takes, else the BF16 one, else FP32
     const int form = refine_form(ix, s->flags, b.max_mq);
     const bool mma = form > 0;
-    if (mma)
-        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq,
-                                  form == 2 ? (const void *)ix->vec8 : (const void *)ix->vec16,
-                                  ix->vscale8, form == 2 ? ix->vnorm8 : ix->vnorm16, form == 2,
+    const void *vecb = form == 2 ? (const void *)ix->vec8 : (const void *)ix->vec16;
+    const float *vnb = form == 2 ? ix->vnorm8 : ix->vnorm16;
+    if (mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, form == 2)) {
+        // the batch's query sets by width: the narrow ones on the 32-wide instance
+        BVSS_CU(launch_width_lists(b.qoff, nb, w.wlist, w.wlist + 2 * nb, st));
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, 32, vecb, ix->vscale8, vnb, form == 2,
+                                  ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
+                                  kn.cand_cta, kn.stages, w.wlist, w.wlist + 2 * nb));
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, form == 2,
+                                  ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
+                                  kn.cand_cta, kn.stages, w.wlist + nb, w.wlist + 2 * nb + 1));
+        n += 2;
+    } else if (mma)
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, form == 2,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages));
     else if (refine_tma_supported(d, b.max_mq))
@@ -656,7 +680,9 @@ int plan_enqueue(bvss_plan *p, cudaStream_t st, int64_t *launches) {
     const int rc0 = encode_vectors(ix, p->qv, p->max_v, p->w.qpos, nullptr, p->w.enc_x,
                                    p->w.enc_act, st, p->qoff + p->n_q, launches);
     if (rc0) return rc0;
-    const int64_t QB = p->w.cap_q;
+    // the internal batch: the tuner's choice, else the default cap, within the workspace
+    int64_t QB = p->kn.batch > 0 ? p->kn.batch : batch_cap(ix);
+    if (QB > p->w.cap_q) QB = p->w.cap_q;
     for (int64_t b0 = 0; b0 < p->n_q; b0 += QB) {
         Batch b;
         b.qv = p->qv;
@@ -1109,7 +1135,7 @@ int bvss_plan_create(bvss_index *ix, const bvss_search *s, int64_t n_queries,
     p->qoff_in = q_offsets;
     p->ids = out_ids;
     p->dist = out_dist;
-    const int64_t QB = batch_cap(ix);
+    const int64_t QB = plan_batch_cap(ix);
     rc = alloc_workspace(ix, p->w, n_queries < QB ? n_queries : QB, max_vectors, s->C, s->A,
                          s->k, false, false);
     if (!rc && dalloc(&p->qoff, n_queries + 1) != cudaSuccess)
@@ -1178,6 +1204,16 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
         for (int r = ns; r >= 4 && nr < 3; r -= 2) rings[nr++] = r;
         rc = sweep(&Knobs::stages, rings, nr);
     }
+    if (!rc && mma && p->max_qset > 32) {
+        const int buckets[] = {0, 2};
+        rc = sweep(&Knobs::bucket, buckets, 2);
+    }
+    if (!rc && p->w.cap_q > batch_cap(p->ix)) {
+        int bs[3], nb = 0;
+        for (int64_t b = batch_cap(p->ix); b <= p->w.cap_q && nb < 3; b *= 2) bs[nb++] = (int)b;
+        if (nb < 3 && bs[nb - 1] < p->w.cap_q) bs[nb++] = (int)p->w.cap_q;
+        rc = sweep(&Knobs::batch, bs, nb);
+    }
     p->kn = best;
     const int rc2 = plan_capture(p);
     if (rc) return rc;
@@ -1198,6 +1234,9 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
         knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, form == 2) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
+        knobs[4] = mma && p->max_qset > 32 && p->kn.bucket != 2 ? 1 : 0;
+        int64_t qb = p->kn.batch > 0 ? p->kn.batch : batch_cap(p->ix);
+        knobs[5] = (int32_t)(qb < p->w.cap_q ? qb : p->w.cap_q);
     }
     if (launches) *launches = p->launches;
     return BVSS_OK;
@@ -1210,10 +1249,15 @@ int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs) {
     if (knobs[1] < 0 || knobs[1] > 512)
         return fail(BVSS_EINVAL, "candidates per CTA = %d: need 0..512", knobs[1]);
     if (knobs[2] < 0) return fail(BVSS_EINVAL, "stages = %d: need >= 0", knobs[2]);
+    if (knobs[3] != 0 && knobs[3] != 2)
+        return fail(BVSS_EINVAL, "bucket = %d: need 0 or 2", knobs[3]);
+    if (knobs[4] < 0) return fail(BVSS_EINVAL, "batch = %d: need >= 0", knobs[4]);
     const Knobs old = p->kn;
     p->kn.scan = knobs[0];
     p->kn.cand_cta = knobs[1];
     p->kn.stages = knobs[2];
+    p->kn.bucket = knobs[3];
+    p->kn.batch = knobs[4];
     const int rc = plan_capture(p);
     if (rc) p->kn = old;
     return rc;

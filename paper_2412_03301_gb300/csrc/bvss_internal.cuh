@@ -48,6 +48,7 @@ struct Workspace {
     int32_t *cand = nullptr;      // candidate ids                       cap_q x cap_C
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
+    int32_t *wlist = nullptr;     // query sets by width (<= 32, wider), then their two counts
     __nv_bfloat16 *enc_x = nullptr;  // dense projection: a block of query vectors in BF16
     float *enc_act = nullptr;        //   and their activations (kEncChunk x d, x m)
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
@@ -221,7 +222,14 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               const void *vecb, const float *vscale, const float *vnorm,
                               bool f8, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
-                              int cand_cta = 0, int stages = 0);
+                              int cand_cta = 0, int stages = 0, const int32_t *qlist = nullptr,
+                              const int32_t *qcount = nullptr);
+// with qlist / qcount (device): only query sets qlist[0 .. *qcount) (the grid still spans
+// n_q rows; max_mq then bounds the listed sets only)
+// lists (2 n_q ints): the batch's query sets of at most 32 vectors, then the wider ones;
+// counts (2 ints) their numbers
+cudaError_t launch_width_lists(const int64_t *qoff, int n_q, int32_t *lists, int32_t *counts,
+                               cudaStream_t st);
 // stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
 int refine_mma_stages(int d, int max_mq, bool f8 = false);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
@@ -233,7 +241,8 @@ cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // index's rstat; pair: the MMA forms' records (value in the high word of .x); max_mq: the
 // batch's largest query set; exact_band: the FP8 form's band from its rigorous bound
 // (else from its 3-sigma tolerance).  Band members' cand_dist become their exact values;
-// cand_dist[q][n_sel..C) is padded with +inf; results as launch_topk.
+// cand_dist[q][n_sel..C) is padded with +inf; out_ids / out_dist (n_q x k) = the k
+// smallest (distance, id) in that order, -1 / +inf past the candidate count.
 cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, int max_mq, int d,
                              int form, const float *stats, const float *vec,
                              const int64_t *set_off, const int32_t *cand, const int32_t *thr,
@@ -245,10 +254,6 @@ constexpr int kBandKernels = 1;
 cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,
                                const uint8_t *x8, const float *sc8, float *stats,
                                cudaStream_t st);
-// also pads cand_dist[q][n_sel..C) with +inf
-cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *thr,
-                        int n_q, int C, int k, int64_t *out_ids, float *out_dist,
-                        cudaStream_t st);
 
 // ---- api.cu -------------------------------------------------------------------
 // Records a message for bvss_last_error() on this thread and returns code.

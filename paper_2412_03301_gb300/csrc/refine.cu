@@ -186,52 +186,6 @@ k_refine(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     }
 }
 
-__device__ __forceinline__ void cswap(unsigned long long &a, unsigned long long &b, bool up) {
-    if ((a > b) == up) {
-        const unsigned long long t = a;
-        a = b;
-        b = t;
-    }
-}
-
-__global__ void __launch_bounds__(256)
-k_topk(const int32_t *__restrict__ cand, float *__restrict__ cand_dist,
-       const int32_t *__restrict__ thr, int C, int k, int NP, int64_t *__restrict__ out_ids,
-       float *__restrict__ out_dist) {
-    extern __shared__ unsigned long long keys[];   // NP
-    const int q = blockIdx.x, tid = threadIdx.x;
-    const int n = thr[q * 4 + 3];
-    for (int j = tid; j < NP; j += 256) {
-        keys[j] = j < n ? (((unsigned long long)__float_as_uint(cand_dist[(int64_t)q * C + j]) << 32) |
-                           (uint32_t)cand[(int64_t)q * C + j])
-                        : ~0ull;
-    }
-    __syncthreads();
-    // bitonic sort, ascending by (distance bits, id)
-    for (int size = 2; size <= NP; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < NP / 2; t += 256) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                cswap(keys[lo], keys[hi], up);
-            }
-            __syncthreads();
-        }
-    }
-    const float INF = __int_as_float(0x7f800000);
-    for (int j = tid; j < k; j += 256) {
-        if (j < n) {
-            out_ids[(int64_t)q * k + j] = (int64_t)(uint32_t)(keys[j] & 0xffffffffull);
-            out_dist[(int64_t)q * k + j] = __uint_as_float((uint32_t)(keys[j] >> 32));
-        } else {
-            out_ids[(int64_t)q * k + j] = -1;
-            out_dist[(int64_t)q * k + j] = INF;
-        }
-    }
-    for (int j = n + tid; j < C; j += 256) cand_dist[(int64_t)q * C + j] = INF;
-}
-
 }  // namespace
 
 cudaError_t launch_refine(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
@@ -251,20 +205,6 @@ cudaError_t launch_refine(const float *qvec, const int64_t *qoff, int n_q, int m
     if (gx < 1) gx = 1;
     k_refine<<<dim3(gx, n_q), kRefThreads, smem, st>>>(qvec, qoff, vec, vnorm, set_off, d, staged,
                                                         cand, thr, C, cand_dist);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_topk(const int32_t *cand, float *cand_dist, const int32_t *thr, int n_q, int C,
-                        int k, int64_t *out_ids, float *out_dist, cudaStream_t st) {
-    if (n_q <= 0) return cudaSuccess;
-    int NP = 1;
-    while (NP < C) NP <<= 1;
-    if (NP < 2) NP = 2;
-    const size_t smem = sizeof(unsigned long long) * (size_t)NP;
-    cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    k_topk<<<n_q, 256, smem, st>>>(cand, cand_dist, thr, C, k, NP, out_ids, out_dist);
     return cudaGetLastError();
 }
 

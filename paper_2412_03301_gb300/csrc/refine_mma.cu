@@ -45,6 +45,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "block_util.cuh"
 #include "bvss_internal.cuh"
 #include "ptx_util.cuh"
 
@@ -182,9 +183,12 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const float *__restrict__ vnorm,
              const int64_t *__restrict__ set_off, int d, int ns,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int cpc,
-             longlong2 *__restrict__ pair, int *__restrict__ err) {
+             longlong2 *__restrict__ pair, int *__restrict__ err,
+             const int32_t *__restrict__ qlist, const int32_t *__restrict__ qcount) {
     extern __shared__ unsigned char smem_raw[];
-    const int q = blockIdx.y;
+    // with a list, CTA row y takes query set qlist[y] (rows past *qcount have none)
+    if (qcount && (int)blockIdx.y >= *qcount) return;   // uniform over the CTA
+    const int q = qlist ? qlist[blockIdx.y] : (int)blockIdx.y;
     const int n_sel = thr[q * 4 + 3];
     const int c0 = blockIdx.x * cpc;               // cpc <= kCandCTA candidates per CTA
     if (c0 >= n_sel) return;                       // uniform over the CTA
@@ -798,10 +802,12 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               const void *vecb, const float *vscale, const float *vnorm,
                               bool f8, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
-                              int cand_cta, int stages) {
+                              int cand_cta, int stages, const int32_t *qlist,
+                              const int32_t *qcount) {
     if (n_q <= 0) return cudaSuccess;
     if (!refine_mma_supported(d, max_mq, f8)) return cudaErrorInvalidValue;
     if (f8 && !vscale) return cudaErrorInvalidValue;
+    if ((qlist == nullptr) != (qcount == nullptr)) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
     const int ns = refine_mma_ring(d, max_mq, stages, f8);
     const Layout Lo = make_layout(kblocks(d, f8), ns, MQ);
@@ -813,7 +819,43 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(
         qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
-        thr, C, cpc, pair, err);
+        thr, C, cpc, pair, err, qlist, qcount);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// The query sets of a batch split by width: lists[0..) those of at most 32 vectors,
+// lists[n_q..) the wider ones, both in order; counts[0], counts[1] their numbers.
+__global__ void __launch_bounds__(1024)
+k_width_lists(const int64_t *__restrict__ qoff, int n_q, int32_t *__restrict__ lists,
+              int32_t *__restrict__ counts) {
+    __shared__ int scan_sh[1024 / 32 + 1];
+    int base_n = 0, base_w = 0;
+    for (int q0 = 0; q0 < n_q; q0 += 1024) {
+        const int q = q0 + threadIdx.x;
+        const bool valid = q < n_q;
+        const bool wide = valid && qoff[q + 1] - qoff[q] > 32;
+        int tn, tw;
+        const int pn = block_excl_scan<1024>(valid && !wide ? 1 : 0, scan_sh, &tn);
+        const int pw = block_excl_scan<1024>(wide ? 1 : 0, scan_sh, &tw);
+        if (valid && !wide) lists[base_n + pn] = q;
+        if (wide) lists[n_q + base_w + pw] = q;
+        base_n += tn;
+        base_w += tw;
+    }
+    if (threadIdx.x == 0) {
+        counts[0] = base_n;
+        counts[1] = base_w;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_width_lists(const int64_t *qoff, int n_q, int32_t *lists, int32_t *counts,
+                               cudaStream_t st) {
+    if (n_q <= 0) return cudaSuccess;
+    k_width_lists<<<1, 1024, 0, st>>>(qoff, n_q, lists, counts);
     return cudaGetLastError();
 }
 

@@ -98,10 +98,44 @@ def test_tuned_plan_gives_the_same_results(bv, orc, serving):
     kn = plan.info()
     assert kn["scan"] in ("tensor", "popcount") and kn["cand_cta"] in (128, 256, 512)
     assert 4 <= kn["stages"] <= 10 and kn["launches"] >= 8
+    assert kn["width_split"] in (0, 1) and kn["batch"] >= 24
     ids1, dist1 = plan.launch()
     bv.bvss_sync(ix)
     assert torch.equal(ids0, ids1) and torch.equal(dist0, dist1)
     _check_oracle(orc, orc_ix, qv, qo, ids1, dist1, 10, 300, [0, 7, 23])
+    plan.close()
+
+
+def test_width_split_and_batch_knobs_give_the_same_results(bv, orc, serving):
+    # query sets of 1-64 vectors: by default the ones of at most 32 run on the 32-wide
+    # refine and the rest on the 64-wide one (two launches over device lists); without the
+    # split every set runs 64 wide.  A smaller internal batch splits the pass in several.
+    w, ix, orc_ix = serving
+    nq = 40
+    qv, qo = _queries(nq, 1, 64, 21)
+    assert (np.diff(qo) <= 32).any() and (np.diff(qo) > 32).any()
+    plan = bv.Plan(ix, nq, int(qo[-1]), 64, k=10, C=300, fast=True)
+    plan.set_queries(qv.cuda(), qo)
+    kn = plan.info()
+    assert kn["width_split"] == 1 and kn["mq"] == 64
+    ids0, dist0 = [t.clone() for t in plan.launch()]
+    bv.bvss_sync(ix)
+    _check_oracle(orc, orc_ix, qv, qo, ids0, dist0, 10, 300, range(nq))
+    n_split = kn["launches"]
+    for bucket, batch in ((2, 0), (0, 7), (2, 13), (0, 1)):
+        plan.set_knobs(bucket=bucket, batch=batch)
+        kn = plan.info()
+        assert kn["width_split"] == (0 if bucket == 2 else 1)
+        assert kn["batch"] == (batch if batch else nq)
+        ids1, dist1 = plan.launch()
+        bv.bvss_sync(ix)
+        assert torch.equal(ids0, ids1) and torch.equal(dist0, dist1), (bucket, batch)
+        if batch == 0:
+            assert kn["launches"] == n_split - 2
+    with pytest.raises(bv.BvssError):
+        plan.set_knobs(bucket=1)
+    with pytest.raises(bv.BvssError):
+        plan.set_knobs(batch=-1)
     plan.close()
 
 
