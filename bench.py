@@ -337,7 +337,8 @@ def offgrid_line(args, dev, stream):
     out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
     forms, res = {}, {}
     steps = max(1, min(args.steps, 5))
-    for name, f in (("plain", {}), ("fast", {"fast": True}), ("fp8", {"fp8": True})):
+    for name, f in (("plain", {}), ("tf32", {"tf32": True}), ("fast", {"fast": True}),
+                    ("fp8", {"fp8": True})):
         for _ in range(args.warmup):
             bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream,
                             **kw, **f)
@@ -360,7 +361,8 @@ def offgrid_line(args, dev, stream):
                        "stages_ms_per_step": {k_: v / steps for k_, v in st.items()},
                        "gpu_launches_per_step": nl // steps}
     ids_p = res["plain"][0]
-    same = {name: int((res[name][0] == ids_p).all(axis=1).sum()) for name in ("fast", "fp8")}
+    same = {name: int((res[name][0] == ids_p).all(axis=1).sum())
+            for name in ("tf32", "fast", "fp8")}
     # recall and distance errors against the FP64 oracle on the first query sets
     nr = min(args.offgrid_recall_queries, nq)
     vec = w["vectors"]
@@ -379,7 +381,7 @@ def offgrid_line(args, dev, stream):
             cache[i] = vec[int(off[i]):int(off[i + 1])].cpu().numpy()
         return cache[i]
 
-    for name in ("plain", "fast", "fp8"):
+    for name in ("plain", "tf32", "fast", "fp8"):
         ids, dist = res[name][0][:nr], res[name][1][:nr]
         r, d64 = fp64_recall(ids, gt_ids, qvec_h, qo, vec_of, c["k"])
         ok = np.isfinite(d64)
@@ -840,6 +842,10 @@ def run_ours(args, rank, world, local_rank):
     kw = dict(k=c["k"], C=c["C"], A=c["A"], M=c["M"])
 
     kw_fast = dict(kw, fast=fast_ok)
+    # the plain form: FP32 vectors, exact FP32 results; its refine on the tensor cores
+    # reading the FP32 rows as TF32 where the kernel takes the shape (the boundary stage
+    # re-scores the band in FP32), the CUDA-core FP32 refine timed beside it
+    kw_plain = dict(kw, tf32=c["d"] % 32 == 0)
     # one traced pass (outside the timed region): |F1| per query for the roofline
     tr = bvss.bvss_query_trace(ix, qv, qoff, **kw)
     torch.cuda.synchronize(dev)
@@ -949,7 +955,8 @@ def run_ours(args, rank, world, local_rank):
         t_ms = shard.max_over_ranks(t_ms, device=dev)
         return t_ms, st_ms, nb, nl, clk
 
-    ms_plain, stage_plain, _, _, _ = timed(kw, False)
+    ms_plain, stage_plain, _, _, _ = timed(kw_plain, False)
+    ms_simt, stage_simt, _, _, _ = timed(kw, False)
     ms, stage_ms, nbatch, launches, clk = timed(kw_fast, True)
     value = world * nq / (ms / 1e3)
     # the FP8 refine on the same index (approximate: recall and distance error below)
@@ -967,7 +974,7 @@ def run_ours(args, rank, world, local_rank):
                    / measured_peaks()[0]},
                "accuracy": rec.get("fp8") if rec else None,
                "form": "FP8 E4M3 copies with per-vector scales on the tensor cores "
-                       "(tcgen05 kind::f8f6f4), FP32 re-score of the attaining pair"}
+                       "(tcgen05 kind::f8f6f4), 3-sigma boundary band re-scored in FP32"}
 
     # the plain BioVSS search (Alg. 2) on the same index: every set is scored with Haus^H over
     # codes, so it is timed on the first --alg2-queries query sets only
@@ -1074,8 +1081,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if fast_ok else "f32", "data": "synthetic",
         "config": {"workload": workload_name(c),
-                   "form": ("fast: BF16 tensor-core refine (tcgen05) with FP32 re-score of the "
-                            "critical pair; random FlyHash" if fast_ok else
+                   "form": ("fast: BF16 tensor-core refine (tcgen05), boundary band "
+                            "re-scored in FP32 for the exact top-k; random FlyHash" if fast_ok else
                             "plain: FP32 refine, random FlyHash"),
                    "query_sets_per_step_per_gpu": nq,
                    "l2": "inputs larger than L2 (sketch matrix %.0f MB, vectors %.1f GB)"
@@ -1084,7 +1091,23 @@ def run_ours(args, rank, world, local_rank):
         "recall": rec,
         "plain_form": {"value": world * nq / (ms_plain / 1e3), "ms_per_step": ms_plain,
                        "stages_ms_per_step": {k: v / args.steps for k, v in stage_plain.items()},
-                       "dtype": "f32", "same_ids_as_fast": fast_same},
+                       "dtype": "f32", "same_ids_as_fast": fast_same,
+                       "form": "FP32 vectors, random FlyHash; refine on the tensor cores "
+                               "reading the FP32 rows as TF32 (tcgen05 kind::tf32), boundary "
+                               "band re-scored in FP32: the same ids and distances as the "
+                               "CUDA-core FP32 refine" if kw_plain["tf32"] else
+                               "FP32 CUDA-core refine",
+                       "refine_roofline": {
+                           "bound": "hbm", "unit": "GB/s", "peak": measured_peaks()[0],
+                           "achieved": cand_rows * c["d"] * 4
+                           / (stage_plain["refine"] / args.steps / 1e3) / 1e9,
+                           "frac": cand_rows * c["d"] * 4
+                           / (stage_plain["refine"] / args.steps / 1e3) / 1e9
+                           / measured_peaks()[0]},
+                       "cuda_core_refine": {
+                           "value": world * nq / (ms_simt / 1e3), "ms_per_step": ms_simt,
+                           "stages_ms_per_step": {k: v / args.steps
+                                                  for k, v in stage_simt.items()}}},
         "roofline": roof,
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "cpu_baseline": cpu,

@@ -118,6 +118,18 @@ typedef struct bvss_params {
                                to 64 vectors; batches with a larger one use the FP32 refine */
 #define BVSS_SEARCH_FP8_EXACT 16  /* with BVSS_SEARCH_FP8: the band from the rigorous bound, so
                                      the top k are exact as in bvss_query */
+#define BVSS_SEARCH_TF32 32  /* refine on the tensor cores from the FP32 vectors themselves
+                                (no copy needed), which the tensor core reads as TF32, with
+                                the query vectors rounded to TF32 (to nearest): squared
+                                distances |q~|^2 + |v|^2 - 2 q~.v~ with FP32 accumulation,
+                                whose error (at most 2^-10 relative per value, zero for
+                                values TF32 holds, such as those on the 2^-8 grid) widens the
+                                boundary band; the top k and their distances are exact as in
+                                bvss_query, and outside the band the trace's cand_dist is that
+                                GEMM-form value.  d % 32 == 0; query sets of up to 64 vectors
+                                (and at d > 768 the stages must fit: batches the kernel cannot
+                                take use the CUDA-core FP32 refine).  BVSS_SEARCH_FAST and
+                                BVSS_SEARCH_FP8 take precedence */
 
 typedef struct bvss_search {
     int32_t k;      /* results per query set, 1..BVSS_MAX_K */
@@ -125,7 +137,7 @@ typedef struct bvss_search {
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
     int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2,
-                       BVSS_SEARCH_FP8, BVSS_SEARCH_FP8_EXACT */
+                       BVSS_SEARCH_FP8, BVSS_SEARCH_FP8_EXACT, BVSS_SEARCH_TF32 */
     int32_t reserved;
 } bvss_search;
 

@@ -40,6 +40,7 @@ BVSS_SEARCH_POPC_SCAN = 2
 BVSS_SEARCH_ALG2 = 4
 BVSS_SEARCH_FP8 = 8
 BVSS_SEARCH_FP8_EXACT = 16
+BVSS_SEARCH_TF32 = 32
 
 
 class bvss_trace(ctypes.Structure):
@@ -200,16 +201,16 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
     return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
 
 
-def _search_flags(fast, popc_scan, alg2=False, fp8=False, fp8_exact=False):
+def _search_flags(fast, popc_scan, alg2=False, fp8=False, fp8_exact=False, tf32=False):
     return ((BVSS_SEARCH_FAST if fast else 0) | (BVSS_SEARCH_POPC_SCAN if popc_scan else 0)
             | (BVSS_SEARCH_ALG2 if alg2 else 0) | (BVSS_SEARCH_FP8 if fp8 else 0)
-            | (BVSS_SEARCH_FP8_EXACT if fp8_exact else 0))
+            | (BVSS_SEARCH_FP8_EXACT if fp8_exact else 0) | (BVSS_SEARCH_TF32 if tf32 else 0))
 
 
 def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
                M: int = 1, fast: bool = False, popc_scan: bool = False, alg2: bool = False,
-               fp8: bool = False, fp8_exact: bool = False, out_ids=None, out_dist=None,
-               stream=None):
+               fp8: bool = False, fp8_exact: bool = False, tf32: bool = False, out_ids=None,
+               out_dist=None, stream=None):
     """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
 
     q_vectors and the outputs may live on the host or on the index's GPU."""
@@ -222,7 +223,7 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
     s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -239,7 +240,8 @@ class Plan:
 
     def __init__(self, ix: Index, n_queries: int, max_vectors: int, max_qset: int, *, k: int,
                  C: int, A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
-                 alg2: bool = False, fp8: bool = False, fp8_exact: bool = False, stream=None):
+                 alg2: bool = False, fp8: bool = False, fp8_exact: bool = False,
+                 tf32: bool = False, stream=None):
         lib = load()
         dev = ix.device
         self.ix = ix
@@ -249,7 +251,7 @@ class Plan:
         self.ids = torch.empty((n_queries, k), dtype=torch.int64, device=dev)
         self.dist = torch.empty((n_queries, k), dtype=torch.float32, device=dev)
         s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.bvss_plan_create(ix.handle, ctypes.byref(s), n_queries, max_vectors,
@@ -312,7 +314,7 @@ class Plan:
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
                      A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
                      alg2: bool = False, fp8: bool = False, fp8_exact: bool = False,
-                     stream=None):
+                     tf32: bool = False, stream=None):
     """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
 
     Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
@@ -336,7 +338,7 @@ def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
     s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
     _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                                 _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
     t["ids"] = ids

@@ -371,7 +371,7 @@ int check_search(const bvss_index *ix, const bvss_search *s) {
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
     if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2 | BVSS_SEARCH_FP8 |
-                     BVSS_SEARCH_FP8_EXACT))
+                     BVSS_SEARCH_FP8_EXACT | BVSS_SEARCH_TF32))
         return fail(BVSS_EINVAL, "unknown search flags");
     if ((s->flags & BVSS_SEARCH_FAST) && !ix->vec16)
         return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
@@ -383,9 +383,12 @@ int check_search(const bvss_index *ix, const bvss_search *s) {
 // Refine a batch runs: 2 FP8 tensor cores, 1 BF16 tensor cores, 0 FP32.
 int refine_form(const bvss_index *ix, int flags, int max_mq) {
     const int d = ix->p.d;
-    if ((flags & BVSS_SEARCH_FP8) && ix->vec8 && refine_mma_supported(d, max_mq, true)) return 2;
-    if ((flags & (BVSS_SEARCH_FAST | BVSS_SEARCH_FP8)) && ix->vec16 && refine_mma_supported(d, max_mq))
+    if ((flags & BVSS_SEARCH_FP8) && ix->vec8 && refine_mma_supported(d, max_mq, Elem::FP8))
+        return 2;
+    if ((flags & (BVSS_SEARCH_FAST | BVSS_SEARCH_FP8)) && ix->vec16 &&
+        refine_mma_supported(d, max_mq, Elem::BF16))
         return 1;
+    if ((flags & BVSS_SEARCH_TF32) && refine_mma_supported(d, max_mq, Elem::TF32)) return 3;
     return 0;
 }
 
@@ -463,20 +466,23 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     // the FP8 copy for query sets it takes, else the BF16 one, else FP32
     const int form = refine_form(ix, s->flags, b.max_mq);
     const bool mma = form > 0;
-    const void *vecb = form == 2 ? (const void *)ix->vec8 : (const void *)ix->vec16;
-    const float *vnb = form == 2 ? ix->vnorm8 : ix->vnorm16;
-    if (mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, form == 2)) {
+    const Elem el = static_cast<Elem>(mma ? form : 1);
+    const void *vecb = form == 2   ? (const void *)ix->vec8
+                       : form == 3 ? (const void *)ix->vec
+                                   : (const void *)ix->vec16;
+    const float *vnb = form == 2 ? ix->vnorm8 : (form == 3 ? ix->vnorm : ix->vnorm16);
+    if (mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, el)) {
         // the batch's query sets by width: the narrow ones on the 32-wide instance
         BVSS_CU(launch_width_lists(b.qoff, nb, w.wlist, w.wlist + 2 * nb, st));
-        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, 32, vecb, ix->vscale8, vnb, form == 2,
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, 32, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages, w.wlist, w.wlist + 2 * nb));
-        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, form == 2,
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages, w.wlist + nb, w.wlist + 2 * nb + 1));
         n += 2;
     } else if (mma)
-        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, form == 2,
+        BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages));
     else if (refine_tma_supported(d, b.max_mq))
@@ -855,7 +861,7 @@ int build_impl(const float *vectors, const int64_t *set_offsets, int64_t n_sets,
             BVSS_CU(dalloc(&ix->vnorm8, (size_t)nv));
             BVSS_CU(launch_to_fp8(ix->vec, nv, p.d, ix->vec8, ix->vscale8, ix->vnorm8, st));
         }
-        BVSS_CU(dalloc(&ix->rstat, 4));
+        BVSS_CU(dalloc(&ix->rstat, kRoundStats));
         BVSS_CU(launch_round_stats(ix->vec, nv, p.d, ix->vec16, ix->vec8, ix->vscale8, ix->rstat,
                                    st));
         {
@@ -1170,7 +1176,7 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
     const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
     const int form = refine_form(p->ix, p->s.flags, p->max_qset);
     const bool mma = form > 0;
-    const int ns = mma ? refine_mma_stages(d, p->max_qset, form == 2) : 0;
+    const int ns = mma ? refine_mma_stages(d, p->max_qset, static_cast<Elem>(form)) : 0;
     Knobs best = p->kn;
     float best_t = 0.0f;
     int rc = plan_time(p, best, reps, &best_t);
@@ -1232,7 +1238,7 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
         knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
                                           : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
-        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, form == 2) : 0;
+        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, static_cast<Elem>(form)) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
         knobs[4] = mma && p->max_qset > 32 && p->kn.bucket != 2 ? 1 : 0;
         int64_t qb = p->kn.batch > 0 ? p->kn.batch : batch_cap(p->ix);

@@ -47,6 +47,7 @@
 
 #include "block_util.cuh"
 #include "bvss_internal.cuh"
+#include "ptx_util.cuh"
 
 namespace bvss {
 
@@ -218,7 +219,8 @@ __device__ __forceinline__ int frac_bits(float x) {
 
 // A query vector's norm and the norm of its rounding error in the refine's copy:
 // form 1 BF16 (round to nearest), form 2 FP8 E4M3 with the vector's own scale
-// (largest magnitude -> 448, round to nearest, saturating), form 0 none.  One warp.
+// (largest magnitude -> 448, round to nearest, saturating), form 3 TF32 (to nearest, ties
+// away from zero, as the refine rounds its query operand), form 0 none.  One warp.
 // gbits: the largest frac_bits of its values.
 __device__ void query_round_err(const float *x, int d, int form, float &norm, float &err,
                                 int &gbits) {
@@ -239,6 +241,8 @@ __device__ void query_round_err(const float *x, int d, int form, float &norm, fl
         float r = v;
         if (form == 1) {
             r = __bfloat162float(__float2bfloat16_rn(v));
+        } else if (form == 3) {
+            r = __uint_as_float(f32_to_tf32(v));
         } else if (form == 2) {
             const __nv_fp8_storage_t f8 = __nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
             const __half_raw hr = __nv_cvt_fp8_to_halfraw(f8, __NV_E4M3);
@@ -551,7 +555,7 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     // copy's scaling is never exact.)
     bool cert;
     {
-        const float eV0 = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
+        const float eV0 = form == 1 ? stats[1] : form == 2 ? stats[2] : form == 3 ? stats[4] : 0.0f;
         const float ns0 = __fadd_ru(qst[0], __fadd_ru(stats[0], eV0));
         const int g = (int)fmaxf(qst[2], stats[3]);
         cert = form != 2 && qst[1] == 0.0f && eV0 == 0.0f && g <= 10 &&
@@ -559,7 +563,7 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
     }
     {
         const float eta_d = eta_of(d);
-        const float eV = form == 1 ? stats[1] : (form == 2 ? stats[2] : 0.0f);
+        const float eV = form == 1 ? stats[1] : form == 2 ? stats[2] : form == 3 ? stats[4] : 0.0f;
         const float nsum = __fadd_ru(qst[0], __fadd_ru(stats[0], eV));
         // GEMM-form squared-distance error bound (d + 8) 2^-23 (N_Q + N_V)^2
         const float D = __fmul_ru((float)(d + 8) * 1.1920929e-7f, __fmul_ru(nsum, nsum));
@@ -567,11 +571,17 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
         // form by default 3 standard deviations of the rounding model, in which the
         // per-value errors are independent and zero-mean, so a pair distance moves by
         // about sqrt(e_q^2 + e_v^2) / sqrt(d)
+        // the TF32 form reads the FP32 rows as TF32 inside the tensor core but takes their
+        // FP32 norms, so its GEMM-form value is |q~|^2 + |v|^2 - 2 q~.v~ = |q~ - v|^2 +
+        // 2 q~.(v - v~): an extra additive term of at most 2 N_Q e_v on the squared value,
+        // and only the query's rounding e_q moves the distance itself
         const float e = form == 2 && !exact_band
                             ? __fmul_ru(3.0f, __fdiv_ru(__fsqrt_ru(__fadd_ru(
                                   __fmul_ru(qst[1], qst[1]), __fmul_ru(eV, eV))), sqrtf((float)d) *
                                   (1.0f - 1e-6f)))
-                            : __fadd_ru(qst[1], eV);
+                        : form == 3 ? qst[1]
+                                    : __fadd_ru(qst[1], eV);
+        const float Dv = form == 3 ? __fadd_ru(D, __fmul_ru(2.0f, __fmul_ru(qst[0], eV))) : D;
         const longlong2 *pq = pair + (int64_t)q * C;
         for (int j = tid; j < n_sel; j += kBT) {
             float lo, hi;
@@ -589,8 +599,8 @@ k_boundary(const float *__restrict__ qvec, const int64_t *__restrict__ qoff, int
                 hi = __fsqrt_ru(__fadd_ru(__fmul_ru(rh, rh), D2));
             } else {
                 const float h2 = __uint_as_float((uint32_t)((unsigned long long)pq[j].x >> 32));
-                lo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(h2, D), 0.0f)), e), 0.0f);
-                hi = __fadd_ru(__fsqrt_ru(__fadd_ru(h2, D)), e);
+                lo = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(h2, Dv), 0.0f)), e), 0.0f);
+                hi = __fadd_ru(__fsqrt_ru(__fadd_ru(h2, Dv)), e);
             }
             if (form != 0) cd[j] = sqrtf(__uint_as_float(
                                        (uint32_t)((unsigned long long)pq[j].x >> 32)));
@@ -772,7 +782,7 @@ cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, in
                              int64_t *out_ids, float *out_dist, int *err, int exact_band,
                              cudaStream_t st) {
     if (n_q <= 0) return cudaSuccess;
-    if (C > BVSS_MAX_C || k < 1 || k > BVSS_MAX_K || form < 0 || form > 2 || d % 4 != 0 ||
+    if (C > BVSS_MAX_C || k < 1 || k > BVSS_MAX_K || form < 0 || form > 3 || d % 4 != 0 ||
         max_mq < 1 || max_mq > BVSS_MAX_QSET)
         return cudaErrorInvalidValue;
     // the query set in shared memory whenever it fits beside the rest (else read in place)
@@ -792,8 +802,13 @@ cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, in
 }
 
 // The largest vector norm of the database and the largest rounding-error norm of its
-// BF16 and FP8 copies (stats[0..2]), each rounded up, read from the stored copies, and
-// the largest frac_bits of its values (stats[3]).
+// BF16 and FP8 copies (stats[0..2]), each rounded up, read from the stored copies, the
+// largest frac_bits of its values (stats[3]), and a bound on the largest rounding-error
+// norm of the vectors read as TF32 (stats[4]).  A tensor core that reads an FP32 value as
+// TF32 keeps 10 of its 23 mantissa bits; whichever way it rounds (to nearest or toward
+// zero), a value it cannot hold moves by less than one TF32 unit in the last place,
+// 2^(e - 10) <= 2^-10 |x| for x = 1.m 2^e, and a value it can hold (low 13 bits zero) does
+// not move.  A subnormal counts with its whole magnitude (it may be flushed to zero).
 __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
                               const __nv_bfloat16 *__restrict__ x16,
                               const uint8_t *__restrict__ x8, const float *__restrict__ sc8,
@@ -801,16 +816,19 @@ __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const float up = 1.0f + 2.0f * eta_of(d);
-    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, m4 = 0.0f;
     int g = 0;
     for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
          v += warps) {
-        float s = 0.0f, e16 = 0.0f, e8 = 0.0f;
+        float s = 0.0f, e16 = 0.0f, e8 = 0.0f, e32 = 0.0f;
         const float sc = x8 ? sc8[v] : 1.0f;
         for (int k = lane; k < d; k += 32) {
             const float a = x[v * d + k];
             g = max(g, frac_bits(a));
             s = fmaf(a, a, s);
+            const uint32_t ua = __float_as_uint(a) & 0x7fffffffu;
+            if ((ua >> 23) == 0) e32 = fmaf(a, a, e32);
+            else if (ua & 0x1fffu) e32 = fmaf(a, a * 0x1p-20f, e32);
             if (x16) {
                 const float b = __bfloat162float(x16[v * d + k]);
                 e16 = fmaf(a - b, a - b, e16);
@@ -826,10 +844,12 @@ __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
             s += __shfl_xor_sync(0xffffffffu, s, o);
             e16 += __shfl_xor_sync(0xffffffffu, e16, o);
             e8 += __shfl_xor_sync(0xffffffffu, e8, o);
+            e32 += __shfl_xor_sync(0xffffffffu, e32, o);
         }
         m0 = fmaxf(m0, __fmul_ru(__fsqrt_ru(s), up));
         m1 = fmaxf(m1, __fmul_ru(__fsqrt_ru(e16), up));
         m2 = fmaxf(m2, __fmul_ru(__fsqrt_ru(e8), up));
+        m4 = fmaxf(m4, __fmul_ru(__fsqrt_ru(e32), up));
     }
     g = (int)__reduce_max_sync(0xffffffffu, (unsigned)g);
     if (lane == 0) {
@@ -837,13 +857,14 @@ __global__ void k_round_stats(const float *__restrict__ x, int64_t n, int d,
         atomicMax(reinterpret_cast<unsigned *>(&stats[0]), __float_as_uint(m0));
         atomicMax(reinterpret_cast<unsigned *>(&stats[1]), __float_as_uint(m1));
         atomicMax(reinterpret_cast<unsigned *>(&stats[2]), __float_as_uint(m2));
+        atomicMax(reinterpret_cast<unsigned *>(&stats[4]), __float_as_uint(m4));
     }
 }
 
 cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,
                                const uint8_t *x8, const float *sc8, float *stats,
                                cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(stats, 0, 4 * sizeof(float), st);
+    cudaError_t e = cudaMemsetAsync(stats, 0, kRoundStats * sizeof(float), st);
     if (e != cudaSuccess || n <= 0) return e;
     int64_t g = (n + 7) / 8;
     if (g > 152 * 16) g = 152 * 16;

@@ -71,9 +71,11 @@ struct bvss_index {
     uint8_t *vec8 = nullptr;          // n_vec x d FP8 E4M3 copy (BVSS_BUILD_FP8)
     float *vscale8 = nullptr;         // its per-vector scales
     float *vnorm8 = nullptr;          // squared norms of the scaled FP8 values
-    float *rstat = nullptr;           // [0] largest norm, [1] / [2] largest rounding-error
-                                      // norm of the BF16 / FP8 copy (rounded up), [3] the
-                                      // largest frac_bits of the values
+    float *rstat = nullptr;           // kRoundStats entries: [0] largest norm, [1] / [2]
+                                      // largest rounding-error norm of the BF16 / FP8 copy
+                                      // (rounded up), [3] the largest frac_bits of the
+                                      // values, [4] a bound on the largest rounding-error
+                                      // norm of the vectors read as TF32
     __nv_bfloat16 *wproj16 = nullptr; // learned dense projection (m x d BF16), or null for
                                       // the sparse binary FlyHash projection proj
     int64_t *set_off = nullptr;  // n_sets + 1
@@ -205,22 +207,25 @@ cudaError_t launch_refine_tma(const float *qvec, const int64_t *qoff, int n_q, i
                               const float *vec, const float *vnorm, const int64_t *set_off,
                               int d, const int32_t *cand, const int32_t *thr, int C,
                               float *cand_dist, int *err, cudaStream_t st);
-// refine_mma.cu: the same on the tensor cores from BF16 or FP8 vectors (query sets <= 64)
-// f8: the FP8 copy (d % 128 == 0) instead of the BF16 one
-bool refine_mma_supported(int d, int max_mq, bool f8 = false);
+// refine_mma.cu: the same on the tensor cores (query sets <= 64) from the BF16 copy
+// (d % 64 == 0), the FP8 copy (d % 128 == 0) or the FP32 vectors read as TF32
+// (d % 32 == 0); the values match the boundary stage's form numbers
+enum class Elem : int { BF16 = 1, FP8 = 2, TF32 = 3 };
+bool refine_mma_supported(int d, int max_mq, Elem e);
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st);
 // FP8 E4M3 copy with one scale per vector and the squared norms of the scaled values
 cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *scale,
                           float *norm, cudaStream_t st);
 // records each candidate's attaining (query vector, row) pair and, in the high word of
-// pair.x, its squared Hausdorff value over the stored copies (read by the boundary stage).  vecb: the BF16 copy, or with
-// f8 the FP8 copy and its per-vector scales vscale; vnorm: squared norms of the stored
-// values.  cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy
+// pair.x, its squared Hausdorff value over the stored copies (read by the boundary
+// stage).  vecb: the BF16 copy, the FP8 copy (with its per-vector scales vscale) or the
+// FP32 vectors, as el says; vnorm: squared norms of the stored values (of the FP32 values
+// for TF32).  cand_cta: candidates per CTA (1..512, 0 = 512); stages: depth of the copy
 // ring (4 up to the most that fit; otherwise, and for 0, the most that fit).
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const void *vecb, const float *vscale, const float *vnorm,
-                              bool f8, const int64_t *set_off, int d, const int32_t *cand,
+                              Elem el, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta = 0, int stages = 0, const int32_t *qlist = nullptr,
                               const int32_t *qcount = nullptr);
@@ -231,13 +236,13 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
 cudaError_t launch_width_lists(const int64_t *qoff, int n_q, int32_t *lists, int32_t *counts,
                                cudaStream_t st);
 // stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
-int refine_mma_stages(int d, int max_mq, bool f8 = false);
+int refine_mma_stages(int d, int max_mq, Elem e);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
-int refine_mma_ring(int d, int max_mq, int stages, bool f8 = false);
+int refine_mma_ring(int d, int max_mq, int stages, Elem e);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------
-// form: the refine that ran (0 FP32, 1 BF16 tensor cores, 2 FP8 tensor cores); stats: the
+// form: the refine that ran (0 FP32, 1 BF16, 2 FP8, 3 TF32 tensor cores); stats: the
 // index's rstat; pair: the MMA forms' records (value in the high word of .x); max_mq: the
 // batch's largest query set; exact_band: the FP8 form's band from its rigorous bound
 // (else from its 3-sigma tolerance).  Band members' cand_dist become their exact values;
@@ -250,6 +255,7 @@ cudaError_t launch_band_topk(const float *qvec, const int64_t *qoff, int n_q, in
                              int64_t *out_ids, float *out_dist, int *err, int exact_band,
                              cudaStream_t st);
 constexpr int kBandKernels = 1;
+constexpr int kRoundStats = 5;   // entries of an index's rstat
 // rstat of an index (x16 / x8 may be null: their entries stay 0)
 cudaError_t launch_round_stats(const float *x, int64_t n, int d, const __nv_bfloat16 *x16,
                                const uint8_t *x8, const float *sc8, float *stats,

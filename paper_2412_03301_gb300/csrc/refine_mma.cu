@@ -173,10 +173,13 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
     return ((unsigned long long)__float_as_uint(d2) << 32) | low;
 }
 
-// F8: the database rows are the FP8 copy (vecb: d bytes per row, with scale vscale and
-// squared norm vnorm of the scaled values) and the query vectors are quantised the same
-// way in the CTA; otherwise both are BF16 (vecb: 2d bytes per row).
-template <int MQ, bool F8>
+// EK = Elem::FP8: the database rows are the FP8 copy (vecb: d bytes per row, with scale
+// vscale and squared norm vnorm of the scaled values) and the query vectors are quantised
+// the same way in the CTA; Elem::BF16: both are BF16 (vecb: 2d bytes per row, vnorm the
+// squared norms of the BF16 values); Elem::TF32: the rows are the FP32 vectors themselves
+// (vecb: 4d bytes per row, vnorm their FP32 squared norms), which the tensor core reads
+// as TF32, and the query vectors are rounded to TF32 (to nearest) in the CTA.
+template <int MQ, int EK>
 __global__ void __launch_bounds__(threads_for(split_for(MQ)), 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const unsigned char *__restrict__ vecb, const float *__restrict__ vscale,
@@ -199,7 +202,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     constexpr int kQBlock = MQ * 128;               // query rows x 128 bytes per K-block
     constexpr int kRowB = MQ * 4;                    // bytes of one row's distances
     constexpr uint32_t kTmemCols = 2 * MQ;           // two accumulators of MQ columns
-    const int RB = F8 ? d : 2 * d;                  // bytes of one stored row
+    constexpr bool F8 = EK == (int)Elem::FP8, TF = EK == (int)Elem::TF32;
+    const int RB = F8 ? d : (TF ? 4 * d : 2 * d);   // bytes of one stored row
     const int KB = RB / 128;
     constexpr bool SPLIT = split_for(MQ);
     constexpr int kThreads = threads_for(SPLIT);
@@ -275,7 +279,17 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) =
             float16_to_fp8(x);
     }
-    for (int e = tid; e < MQ * nch && !F8; e += kThreads) {
+    for (int e = tid; e < MQ * nch && TF; e += kThreads) {
+        const int a = e / nch, ch = e - (e / nch) * nch;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (a < mq) {
+            const float4 u = reinterpret_cast<const float4 *>(qvec + (a0 + a) * d)[ch];
+            pk = make_uint4(f32_to_tf32(u.x), f32_to_tf32(u.y), f32_to_tf32(u.z),
+                            f32_to_tf32(u.w));
+        }
+        *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) = pk;
+    }
+    for (int e = tid; e < MQ * nch && !F8 && !TF; e += kThreads) {
         const int a = e / nch, ch = e - (e / nch) * nch;
         float x[8];
         if (a < mq) {
@@ -347,6 +361,11 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 fp8x16_to_float(pk, f);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) sq = fmaf(f[i], f[i], sq);
+            } else if (TF) {
+                const float f[4] = {__uint_as_float(pk.x), __uint_as_float(pk.y),
+                                    __uint_as_float(pk.z), __uint_as_float(pk.w)};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sq = fmaf(f[i], f[i], sq);
             } else {
                 const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
 #pragma unroll
@@ -433,7 +452,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     } else if (warp == 8) {
         // ---- MMA issue: one thread ----------------------------------------------
         if (lane == 0) {
-            constexpr uint32_t idesc = F8 ? umma_idesc_e4m3(kRowsN, MQ) : umma_idesc_bf16(kRowsN, MQ);
+            constexpr uint32_t idesc = F8   ? umma_idesc_e4m3(kRowsN, MQ)
+                                       : TF ? umma_idesc_tf32(kRowsN, MQ)
+                                            : umma_idesc_bf16(kRowsN, MQ);
             const uint32_t qaddr = smem_u32(Qs), saddr = smem_u32(stages);
             bool ok = true;
             for (int t = 0; t < n_tiles && ok; ++t) {
@@ -448,13 +469,15 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     if (!ok) break;
                     fence_proxy_async();   // the producers' copies, seen by the tensor core
                     tc_fence_after();
-                    // four MMAs per 128-byte K-block: K = 16 BF16 or 32 FP8 values each
+                    // four MMAs per 128-byte K-block: K = 16 BF16, 32 FP8 or 8 TF32 values each
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const uint64_t ad = umma_desc_sw128(saddr + s * kStageBytes + 32 * k);
                         const uint64_t bd = umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
                         if (F8)
                             umma_f8(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                        else if (TF)
+                            umma_tf32(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
                         else
                             umma_bf16(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
                     }
@@ -761,13 +784,16 @@ __global__ void k_to_fp8(const float *__restrict__ x, int64_t n, int d, uint8_t 
 // query-set width of the kernel instance for the batch's largest query set
 inline int mq_for(int max_mq) { return max_mq <= 32 ? 32 : 64; }
 
+// values per 128-byte K-block of a stored row
+inline int kb_values(Elem e) { return e == Elem::FP8 ? 128 : (e == Elem::TF32 ? 32 : 64); }
 // K-blocks of 128 bytes per stored row
-inline int kblocks(int d, bool f8) { return f8 ? d / 128 : d / 64; }
+inline int kblocks(int d, Elem e) { return d / kb_values(e); }
 
-bool refine_mma_supported(int d, int max_mq, bool f8) {
+bool refine_mma_supported(int d, int max_mq, Elem e) {
     if (max_mq < 1 || max_mq > kMaxQ) return false;
-    if (f8 ? (d % 128 != 0 || d < 128) : (d % kKB != 0 || d < kKB)) return false;
-    return pick_stages(kblocks(d, f8), mq_for(max_mq)) > 0;
+    const int kv = kb_values(e);
+    if (d % kv != 0 || d < kv) return false;
+    return pick_stages(kblocks(d, e), mq_for(max_mq)) > 0;
 }
 
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
@@ -789,32 +815,34 @@ cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *s
     return cudaGetLastError();
 }
 
-int refine_mma_stages(int d, int max_mq, bool f8) {
-    return refine_mma_supported(d, max_mq, f8) ? pick_stages(kblocks(d, f8), mq_for(max_mq)) : 0;
+int refine_mma_stages(int d, int max_mq, Elem e) {
+    return refine_mma_supported(d, max_mq, e) ? pick_stages(kblocks(d, e), mq_for(max_mq)) : 0;
 }
 
-int refine_mma_ring(int d, int max_mq, int stages, bool f8) {
-    const int ns = refine_mma_stages(d, max_mq, f8);
+int refine_mma_ring(int d, int max_mq, int stages, Elem e) {
+    const int ns = refine_mma_stages(d, max_mq, e);
     return stages >= kMinNS && stages < ns ? stages : ns;
 }
 
 cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, int max_mq,
                               const void *vecb, const float *vscale, const float *vnorm,
-                              bool f8, const int64_t *set_off, int d, const int32_t *cand,
+                              Elem el, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta, int stages, const int32_t *qlist,
                               const int32_t *qcount) {
     if (n_q <= 0) return cudaSuccess;
-    if (!refine_mma_supported(d, max_mq, f8)) return cudaErrorInvalidValue;
-    if (f8 && !vscale) return cudaErrorInvalidValue;
+    if (!refine_mma_supported(d, max_mq, el)) return cudaErrorInvalidValue;
+    if (el == Elem::FP8 && !vscale) return cudaErrorInvalidValue;
     if ((qlist == nullptr) != (qcount == nullptr)) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
-    const int ns = refine_mma_ring(d, max_mq, stages, f8);
-    const Layout Lo = make_layout(kblocks(d, f8), ns, MQ);
+    const int ns = refine_mma_ring(d, max_mq, stages, el);
+    const Layout Lo = make_layout(kblocks(d, el), ns, MQ);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
-    const auto kern = f8 ? (MQ == 32 ? k_refine_mma<32, true> : k_refine_mma<64, true>)
-                         : (MQ == 32 ? k_refine_mma<32, false> : k_refine_mma<64, false>);
+    constexpr int kB = (int)Elem::BF16, kF = (int)Elem::FP8, kT = (int)Elem::TF32;
+    const auto kern = el == Elem::FP8    ? (MQ == 32 ? k_refine_mma<32, kF> : k_refine_mma<64, kF>)
+                      : el == Elem::TF32 ? (MQ == 32 ? k_refine_mma<32, kT> : k_refine_mma<64, kT>)
+                                         : (MQ == 32 ? k_refine_mma<32, kB> : k_refine_mma<64, kB>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(

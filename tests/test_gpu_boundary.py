@@ -1,7 +1,8 @@
 """The exact top-k (Alg. 6 line 23 over Def. 4) for every refine form.
 
-Off the 2^-8 grid the BF16 and FP8 copies round the vectors and FP32 GEMM-form
-sums round too, so each form's candidate values are approximate.  The
+Off the 2^-8 grid the BF16 and FP8 copies round the vectors, the TF32 form's tensor
+cores round them as they read them, and FP32 GEMM-form sums round too, so each form's
+candidate values are approximate.  The
 boundary stage re-scores, directly in FP32 over all pairs, every candidate
 whose error interval reaches the k-th smallest upper bound, and in FP64 the
 candidates that FP32 cannot order at the top k.  So every form (the FP8 form
@@ -17,7 +18,7 @@ from paper_2412_03301_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
 
-FORMS = (dict(), dict(fast=True), dict(fp8=True, fp8_exact=True))
+FORMS = (dict(), dict(fast=True), dict(fp8=True, fp8_exact=True), dict(tf32=True))
 
 
 @pytest.fixture(scope="module")
@@ -57,6 +58,7 @@ def _check(bv, orc, w, L, k, C, A, M, forms=FORMS):
     (3000, 4, 16, 128, 4, 16, 300, 10),
     (1500, 8, 40, 256, 8, 32, 400, 25),    # rows over one 32-row pair tile, wider k
     (600, 1, 3, 128, 1, 4, 600, 7),        # tiny sets, every set a candidate
+    (800, 8, 32, 384, 1, 64, 200, 10),     # the large workload's d, 32- and 64-wide sets
 ])
 def test_every_form_returns_the_fp64_top_k_off_the_grid(bv, orc, n_sets, lo, hi, d, qlo, qhi,
                                                         C, k):

@@ -71,12 +71,12 @@ def test_database_filters(bv, small):
     assert np.array_equal(cnt, small.orc_ix.count.T)
 
 
-def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False, popc_scan=False):
+def _check_query(bv, orc, case, k, C, A, M, nq=None, fast=False, popc_scan=False, tf32=False):
     w = case.w
     qo = w["q_offsets"] if nq is None else w["q_offsets"][:nq + 1]
     nq = qo.shape[0] - 1
     t = bv.bvss_query_trace(case.ix, case.qv_cuda, qo, k=k, C=C, A=A, M=M, fast=fast,
-                            popc_scan=popc_scan)
+                            popc_scan=popc_scan, tf32=tf32)
     torch.cuda.synchronize()
     qpos = _np(t["qpos"], np.uint16)
     h = _np(t["h"], np.uint16)
@@ -297,6 +297,37 @@ def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     case = Case(bv, orc, w, 24, bf16=True)
     _check_query(bv, orc, case, k=10, C=C, A=3, M=1, fast=True)
     _check_query(bv, orc, case, k=10, C=C, A=2, M=0, nq=4, fast=True)
+
+
+# ---- TF32 form: tensor-core refine from the FP32 vectors read as TF32 ----------------
+# TF32 holds every value on the 2^-8 grid (at most 9 significant bits here), so this form
+# too is exact on grid inputs and must match the oracle like the plain one.
+
+@pytest.mark.parametrize("n_sets,lo,hi,d,qlo,qhi,C,seed", [
+    (2000, 4, 16, 128, 4, 16, 200, 0),     # the small workload's shapes
+    (3000, 8, 32, 384, 8, 32, 1000, 13),   # the large workload's shapes, 8 CTAs per query
+    (300, 1, 3, 32, 1, 5, 300, 14),        # one 32-dim block, tiny sets, C > |F1|
+    (500, 20, 140, 160, 2, 32, 150, 15),   # sets longer than one 128-row tile, odd K-blocks
+    (3000, 1, 1, 64, 1, 3, 1500, 21),      # one-row sets: 128 candidates finish per tile
+    (400, 2, 6, 512, 2, 8, 300, 22),       # the widest rows the 32-wide ring takes
+    (500, 8, 32, 384, 1, 64, 700, 24),     # mixed widths: the 32- and 64-wide instances
+    (300, 20, 140, 192, 60, 64, 150, 25),  # long sets and wide query sets together
+])
+def test_tf32_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
+    w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
+    case = Case(bv, orc, w, 24)
+    _check_query(bv, orc, case, k=10, C=C, A=3, M=1, tf32=True)
+    _check_query(bv, orc, case, k=10, C=C, A=2, M=0, nq=4, tf32=True)
+
+
+def test_tf32_form_falls_back(bv, orc):
+    # shapes the TF32 refine does not take run the CUDA-core FP32 refine: d % 32 != 0,
+    # rows too wide for the ring (d = 768), query sets over 64 vectors
+    for n_sets, d, qlo, qhi, seed in ((100, 48, 2, 6, 26), (80, 768, 2, 8, 27),
+                                      (100, 64, 65, 80, 28)):
+        w = _workload(n_sets, 2, 8, d, 16, 4, qlo, qhi, 256, 4, seed=seed)
+        case = Case(bv, orc, w, 8)
+        _check_query(bv, orc, case, k=5, C=40, A=3, M=1, tf32=True)
 
 
 def test_fast_form_falls_back_and_validates(bv, orc):
