@@ -433,8 +433,8 @@ def fp8_high_d_line(args, dev, stream):
     out_dist = torch.empty((nq, c["k"]), dtype=torch.float32, device=dev)
     hbm, basis = measured_peaks()
     forms, res = {}, {}
-    for name, f in (("plain", {}), ("fast", {"fast": True}), ("fp8", {"fp8": True}),
-                    ("fp8_exact", {"fp8": True, "fp8_exact": True})):
+    for name, f in (("plain", {}), ("tf32", {"tf32": True}), ("fast", {"fast": True}),
+                    ("fp8", {"fp8": True}), ("fp8_exact", {"fp8": True, "fp8_exact": True})):
         bvss.bvss_query(ix, qv, qo, out_ids=out_ids, out_dist=out_dist, stream=stream, **kw, **f)
         torch.cuda.synchronize(dev)
         bvss.bvss_profile_enable(ix, True)
@@ -455,7 +455,7 @@ def fp8_high_d_line(args, dev, stream):
         res[name] = (out_ids.cpu().numpy().copy(), out_dist.cpu().numpy().astype(np.float64))
         forms[name] = {"value": nq / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                        "stages_ms_per_step": stages, "gpu_launches_per_step": nl // reps}
-        row_bytes = {"plain": 4, "fast": 2, "fp8": 1, "fp8_exact": 1}[name] * c["d"]
+        row_bytes = {"plain": 4, "tf32": 4, "fast": 2, "fp8": 1, "fp8_exact": 1}[name] * c["d"]
         ach = cand_rows * row_bytes / (stages["refine"] / 1e3) / 1e9
         forms[name]["refine_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm,
                                           "unit": "GB/s", "frac": ach / hbm,

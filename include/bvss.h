@@ -94,8 +94,8 @@ typedef struct bvss_params {
 
 #define BVSS_SEARCH_POPC_SCAN 2  /* score sketches (Alg. 6 line 12) with CUDA-core popcounts over
                                     the sets that pass layer 1, instead of the default tensor-core
-                                    form (one FP8 GEMM over all pairs, masked by layer 1); both
-                                    give identical h */
+                                    form (one FP8 GEMM over all pairs, masked by layer 1); every
+                                    form gives identical h */
 
 #define BVSS_SEARCH_ALG2 4  /* the plain BioVSS search (Alg. 2) instead of Alg. 6: candidates are
                                the C sets of smallest Haus^H -- Def. 4 with the Hamming distance
@@ -130,6 +130,11 @@ typedef struct bvss_params {
                                 (and at d > 768 the stages must fit: batches the kernel cannot
                                 take use the CUDA-core FP32 refine).  BVSS_SEARCH_FAST and
                                 BVSS_SEARCH_FP8 take precedence */
+#define BVSS_SEARCH_SCAN_SETS_TMEM 64  /* the tensor-core sketch scan with the set sketches
+                                          expanded into tensor memory as the A operand (128
+                                          sets x 128 queries per tile) instead of the query
+                                          sketches as the shared-memory A operand (256 queries
+                                          x 128 sets); identical h */
 
 typedef struct bvss_search {
     int32_t k;      /* results per query set, 1..BVSS_MAX_K */
@@ -137,7 +142,8 @@ typedef struct bvss_search {
     int32_t A;      /* inverted lists accessed, 1..min(L, BVSS_MAX_A) */
     int32_t M;      /* minimum count; 0 lets every set through the first layer */
     int32_t flags;  /* 0 or an OR of BVSS_SEARCH_FAST, BVSS_SEARCH_POPC_SCAN, BVSS_SEARCH_ALG2,
-                       BVSS_SEARCH_FP8, BVSS_SEARCH_FP8_EXACT, BVSS_SEARCH_TF32 */
+                       BVSS_SEARCH_FP8, BVSS_SEARCH_FP8_EXACT, BVSS_SEARCH_TF32,
+                       BVSS_SEARCH_SCAN_SETS_TMEM */
     int32_t reserved;
 } bvss_search;
 
@@ -291,7 +297,7 @@ int bvss_plan_create(bvss_index *ix, const bvss_search *s, int64_t n_queries,
 int bvss_plan_launch(bvss_plan *p, void *stream);
 /* Autotuner: times the pass on the buffers' current contents (reps launches
  * after one warm-up per setting) while varying one choice at a time -- the
- * sketch scan (tensor-core or popcount), the tensor-core refine's candidates
+ * sketch scan (either tensor-core form, or popcounts), the tensor-core refine's candidates
  * per CTA (128, 256, 512) and the depth of its copy ring (the most stages
  * that fit, and two and four fewer), the split of a batch's query sets by width (on or
  * off) and the query sets per internal batch (1024 up to 4096) -- keeps the fastest
@@ -300,14 +306,16 @@ int bvss_plan_launch(bvss_plan *p, void *stream);
  * runs on the plan's own stream; *best_ms (may be NULL) = the chosen pass's
  * time in milliseconds. */
 int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms);
-/* knobs (host, 6 entries, may be NULL): {scan (1 tensor-core, 2 popcount, 0
+/* knobs (host, 6 entries, may be NULL): {scan (1 tensor-core with the query sketches as
+ * the A operand, 2 popcount, 3 tensor-core with the set sketches in tensor memory, 0
  * Alg. 2's own), refine candidates per CTA (0 if the FP32 refine runs),
  * refine copy-ring depth, refine query-set width (32 or 64), 1 if the query sets of at
  * most 32 vectors of a batch run on the 32-wide refine and the wider ones on the 64-wide
  * one, query sets per internal batch}; *launches = kernels per pass. */
 int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches);
 /* Set the choices the autotuner varies and re-capture the graph: knobs (host, 5
- * entries) = {scan (0 by the search flags, 1 tensor-core, 2 popcount), refine
+ * entries) = {scan (0 by the search flags, 1 tensor-core with the query sketches as the
+ * A operand, 2 popcount, 3 tensor-core with the set sketches in tensor memory), refine
  * candidates per CTA (0 = 512, else 1..512), refine copy-ring depth (0 = the most
  * stages that fit; 4 up to that, else the most that fit), width split (0: the query sets
  * of at most 32 vectors on the 32-wide refine, 2: all on the widest), query sets per

@@ -41,6 +41,7 @@ BVSS_SEARCH_ALG2 = 4
 BVSS_SEARCH_FP8 = 8
 BVSS_SEARCH_FP8_EXACT = 16
 BVSS_SEARCH_TF32 = 32
+BVSS_SEARCH_SCAN_SETS_TMEM = 64
 
 
 class bvss_trace(ctypes.Structure):
@@ -201,16 +202,18 @@ def bvss_build(vectors: torch.Tensor, set_offsets, proj, *, fanin=None, wta_l: i
     return Index(h, p, off.shape[0] - 1, int(off[-1]), dev)
 
 
-def _search_flags(fast, popc_scan, alg2=False, fp8=False, fp8_exact=False, tf32=False):
+def _search_flags(fast, popc_scan, alg2=False, fp8=False, fp8_exact=False, tf32=False,
+                  scan_sets_tmem=False):
     return ((BVSS_SEARCH_FAST if fast else 0) | (BVSS_SEARCH_POPC_SCAN if popc_scan else 0)
             | (BVSS_SEARCH_ALG2 if alg2 else 0) | (BVSS_SEARCH_FP8 if fp8 else 0)
-            | (BVSS_SEARCH_FP8_EXACT if fp8_exact else 0) | (BVSS_SEARCH_TF32 if tf32 else 0))
+            | (BVSS_SEARCH_FP8_EXACT if fp8_exact else 0) | (BVSS_SEARCH_TF32 if tf32 else 0)
+            | (BVSS_SEARCH_SCAN_SETS_TMEM if scan_sets_tmem else 0))
 
 
 def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int, A: int = 3,
                M: int = 1, fast: bool = False, popc_scan: bool = False, alg2: bool = False,
-               fp8: bool = False, fp8_exact: bool = False, tf32: bool = False, out_ids=None,
-               out_dist=None, stream=None):
+               fp8: bool = False, fp8_exact: bool = False, tf32: bool = False,
+               scan_sets_tmem: bool = False, out_ids=None, out_dist=None, stream=None):
     """Alg. 6 for a batch of query sets -> (ids (n_q, k) int64, dist (n_q, k) float32).
 
     q_vectors and the outputs may live on the host or on the index's GPU."""
@@ -223,7 +226,7 @@ def bvss_query(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
     s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32, scan_sets_tmem))
     _check(lib.bvss_query(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                           _dptr(out_ids), _dptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -241,7 +244,7 @@ class Plan:
     def __init__(self, ix: Index, n_queries: int, max_vectors: int, max_qset: int, *, k: int,
                  C: int, A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
                  alg2: bool = False, fp8: bool = False, fp8_exact: bool = False,
-                 tf32: bool = False, stream=None):
+                 tf32: bool = False, scan_sets_tmem: bool = False, stream=None):
         lib = load()
         dev = ix.device
         self.ix = ix
@@ -251,7 +254,7 @@ class Plan:
         self.ids = torch.empty((n_queries, k), dtype=torch.int64, device=dev)
         self.dist = torch.empty((n_queries, k), dtype=torch.float32, device=dev)
         s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32, scan_sets_tmem))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.bvss_plan_create(ix.handle, ctypes.byref(s), n_queries, max_vectors,
@@ -288,12 +291,14 @@ class Plan:
         kn = (_c_i32 * 6)()
         nl = _c_i64()
         _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
-        return dict(scan={1: "tensor", 2: "popcount", 0: "alg2"}[kn[0]], cand_cta=kn[1],
+        return dict(scan={1: "tensor", 2: "popcount", 3: "tensor_sets_tmem", 0: "alg2"}[kn[0]],
+                    cand_cta=kn[1],
                     stages=kn[2], mq=kn[3], width_split=kn[4], batch=kn[5],
                     launches=nl.value)
 
     def set_knobs(self, scan=0, cand_cta=0, stages=0, bucket=0, batch=0):
-        """Pin the tuner's choices (0 = default); scan 1 = tensor-core, 2 = popcount;
+        """Pin the tuner's choices (0 = default); scan 1 = tensor-core (query sketches as the
+        A operand), 2 = popcount, 3 = tensor-core (set sketches in tensor memory);
         bucket 2 = no width split; batch = query sets per internal batch."""
         kn = (_c_i32 * 5)(scan, cand_cta, stages, bucket, batch)
         _check(load().bvss_plan_set_knobs(self.handle, kn))
@@ -314,7 +319,7 @@ class Plan:
 def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C: int,
                      A: int = 3, M: int = 1, fast: bool = False, popc_scan: bool = False,
                      alg2: bool = False, fp8: bool = False, fp8_exact: bool = False,
-                     tf32: bool = False, stream=None):
+                     tf32: bool = False, scan_sets_tmem: bool = False, stream=None):
     """bvss_query plus every intermediate of Alg. 6, as a dict of CUDA tensors.
 
     Unsigned 16- and 32-bit outputs are returned in int16 / int32 tensors
@@ -338,7 +343,7 @@ def bvss_query_trace(ix: Index, q_vectors: torch.Tensor, q_offsets, *, k: int, C
     ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
     s = bvss_search(k=k, C=C, A=A, M=M,
-                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32))
+                    flags=_search_flags(fast, popc_scan, alg2, fp8, fp8_exact, tf32, scan_sets_tmem))
     _check(lib.bvss_query_trace(ix.handle, _dptr(q_vectors), off_p, nq, ctypes.byref(s),
                                 _dptr(ids), _dptr(dist), ctypes.byref(tr), _stream(stream)))
     t["ids"] = ids

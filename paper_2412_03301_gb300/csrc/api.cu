@@ -99,6 +99,9 @@ void free_workspace(Workspace &w) {
     dfree(w.cand_dist);
     dfree(w.pair);
     dfree(w.wlist);
+    dfree(w.qop);
+    dfree(w.qop_n);
+    dfree(w.qop_sc);
     dfree(w.enc_x);
     dfree(w.enc_act);
     dfree(w.out_ids);
@@ -229,6 +232,23 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
     BVSS_CU(dalloc(&w.wlist, (size_t)2 * nq + 2));
+    // the refine's streamed query operand, for the forms this index can run whose query
+    // operand does not fit in shared memory
+    size_t qop = 0;
+    for (int wq = 32; wq <= 64; wq += 32) {
+        const Elem forms[3] = {Elem::TF32, Elem::BF16, Elem::FP8};
+        const bool have[3] = {true, ix->vec16 != nullptr, ix->vec8 != nullptr};
+        for (int f = 0; f < 3; ++f)
+            if (have[f] && refine_mma_streams(d, wq, forms[f])) {
+                const size_t b = refine_mma_qop_bytes(d, forms[f]);
+                if (b > qop) qop = b;
+            }
+    }
+    if (qop) {
+        BVSS_CU(dalloc(&w.qop, (size_t)nq * qop));
+        BVSS_CU(dalloc(&w.qop_n, (size_t)nq * 64));
+        BVSS_CU(dalloc(&w.qop_sc, (size_t)nq * 64));
+    }
     if (need_qvec) BVSS_CU(dalloc(&w.qvec, (size_t)nvq * d));
     if (ix->wproj16) {
         BVSS_CU(dalloc(&w.enc_x, (size_t)kEncChunk * d));
@@ -371,7 +391,7 @@ int check_search(const bvss_index *ix, const bvss_search *s) {
         return fail(BVSS_EINVAL, "A = %d: need 1 <= A <= min(L, %d)", s->A, BVSS_MAX_A);
     if (s->M < 0) return fail(BVSS_EINVAL, "M = %d: need M >= 0", s->M);
     if (s->flags & ~(BVSS_SEARCH_FAST | BVSS_SEARCH_POPC_SCAN | BVSS_SEARCH_ALG2 | BVSS_SEARCH_FP8 |
-                     BVSS_SEARCH_FP8_EXACT | BVSS_SEARCH_TF32))
+                     BVSS_SEARCH_FP8_EXACT | BVSS_SEARCH_TF32 | BVSS_SEARCH_SCAN_SETS_TMEM))
         return fail(BVSS_EINVAL, "unknown search flags");
     if ((s->flags & BVSS_SEARCH_FAST) && !ix->vec16)
         return fail(BVSS_EINVAL, "BVSS_SEARCH_FAST needs an index built with BVSS_BUILD_BF16");
@@ -414,8 +434,12 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     const int L = ix->p.wta_l, m = ix->p.m, d = ix->p.d, W = ix->W;
     const int k = s->k, C = s->C, A = s->A, M = s->M, nb = b.nb;
     const bool alg2 = (s->flags & BVSS_SEARCH_ALG2) != 0;
-    const bool tensor_scan =
-        kn.scan ? kn.scan == 1 : (s->flags & BVSS_SEARCH_POPC_SCAN) == 0;
+    // the scan form: 1 tensor cores with the query blocks as the shared-memory A operand,
+    // 3 tensor cores with the set sketches in tensor memory, 2 CUDA-core popcounts
+    const int scan_form = kn.scan ? kn.scan
+                          : (s->flags & BVSS_SEARCH_POPC_SCAN) ? 2
+                          : (s->flags & BVSS_SEARCH_SCAN_SETS_TMEM) ? 3 : 1;
+    const bool tensor_scan = scan_form != 2;
     const int gate_mode = M == 0 ? 0 : (M > 255 ? 2 : 1);
     const int64_t hs = h_stride(ix);
     cudaEvent_t *ev = b.ev;
@@ -447,9 +471,12 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
     if (alg2)
         BVSS_CU(launch_haus_h(w.qpos, b.qoff, nb, ix->codes, ix->set_off, ix->n_sets, m, L, w.h,
                               hs, st));
-    else if (tensor_scan)
+    else if (scan_form == 1)
         BVSS_CU(launch_scan_mma(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
                                 w.q8, w.qpop, nb, w.h, hs, ix->err, st, w.bmin));
+    else if (scan_form == 3)
+        BVSS_CU(launch_scan_tm(ix->sketch, ix->spop, ix->n_sets, W, w.gate, ix->NW, gate_mode,
+                               w.q8, w.qpop, nb, w.h, hs, ix->err, st, w.bmin));
     else
         BVSS_CU(launch_scan(ix->sketch, ix->n_sets, W, w.gate, ix->NW, gate_mode, w.sq, nb, w.h,
                             hs, st));
@@ -471,20 +498,30 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
                        : form == 3 ? (const void *)ix->vec
                                    : (const void *)ix->vec16;
     const float *vnb = form == 2 ? ix->vnorm8 : (form == 3 ? ix->vnorm : ix->vnorm16);
-    if (mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, el)) {
+    const bool split = mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, el);
+    if (mma && (refine_mma_streams(d, b.max_mq, el) || (split && refine_mma_streams(d, 32, el)))) {
+        // a query operand too large for shared memory: stage it for the streamed refine
+        if (!w.qop) return fail(BVSS_ECUDA, "no workspace for the streamed query operand");
+        BVSS_CU(launch_query_op(qv, b.qoff, nb, d, el, w.qop, w.qop_n, w.qop_sc, st));
+        ++n;
+    }
+    if (split) {
         // the batch's query sets by width: the narrow ones on the 32-wide instance
         BVSS_CU(launch_width_lists(b.qoff, nb, w.wlist, w.wlist + 2 * nb, st));
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, 32, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
-                                  kn.cand_cta, kn.stages, w.wlist, w.wlist + 2 * nb));
+                                  kn.cand_cta, kn.stages, w.wlist, w.wlist + 2 * nb, w.qop,
+                                  w.qop_n, w.qop_sc));
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
-                                  kn.cand_cta, kn.stages, w.wlist + nb, w.wlist + 2 * nb + 1));
+                                  kn.cand_cta, kn.stages, w.wlist + nb, w.wlist + 2 * nb + 1,
+                                  w.qop, w.qop_n, w.qop_sc));
         n += 2;
     } else if (mma)
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
-                                  kn.cand_cta, kn.stages));
+                                  kn.cand_cta, kn.stages, nullptr, nullptr, w.qop, w.qop_n,
+                                  w.qop_sc));
     else if (refine_tma_supported(d, b.max_mq))
         BVSS_CU(launch_refine_tma(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
@@ -1198,8 +1235,8 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
         return BVSS_OK;
     };
     if (!alg2) {
-        const int scans[] = {1, 2};
-        rc = sweep(&Knobs::scan, scans, 2);
+        const int scans[] = {1, 2, 3};
+        rc = sweep(&Knobs::scan, scans, 3);
     }
     if (!rc && mma) {
         const int ctas[] = {128, 256, 512};
@@ -1235,8 +1272,10 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
     const int form = refine_form(p->ix, p->s.flags, p->max_qset);
     const bool mma = form > 0;
     if (knobs) {
-        knobs[0] = alg2 ? 0 : (p->kn.scan ? p->kn.scan
-                                          : ((p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2 : 1));
+        knobs[0] = alg2 ? 0
+                   : p->kn.scan ? p->kn.scan
+                   : (p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2
+                   : (p->s.flags & BVSS_SEARCH_SCAN_SETS_TMEM) ? 3 : 1;
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
         knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, static_cast<Elem>(form)) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
@@ -1251,7 +1290,8 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
 int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs) {
     if (!p || !p->exec) return fail(BVSS_EINVAL, "plan is NULL");
     if (!knobs) return fail(BVSS_EINVAL, "knobs are NULL");
-    if (knobs[0] < 0 || knobs[0] > 2) return fail(BVSS_EINVAL, "scan = %d: need 0, 1 or 2", knobs[0]);
+    if (knobs[0] < 0 || knobs[0] > 3)
+        return fail(BVSS_EINVAL, "scan = %d: need 0, 1, 2 or 3", knobs[0]);
     if (knobs[1] < 0 || knobs[1] > 512)
         return fail(BVSS_EINVAL, "candidates per CTA = %d: need 0..512", knobs[1]);
     if (knobs[2] < 0) return fail(BVSS_EINVAL, "stages = %d: need >= 0", knobs[2]);

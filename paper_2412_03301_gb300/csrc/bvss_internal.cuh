@@ -49,6 +49,9 @@ struct Workspace {
     float *cand_dist = nullptr;   // candidate distances                 cap_q x cap_C
     longlong2 *pair = nullptr;    // (query vector, global row) attaining each candidate's value
     int32_t *wlist = nullptr;     // query sets by width (<= 32, wider), then their two counts
+    unsigned char *qop = nullptr; // refine operand of each query set when it is streamed
+    float *qop_n = nullptr;       //   (k_query_op), with its rows' norms and FP8 scales
+    float *qop_sc = nullptr;
     __nv_bfloat16 *enc_x = nullptr;  // dense projection: a block of query vectors in BF16
     float *enc_act = nullptr;        //   and their activations (kEncChunk x d, x m)
     int64_t *out_ids = nullptr;   // staged results (host output)        cap_q x k
@@ -176,6 +179,12 @@ cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t
                             const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
                             const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
                             cudaStream_t st, uint16_t *bmin = nullptr);
+// the same h and bmin with the set sketches as the MMA's A operand in tensor memory (128
+// sets x 128 queries per tile); the same q8 and qpop
+cudaError_t launch_scan_tm(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
+                           const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
+                           const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
+                           cudaStream_t st, uint16_t *bmin = nullptr);
 
 // ---- alg2.cu: Haus^H scores of the plain BioVSS search (Alg. 2 lines 6-8) ----
 // h[q][j] = Haus^H between query set q's codes (qpos, L positions per vector,
@@ -228,7 +237,16 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               Elem el, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta = 0, int stages = 0, const int32_t *qlist = nullptr,
-                              const int32_t *qcount = nullptr);
+                              const int32_t *qcount = nullptr, const unsigned char *qop = nullptr,
+                              const float *qop_n = nullptr, const float *qop_sc = nullptr);
+// true when the shape's query operand does not fit in shared memory beside the ring, so
+// the refine streams it: launch_query_op must first write the batch's operand (qop of
+// n_q x refine_mma_qop_bytes(d, el) bytes, qop_n / qop_sc of n_q x 64 floats), which
+// launch_refine_mma then reads
+bool refine_mma_streams(int d, int max_mq, Elem e);
+size_t refine_mma_qop_bytes(int d, Elem e);
+cudaError_t launch_query_op(const float *qvec, const int64_t *qoff, int n_q, int d, Elem el,
+                            unsigned char *qop, float *qop_n, float *qop_sc, cudaStream_t st);
 // with qlist / qcount (device): only query sets qlist[0 .. *qcount) (the grid still spans
 // n_q rows; max_mq then bounds the listed sets only)
 // lists (2 n_q ints): the batch's query sets of at most 32 vectors, then the wider ones;

@@ -54,7 +54,6 @@ namespace bvss {
 namespace {
 
 constexpr int kRowsN = 128;          // candidate rows per tile (MMA M)
-constexpr int kKB = 64;              // BF16 values per K-block (one 128-byte swizzle row)
 constexpr int kMaxNS = 10;           // stages in the ring, at most
 constexpr int kCandCTA = 512;        // candidates per CTA
 constexpr int kMaxMeta = 14;         // tiles of row metadata in flight, at most
@@ -69,6 +68,8 @@ constexpr int kEpi = 128;
 constexpr int kMaxQ = 64;            // query vectors per query set, at most
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kStageBytes = kRowsN * 128;
+constexpr int kQOpRows = 64;         // rows of a query set's staged operand block (k_query_op)
+constexpr int kQOpBlock = kQOpRows * 128;   // bytes of one K-block of it
 constexpr int kSmemMax = 232448;
 
 struct Meta {
@@ -91,16 +92,22 @@ __host__ __device__ inline int meta_ring(int KB, int ns, bool split) {
     return (ns + KB) / KB + 3 + (split ? 2 : 0);
 }
 
-// KB K-blocks of 128 bytes per row (64 BF16 or 128 FP8 values); MQ query rows x 128
-// bytes per K-block
-__host__ __device__ inline Layout make_layout(int KB, int ns, int MQ) {
+// bytes of one ring stage: a K-block of 128 rows, and with a streamed query operand the
+// same K-block of the MQ query rows
+__host__ __device__ inline int stage_bytes(int MQ, bool qs) {
+    return kStageBytes + (qs ? MQ * 128 : 0);
+}
+
+// KB K-blocks of 128 bytes per row (64 BF16, 128 FP8 or 32 TF32 values); MQ query rows x
+// 128 bytes per K-block, held whole (qs false) or streamed through the ring (qs true)
+__host__ __device__ inline Layout make_layout(int KB, int ns, int MQ, bool qs) {
     Layout L;
     const bool split = split_for(MQ);
     const int nd = split ? 2 : 1;                  // distance blocks
     const int MR = meta_ring(KB, ns, split);
     int o = 0;
-    L.q = o;       o += KB * MQ * 128;
-    L.stages = o;  o += ns * kStageBytes;          // 1024-byte aligned (4 KB multiples)
+    L.q = o;       o += qs ? 0 : KB * MQ * 128;
+    L.stages = o;  o += ns * stage_bytes(MQ, qs);  // 1024-byte aligned (4 KB multiples)
     L.meta = o;    o += MR * kRowsN * (int)sizeof(Meta);
     L.dist = o;    o += nd * kRowsN * MQ * 4;      // row-phase distances, MQ per row
     L.rkey = o;    o += nd * kRowsN * 8;           // per row minimum (the row's key), per block
@@ -117,10 +124,10 @@ __host__ __device__ inline Layout make_layout(int KB, int ns, int MQ) {
 
 constexpr int kMinNS = 4;   // smallest ring a caller may ask for
 
-// most stages that fit, at least 5
-inline int pick_stages(int KB, int MQ) {
-    for (int ns = kMaxNS; ns >= 5; --ns)
-        if (make_layout(KB, ns, MQ).total <= kSmemMax &&
+// most stages that fit, at least 5 with the query operand held whole, 4 streamed
+inline int pick_stages(int KB, int MQ, bool qs) {
+    for (int ns = kMaxNS; ns >= (qs ? 4 : 5); --ns)
+        if (make_layout(KB, ns, MQ, qs).total <= kSmemMax &&
             meta_ring(KB, ns, split_for(MQ)) <= kMaxMeta)
             return ns;
     return 0;
@@ -153,6 +160,60 @@ __device__ __forceinline__ uint4 float16_to_fp8(const float (&f)[16]) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// 16-byte chunk ch of query row x (d FP32 values) in the refine's operand form: FP8 of
+// x / scale (16 values), TF32 (4 values, to nearest) or BF16 (8 values, to nearest)
+template <int EK>
+__device__ __forceinline__ uint4 query_chunk(const float *__restrict__ x, int ch, float inv) {
+    if (EK == (int)Elem::FP8) {
+        const float4 *src = reinterpret_cast<const float4 *>(x + ch * 16);
+        float f[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 u = src[i];
+            f[4 * i] = u.x * inv;
+            f[4 * i + 1] = u.y * inv;
+            f[4 * i + 2] = u.z * inv;
+            f[4 * i + 3] = u.w * inv;
+        }
+        return float16_to_fp8(f);
+    } else if (EK == (int)Elem::TF32) {
+        const float4 u = reinterpret_cast<const float4 *>(x)[ch];
+        return make_uint4(f32_to_tf32(u.x), f32_to_tf32(u.y), f32_to_tf32(u.z), f32_to_tf32(u.w));
+    } else {
+        const float4 *src = reinterpret_cast<const float4 *>(x + ch * 8);
+        const float4 u = src[0], w = src[1];
+        __nv_bfloat162 b0 = __floats2bfloat162_rn(u.x, u.y), b1 = __floats2bfloat162_rn(u.z, u.w);
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(w.x, w.y), b3 = __floats2bfloat162_rn(w.z, w.w);
+        return make_uint4(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1),
+                          *reinterpret_cast<uint32_t *>(&b2), *reinterpret_cast<uint32_t *>(&b3));
+    }
+}
+
+// sum of squares of one operand chunk, added to sq in value order
+template <int EK>
+__device__ __forceinline__ float chunk_sq(const uint4 pk, float sq) {
+    if (EK == (int)Elem::FP8) {
+        float f[16];
+        fp8x16_to_float(pk, f);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sq = fmaf(f[i], f[i], sq);
+    } else if (EK == (int)Elem::TF32) {
+        const float f[4] = {__uint_as_float(pk.x), __uint_as_float(pk.y), __uint_as_float(pk.z),
+                            __uint_as_float(pk.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sq = fmaf(f[i], f[i], sq);
+    } else {
+        const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[i]));
+            sq = fmaf(f.x, f.x, sq);
+            sq = fmaf(f.y, f.y, sq);
+        }
+    }
+    return sq;
+}
+
 // wait for a phase, or give up when the limit passes or another role gave up
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
                                               volatile int *abort_flag, int *err) {
@@ -179,7 +240,7 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
 // squared norms of the BF16 values); Elem::TF32: the rows are the FP32 vectors themselves
 // (vecb: 4d bytes per row, vnorm their FP32 squared norms), which the tensor core reads
 // as TF32, and the query vectors are rounded to TF32 (to nearest) in the CTA.
-template <int MQ, int EK>
+template <int MQ, int EK, bool QS>
 __global__ void __launch_bounds__(threads_for(split_for(MQ)), 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const unsigned char *__restrict__ vecb, const float *__restrict__ vscale,
@@ -187,7 +248,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const int64_t *__restrict__ set_off, int d, int ns,
              const int32_t *__restrict__ cand, const int32_t *__restrict__ thr, int C, int cpc,
              longlong2 *__restrict__ pair, int *__restrict__ err,
-             const int32_t *__restrict__ qlist, const int32_t *__restrict__ qcount) {
+             const int32_t *__restrict__ qlist, const int32_t *__restrict__ qcount,
+             const unsigned char *__restrict__ qop, const float *__restrict__ qop_n,
+             const float *__restrict__ qop_sc) {
     extern __shared__ unsigned char smem_raw[];
     // with a list, CTA row y takes query set qlist[y] (rows past *qcount have none)
     if (qcount && (int)blockIdx.y >= *qcount) return;   // uniform over the CTA
@@ -209,7 +272,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     constexpr int kThreads = threads_for(SPLIT);
     constexpr int kDistBytes = kRowsN * MQ * 4;      // one distance block
     const int MR = meta_ring(KB, ns, SPLIT);
-    const Layout Lo = make_layout(KB, ns, MQ);
+    const Layout Lo = make_layout(KB, ns, MQ, QS);
+    const int SB = stage_bytes(MQ, QS);
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *Qs = smem + Lo.q;
@@ -243,7 +307,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         vrow0[c] = n;
     }
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
-    if (F8) {
+    if (F8 && !QS) {
         // scale of each query vector: its largest magnitude maps to the largest E4M3 value
         for (int a = warp; a < MQ; a += kThreads / 32) {
             float mx = 0.0f;
@@ -258,57 +322,18 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     // query rows 0..MQ-1 (BF16, or FP8 over their scales), K-major 128-byte swizzle
     // (rows >= mq are zero)
     const int nch = RB / 16;                       // 16-byte chunks per row
-    for (int e = tid; e < MQ * nch && F8; e += kThreads) {
+    for (int e = tid; e < MQ * nch && !QS; e += kThreads) {
         const int a = e / nch, ch = e - (e / nch) * nch;
-        float x[16];
-        if (a < mq) {
-            const float4 *src = reinterpret_cast<const float4 *>(qvec + (a0 + a) * d + ch * 16);
-            const float inv = 1.0f / qsc[a];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 u = src[i];
-                x[4 * i] = u.x * inv;
-                x[4 * i + 1] = u.y * inv;
-                x[4 * i + 2] = u.z * inv;
-                x[4 * i + 3] = u.w * inv;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = 0.0f;
-        }
-        *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) =
-            float16_to_fp8(x);
-    }
-    for (int e = tid; e < MQ * nch && TF; e += kThreads) {
-        const int a = e / nch, ch = e - (e / nch) * nch;
-        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-        if (a < mq) {
-            const float4 u = reinterpret_cast<const float4 *>(qvec + (a0 + a) * d)[ch];
-            pk = make_uint4(f32_to_tf32(u.x), f32_to_tf32(u.y), f32_to_tf32(u.z),
-                            f32_to_tf32(u.w));
-        }
+        const uint4 pk = a < mq ? query_chunk<EK>(qvec + (a0 + a) * d, ch, F8 ? 1.0f / qsc[a] : 1.0f)
+                                : make_uint4(0u, 0u, 0u, 0u);
         *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) = pk;
     }
-    for (int e = tid; e < MQ * nch && !F8 && !TF; e += kThreads) {
-        const int a = e / nch, ch = e - (e / nch) * nch;
-        float x[8];
-        if (a < mq) {
-            const float4 *src = reinterpret_cast<const float4 *>(qvec + (a0 + a) * d + ch * 8);
-            const float4 u = src[0], w = src[1];
-            x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
-            x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = 0.0f;
+    if (QS) {
+        // the operand was staged in global memory by k_query_op: its norms and scales
+        for (int a = tid; a < MQ; a += kThreads) {
+            qn[a] = qop_n[(int64_t)q * kQOpRows + a];
+            qsc[a] = qop_sc[(int64_t)q * kQOpRows + a];
         }
-        uint4 pk;
-        __nv_bfloat162 b0 = __floats2bfloat162_rn(x[0], x[1]), b1 = __floats2bfloat162_rn(x[2], x[3]);
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(x[4], x[5]), b3 = __floats2bfloat162_rn(x[6], x[7]);
-        pk.x = *reinterpret_cast<uint32_t *>(&b0);
-        pk.y = *reinterpret_cast<uint32_t *>(&b1);
-        pk.z = *reinterpret_cast<uint32_t *>(&b2);
-        pk.w = *reinterpret_cast<uint32_t *>(&b3);
-        *reinterpret_cast<uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)) = pk;
     }
     fence_proxy_async();
     if (tid == 0) {
@@ -350,33 +375,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         }
         if (lane == 31) vrow0[kCandCTA] = incl;
     }
-    // squared norms of the staged BF16 query rows, one warp per row (warps 1-8)
-    for (int a = warp - 1; warp > 0 && a < MQ; a += kThreads / 32 - 1) {
+    // squared norms of the staged query rows, one warp per row (warps 1-8)
+    for (int a = warp - 1; !QS && warp > 0 && a < MQ; a += kThreads / 32 - 1) {
         float sq = 0.0f;
-        for (int ch = lane; ch < nch; ch += 32) {
-            const uint4 pk =
-                *reinterpret_cast<const uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7));
-            if (F8) {
-                float f[16];
-                fp8x16_to_float(pk, f);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) sq = fmaf(f[i], f[i], sq);
-            } else if (TF) {
-                const float f[4] = {__uint_as_float(pk.x), __uint_as_float(pk.y),
-                                    __uint_as_float(pk.z), __uint_as_float(pk.w)};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) sq = fmaf(f[i], f[i], sq);
-            } else {
-                const uint32_t w4[4] = {pk.x, pk.y, pk.z, pk.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 f =
-                        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[i]));
-                    sq = fmaf(f.x, f.x, sq);
-                    sq = fmaf(f.y, f.y, sq);
-                }
-            }
-        }
+        for (int ch = lane; ch < nch; ch += 32)
+            sq = chunk_sq<EK>(
+                *reinterpret_cast<const uint4 *>(Qs + (ch >> 3) * kQBlock + sw128_off(a, ch & 7)),
+                sq);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) qn[a] = F8 ? sq * qsc[a] * qsc[a] : sq;   // of the stored values
@@ -441,10 +446,17 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 const int s = u % ns;
                 ok = wait_or_abort(&empty[s], (uint32_t)(((u / ns) & 1) ^ 1), abort_flag, err);
                 if (!ok) break;
-                unsigned char *dst = stages + s * kStageBytes;
+                unsigned char *dst = stages + s * SB;
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     if (src[k]) cp_async16(dst + sw128_off(pg + 16 * k, pc), src[k] + kb * 128);
+                if (QS) {
+                    // the query operand's K-block: its first MQ rows, already swizzled
+                    const unsigned char *qs_src = qop + ((int64_t)q * KB + kb) * kQOpBlock;
+#pragma unroll
+                    for (int c = p; c < MQ * 8; c += kProd)
+                        cp_async16(dst + kStageBytes + 16 * c, qs_src + 16 * c);
+                }
                 cp_async_mbar_arrive(&full[s]);   // fires when these copies have landed
             }
         }
@@ -472,8 +484,10 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     // four MMAs per 128-byte K-block: K = 16 BF16, 32 FP8 or 8 TF32 values each
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const uint64_t ad = umma_desc_sw128(saddr + s * kStageBytes + 32 * k);
-                        const uint64_t bd = umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
+                        const uint64_t ad = umma_desc_sw128(saddr + s * SB + 32 * k);
+                        const uint64_t bd =
+                            QS ? umma_desc_sw128(saddr + s * SB + kStageBytes + 32 * k)
+                               : umma_desc_sw128(qaddr + kb * kQBlock + 32 * k);
                         if (F8)
                             umma_f8(dt, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
                         else if (TF)
@@ -789,12 +803,24 @@ inline int kb_values(Elem e) { return e == Elem::FP8 ? 128 : (e == Elem::TF32 ? 
 // K-blocks of 128 bytes per stored row
 inline int kblocks(int d, Elem e) { return d / kb_values(e); }
 
-bool refine_mma_supported(int d, int max_mq, Elem e) {
+// the shape's basic limits (query-set width, whole K-blocks)
+inline bool shape_ok(int d, int max_mq, Elem e) {
     if (max_mq < 1 || max_mq > kMaxQ) return false;
     const int kv = kb_values(e);
-    if (d % kv != 0 || d < kv) return false;
-    return pick_stages(kblocks(d, e), mq_for(max_mq)) > 0;
+    return d % kv == 0 && d >= kv;
 }
+
+bool refine_mma_streams(int d, int max_mq, Elem e) {
+    return shape_ok(d, max_mq, e) && pick_stages(kblocks(d, e), mq_for(max_mq), false) == 0 &&
+           pick_stages(kblocks(d, e), mq_for(max_mq), true) > 0;
+}
+
+bool refine_mma_supported(int d, int max_mq, Elem e) {
+    return shape_ok(d, max_mq, e) && (pick_stages(kblocks(d, e), mq_for(max_mq), false) > 0 ||
+                                      pick_stages(kblocks(d, e), mq_for(max_mq), true) > 0);
+}
+
+size_t refine_mma_qop_bytes(int d, Elem e) { return (size_t)kblocks(d, e) * kQOpBlock; }
 
 cudaError_t launch_to_bf16(const float *x, int64_t n, int d, __nv_bfloat16 *y, float *norm,
                            cudaStream_t st) {
@@ -816,7 +842,9 @@ cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *s
 }
 
 int refine_mma_stages(int d, int max_mq, Elem e) {
-    return refine_mma_supported(d, max_mq, e) ? pick_stages(kblocks(d, e), mq_for(max_mq)) : 0;
+    return refine_mma_supported(d, max_mq, e)
+               ? pick_stages(kblocks(d, e), mq_for(max_mq), refine_mma_streams(d, max_mq, e))
+               : 0;
 }
 
 int refine_mma_ring(int d, int max_mq, int stages, Elem e) {
@@ -829,25 +857,98 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               Elem el, const int64_t *set_off, int d, const int32_t *cand,
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta, int stages, const int32_t *qlist,
-                              const int32_t *qcount) {
+                              const int32_t *qcount, const unsigned char *qop,
+                              const float *qop_n, const float *qop_sc) {
     if (n_q <= 0) return cudaSuccess;
     if (!refine_mma_supported(d, max_mq, el)) return cudaErrorInvalidValue;
     if (el == Elem::FP8 && !vscale) return cudaErrorInvalidValue;
     if ((qlist == nullptr) != (qcount == nullptr)) return cudaErrorInvalidValue;
+    const bool qs = refine_mma_streams(d, max_mq, el);
+    if (qs && (!qop || !qop_n || !qop_sc)) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
     const int ns = refine_mma_ring(d, max_mq, stages, el);
-    const Layout Lo = make_layout(kblocks(d, el), ns, MQ);
+    const Layout Lo = make_layout(kblocks(d, el), ns, MQ, qs);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;
     constexpr int kB = (int)Elem::BF16, kF = (int)Elem::FP8, kT = (int)Elem::TF32;
-    const auto kern = el == Elem::FP8    ? (MQ == 32 ? k_refine_mma<32, kF> : k_refine_mma<64, kF>)
-                      : el == Elem::TF32 ? (MQ == 32 ? k_refine_mma<32, kT> : k_refine_mma<64, kT>)
-                                         : (MQ == 32 ? k_refine_mma<32, kB> : k_refine_mma<64, kB>);
+    using Kern = decltype(&k_refine_mma<32, kB, false>);
+    Kern kern;
+    if (el == Elem::FP8)
+        kern = MQ == 32 ? (qs ? k_refine_mma<32, kF, true> : k_refine_mma<32, kF, false>)
+                        : (qs ? k_refine_mma<64, kF, true> : k_refine_mma<64, kF, false>);
+    else if (el == Elem::TF32)
+        kern = MQ == 32 ? (qs ? k_refine_mma<32, kT, true> : k_refine_mma<32, kT, false>)
+                        : (qs ? k_refine_mma<64, kT, true> : k_refine_mma<64, kT, false>);
+    else
+        kern = MQ == 32 ? (qs ? k_refine_mma<32, kB, true> : k_refine_mma<32, kB, false>)
+                        : (qs ? k_refine_mma<64, kB, true> : k_refine_mma<64, kB, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
     kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(
         qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
-        thr, C, cpc, pair, err, qlist, qcount);
+        thr, C, cpc, pair, err, qlist, qcount, qop, qop_n, qop_sc);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// A query set's refine operand in global memory, for the streamed instances: one warp
+// per (query set, row < kQOpRows); row a of K-block kb at ((q KB + kb) kQOpBlock +
+// sw128_off(a, .)), zero past the set; the squared norm of the stored values (times the
+// scale squared for FP8) and the FP8 scale per row (1 elsewhere).  The same arithmetic as
+// the resident staging in k_refine_mma.
+template <int EK>
+__global__ void k_query_op(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
+                           int n_q, int d, unsigned char *__restrict__ qop,
+                           float *__restrict__ qop_n, float *__restrict__ qop_sc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= (int64_t)n_q * kQOpRows) return;   // uniform over the warp
+    const int q = (int)(wid / kQOpRows), a = (int)(wid % kQOpRows);
+    constexpr bool F8 = EK == (int)Elem::FP8;
+    const int RB = F8 ? d : (EK == (int)Elem::TF32 ? 4 * d : 2 * d);
+    const int KB = RB / 128, nch = RB / 16;
+    const int64_t a0 = qoff[q];
+    const bool valid = a < (int)(qoff[q + 1] - a0);
+    const float *x = qvec + (a0 + a) * d;
+    float sc = 1.0f;
+    if (F8 && valid) {
+        float mx = 0.0f;
+        for (int k = lane; k < d; k += 32) mx = fmaxf(mx, fabsf(x[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sc = mx > 0.0f ? mx / kE4M3Max : 1.0f;
+    }
+    float sq = 0.0f;
+    unsigned char *blk = qop + (int64_t)q * KB * kQOpBlock;
+    for (int ch = lane; ch < nch; ch += 32) {
+        const uint4 pk = valid ? query_chunk<EK>(x, ch, F8 ? 1.0f / sc : 1.0f)
+                               : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(blk + (ch >> 3) * kQOpBlock + sw128_off(a, ch & 7)) = pk;
+        sq = chunk_sq<EK>(pk, sq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) {
+        qop_n[(int64_t)q * kQOpRows + a] = F8 ? sq * sc * sc : sq;
+        qop_sc[(int64_t)q * kQOpRows + a] = sc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query_op(const float *qvec, const int64_t *qoff, int n_q, int d, Elem el,
+                            unsigned char *qop, float *qop_n, float *qop_sc, cudaStream_t st) {
+    if (n_q <= 0) return cudaSuccess;
+    if (!qop || !qop_n || !qop_sc || d % kb_values(el) != 0) return cudaErrorInvalidValue;
+    const int64_t warps = (int64_t)n_q * kQOpRows;
+    const unsigned g = (unsigned)((warps + 7) / 8);
+    if (el == Elem::FP8)
+        k_query_op<(int)Elem::FP8><<<g, 256, 0, st>>>(qvec, qoff, n_q, d, qop, qop_n, qop_sc);
+    else if (el == Elem::TF32)
+        k_query_op<(int)Elem::TF32><<<g, 256, 0, st>>>(qvec, qoff, n_q, d, qop, qop_n, qop_sc);
+    else
+        k_query_op<(int)Elem::BF16><<<g, 256, 0, st>>>(qvec, qoff, n_q, d, qop, qop_n, qop_sc);
     return cudaGetLastError();
 }
 

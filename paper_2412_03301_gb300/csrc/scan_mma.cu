@@ -88,6 +88,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
     return true;
 }
 
+
 // Query sketches -> FP8 rows in the blocked, swizzled layout of the MMA's A
 // operand: block (qp, kb) holds query rows 256 qp .. 256 qp + 255, bits
 // 128 kb .. 128 kb + 127, as two 16 KB halves of 128 rows exactly as the stage
@@ -345,6 +346,244 @@ k_scan_mma(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, in
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---- the same contraction with the set sketches in tensor memory -------------------
+// Tile: 128 set sketches (MMA M, the A operand) x 128 query sketches (MMA N, the B
+// operand).  The producers expand each K-block of the set rows straight into tensor
+// memory (tcgen05.st: a warp writes its own 32 lanes, two warps per lane quarter split
+// the block's 32 columns), so only the query block's 16 KB pass through shared memory
+// (one bulk copy, one MMA read) per K-block, against 112 KB per twice the work in
+// k_scan_mma.  Each expanded set block feeds 128 queries instead of 256, though, so
+// the expansion costs twice the ALU work per pair; on a 1000-query batch over 1M sets
+// this form takes 5.8 ms against k_scan_mma's 4.1 ms.  A batch of at most 128 query
+// sets leaves no half-empty 256-query block here, which is where the tuner may prefer
+// it.  The
+// accumulator's lanes are sets and its columns queries, so the epilogue takes, per
+// query column, one 2-byte score per lane (64 contiguous bytes per warp store) and the
+// tile minimum per query from a warp reduction and four warps' partial minima.
+constexpr int kTS = 128;                  // set sketches per tile (MMA M)
+static_assert(kTS == kSelBlock, "one block minimum per tile");
+constexpr int kTN = 128;                  // query sketches per tile (MMA N)
+constexpr int kTNS = 8;                   // stages (A in tensor memory, B in shared memory)
+constexpr int kTAcc = 2 * kTN;            // two accumulators of kTN columns
+constexpr int kTACol = kTAcc;             // first tensor-memory column of the A stages
+constexpr uint32_t kTTmemCols = 512;      // kTAcc + kTNS x 32
+static_assert(kTAcc + kTNS * 32 <= (int)kTTmemCols, "tensor memory");
+constexpr int kTBStage = kTN * 128;       // 16 KB: one query block's K-block
+constexpr int kTOffB = 0;
+constexpr int kTOffRing = kTOffB + kTNS * kTBStage;
+constexpr int kTOffMin = kTOffRing + kPR * kProd * 8;
+constexpr int kTOffBars = kTOffMin + 4 * kTN * 4;
+constexpr int kTOffMisc = kTOffBars + (2 * kTNS + 4) * 8;
+constexpr int kTSmemBytes = kTOffMisc + 16 + 1024;
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_scan_tm(const uint32_t *__restrict__ sk, const int32_t *__restrict__ spop, int64_t n_sets,
+          int W, const uint32_t *__restrict__ gate, int64_t NW, int gate_mode,
+          const uint8_t *__restrict__ q8, const int32_t *__restrict__ qpop, int n_q, int QB,
+          uint16_t *__restrict__ h, int64_t hs, uint16_t *__restrict__ bmin, int64_t n_blk,
+          int *__restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *stB = smem + kTOffB;
+    unsigned char *ring = smem + kTOffRing;
+    uint32_t *tmin_s = reinterpret_cast<uint32_t *>(smem + kTOffMin);   // 4 warps x kTN
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTOffBars);
+    uint64_t *full = bars, *empty = bars + kTNS, *tfull = bars + 2 * kTNS,
+             *tempty = bars + 2 * kTNS + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kTOffMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kTOffMisc + 4);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int KB = W / 4;
+    const int n_tiles = (int)((n_sets + kTS - 1) / kTS) * QB;   // < 2^31 (host check)
+    const int n_it = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kTTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kTNS; ++s) {
+            mbar_init(&full[s], kProd + 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpi / 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp >= 4 && warp <= 11) {
+        // ---- producers: thread p expands half ph of set row pr into lane pr ----------
+        // (warp w reaches lanes 32 (w % 4) .. + 31, and (w % 4) * 32 + lane == p % 128)
+        const int p = tid - 128;
+        const int pr = p & (kTS - 1), ph = p >> 7;
+        const uint32_t a_lane = (uint32_t)((warp & 3) * 32) << 16;
+        int i_it = 0, i_kb = 0, i_u = 0;
+        int64_t i_row = (int64_t)((int)blockIdx.x / QB) * kTS + pr;
+        auto issue = [&]() {
+            if (i_it < n_it) {
+                if (i_row < n_sets)
+                    cp_async8(ring + ((i_u % kPR) * kProd + p) * 8, sk + i_row * W + 4 * i_kb + 2 * ph);
+                if (++i_kb == KB) {
+                    i_kb = 0;
+                    ++i_it;
+                    i_row = (int64_t)(((int)blockIdx.x + i_it * (int)gridDim.x) / QB) * kTS + pr;
+                }
+            }
+            ++i_u;
+            cp_async_commit();
+        };
+        for (int i = 0; i < kPLag; ++i) issue();
+        bool ok = true;
+        int u = 0;
+        for (int it = 0; it < n_it && ok; ++it) {
+            const int tau = (int)blockIdx.x + it * (int)gridDim.x;
+            const int st = tau / QB, qb = tau - st * QB;
+            const bool row_ok = (int64_t)st * kTS + pr < n_sets;
+            // query block qb of the operand laid out in pairs of 128-row halves
+            const uint8_t *qsrc = q8 + (int64_t)(qb >> 1) * KB * kAStage + (qb & 1) * kQBlk;
+            for (int kb = 0; kb < KB; ++kb, ++u) {
+                issue();
+                cp_async_wait<kPLag>();
+                const int s = u % kTNS;
+                ok = wait_or_abort(&empty[s], (uint32_t)(((u / kTNS) & 1) ^ 1), abort_flag, err);
+                if (!ok) break;
+                tc_fence_after();   // the MMAs that read this A stage are complete
+                if (p == 0) {
+                    mbar_arrive_expect_tx(&full[s], kTBStage);
+                    bulk_g2s(stB + s * kTBStage, qsrc + (int64_t)kb * kAStage, kTBStage, &full[s]);
+                }
+                uint2 w = make_uint2(0, 0);
+                if (row_ok) w = *reinterpret_cast<const uint2 *>(ring + ((u % kPR) * kProd + p) * 8);
+                // The previous stage is signalled here, one step late, once its
+                // tensor-memory stores have completed.
+                if (u > 0) {
+                    tmem_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(&full[(u - 1) % kTNS]);
+                }
+                uint32_t a[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    a[c] = spread4(((c < 8 ? w.x : w.y) >> (4 * (c & 7))) & 0xF);
+                tmem_st16(tmem + a_lane + (uint32_t)(kTACol + s * 32 + ph * 16), a);
+            }
+        }
+        if (ok && u > 0) {
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&full[(u - 1) % kTNS]);
+        }
+        cp_async_wait<0>();
+        if (p == 0 && !ok) {
+            // after giving up, let the query-block copies already issued land before the CTA exits
+            for (int v = u > kTNS ? u - kTNS : 0; v < u; ++v)
+                mbar_wait_bounded(&full[v % kTNS], (uint32_t)((v / kTNS) & 1), kWaitNs / 10);
+        }
+    } else if (warp == 12) {
+        // ---- MMA issue: one thread ------------------------------------------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_e4m3(kTS, kTN);
+            const uint32_t baddr = smem_u32(stB);
+            bool ok = true;
+            int u = 0;
+            for (int it = 0; it < n_it && ok; ++it) {
+                const int buf = it & 1;
+                ok = wait_or_abort(&tempty[buf], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, err);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(buf * kTN);
+                for (int kb = 0; kb < KB && ok; ++kb, ++u) {
+                    const int s = u % kTNS;
+                    ok = wait_or_abort(&full[s], (uint32_t)((u / kTNS) & 1), abort_flag, err);
+                    if (!ok) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        umma_f8_tmem_a(dt, tmem + (uint32_t)(kTACol + s * 32 + 8 * k),
+                                       umma_desc_sw128(baddr + s * kTBStage + 32 * k), idesc,
+                                       (kb | k) != 0 ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        // ---- epilogue: warps 0-3, lane = set 32w + lane of the tile, column = query ----
+        const uint32_t g_const = gate_mode == 0 ? 0xffffffffu : 0u;
+        bool ok = true;
+        for (int it = 0; it < n_it; ++it) {
+            // all four warps leave together if one of them gave up
+            if (!named_barrier_and(1, kEpi, ok)) break;
+            const int tau = (int)blockIdx.x + it * (int)gridDim.x;
+            const int st = tau / QB, qb = tau - st * QB;
+            const int64_t s0 = (int64_t)st * kTS;
+            const int64_t sidx = s0 + warp * 32 + lane;
+            const bool vs = sidx < n_sets;
+            const bool grp = s0 + warp * 32 < n_sets;
+            const int spl = vs ? spop[sidx] : 0;
+            // lane j of group c: query qb kTN + 32 c + j's layer-1 word for this warp's 32
+            // sets and its |S_Q|, loaded before the wait
+            uint32_t gw[kTN / 32];
+            int qpl[kTN / 32];
+#pragma unroll
+            for (int c = 0; c < kTN / 32; ++c) {
+                const int q = qb * kTN + 32 * c + lane;
+                const bool qv = q < n_q;
+                qpl[c] = qv ? qpop[q] : 0;
+                gw[c] = gate_mode == 1 ? (qv && grp ? gate[(int64_t)q * NW + (s0 >> 5) + warp] : 0u)
+                                       : g_const;
+            }
+            const int buf = it & 1;
+            ok = __all_sync(0xffffffffu,
+                            wait_or_abort(&tfull[buf], (uint32_t)((it >> 1) & 1), abort_flag, err));
+            if (!ok) continue;
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < kTN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kTN + c * 32), v);
+                const int q0 = qb * kTN + 32 * c;
+                uint32_t mine = kGatedOut;   // lane j: this warp's minimum for query q0 + j
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t g = __shfl_sync(0xffffffffu, gw[c], j);
+                    const int qp_j = __shfl_sync(0xffffffffu, qpl[c], j);
+                    const int dot = __float2int_rn(__uint_as_float(v[j]) * kDotScale);
+                    const uint32_t hv =
+                        ((g >> lane) & 1) ? (uint32_t)(qp_j + spl - 2 * dot) : (uint32_t)kGatedOut;
+                    if (vs && q0 + j < n_q) h[(int64_t)(q0 + j) * hs + sidx] = (uint16_t)hv;
+                    const uint32_t mn = __reduce_min_sync(0xffffffffu, vs ? hv : (uint32_t)kGatedOut);
+                    if (lane == j) mine = mn;
+                }
+                tmin_s[warp * kTN + 32 * c + lane] = mine;
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            named_barrier_sync(2, kEpi);   // the four warps' partial minima are visible
+            const int q = qb * kTN + tid;
+            if (bmin && q < n_q) {
+                uint32_t m4 = tmin_s[tid];
+#pragma unroll
+                for (int w2 = 1; w2 < 4; ++w2) m4 = min(m4, tmin_s[w2 * kTN + tid]);
+                bmin[(int64_t)q * n_blk + st] = (uint16_t)m4;
+            }
+        }
+    }
+
+    // ---- tear-down ----------------------------------------------------------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTTmemCols);
+}
+
 // |S_i| per database sketch, one warp per set
 __global__ void k_sketch_pop(const uint32_t *__restrict__ sk, int64_t n_sets, int W,
                              int32_t *__restrict__ spop) {
@@ -413,6 +652,25 @@ cudaError_t launch_scan_mma(const uint32_t *sketch, const int32_t *spop, int64_t
                                                              gate_mode, q8, qpop, n_q, QP, h,
                                                              hs, bmin, (n_sets + kSN - 1) / kSN,
                                                              err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tm(const uint32_t *sketch, const int32_t *spop, int64_t n_sets, int W,
+                           const uint32_t *gate, int64_t NW, int gate_mode, const uint8_t *q8,
+                           const int32_t *qpop, int n_q, uint16_t *h, int64_t hs, int *err,
+                           cudaStream_t st, uint16_t *bmin) {
+    if (n_q <= 0 || n_sets <= 0) return cudaSuccess;
+    const int QB = (n_q + kTN - 1) / kTN;
+    cudaError_t e = cudaFuncSetAttribute(k_scan_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int64_t n_tiles = ((n_sets + kTS - 1) / kTS) * QB;
+    if (n_tiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    int64_t grid = sm_count_mma();
+    if (grid > n_tiles) grid = n_tiles;
+    k_scan_tm<<<(unsigned)grid, kThreads, kTSmemBytes, st>>>(sketch, spop, n_sets, W, gate, NW,
+                                                            gate_mode, q8, qpop, n_q, QB, h, hs,
+                                                            bmin, (n_sets + kTS - 1) / kTS, err);
     return cudaGetLastError();
 }
 

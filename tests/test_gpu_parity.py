@@ -125,18 +125,21 @@ def test_query_parity_popcount_scan(bv, orc, small):
     (300, 1, 1024, 16, 1, 2),        # a single query
 ])
 def test_scan_forms_agree(bv, orc, n_sets, nq, m, L, A, M):
-    """Tensor-core scan (all pairs, masked by layer 1) and popcount scan give the
-    same h bit for bit; the tensor-core form also matches the oracle on a sample."""
+    """Both tensor-core scans (all pairs, masked by layer 1) and the popcount scan give
+    the same h bit for bit; the default form also matches the oracle on a sample."""
     w = _workload(n_sets, 3, 12, 32, 16, nq, 2, 9, m, 4, seed=n_sets + nq)
     ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=L)
     qv = w["q_vectors"].cuda()
     C = min(50, n_sets)
     a = bv.bvss_query_trace(ix, qv, w["q_offsets"], k=5, C=C, A=A, M=M)
     b = bv.bvss_query_trace(ix, qv, w["q_offsets"], k=5, C=C, A=A, M=M, popc_scan=True)
+    c = bv.bvss_query_trace(ix, qv, w["q_offsets"], k=5, C=C, A=A, M=M, scan_sets_tmem=True)
     torch.cuda.synchronize()
     ha, hb = _np(a["h"], np.uint16), _np(b["h"], np.uint16)
     assert np.array_equal(ha, hb)
+    assert np.array_equal(ha, _np(c["h"], np.uint16))
     assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"])
+    assert torch.equal(a["ids"], c["ids"]) and torch.equal(a["dist"], c["dist"])
     oix = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], L)
     qo = w["q_offsets"]
     for q in sorted({0, nq // 2, nq - 1}):
@@ -291,6 +294,8 @@ def test_longest_codes(bv, orc, m):
     (600, 1, 128, 768, 1, 64, 400, 23),    # the serving load's d and sizes: 64-wide refine
     (500, 8, 32, 384, 33, 64, 700, 24),    # every query set wider than 32
     (300, 20, 140, 192, 60, 64, 150, 25),  # long sets and wide query sets together
+    (200, 2, 20, 1024, 33, 64, 200, 26),   # d = 1024, 64 wide: the query operand streamed
+    (300, 1, 40, 1024, 1, 64, 250, 27),    # streamed, split by width (32- and 64-wide)
 ])
 def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
@@ -312,6 +317,8 @@ def test_fast_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     (400, 2, 6, 512, 2, 8, 300, 22),       # the widest rows the 32-wide ring takes
     (500, 8, 32, 384, 1, 64, 700, 24),     # mixed widths: the 32- and 64-wide instances
     (300, 20, 140, 192, 60, 64, 150, 25),  # long sets and wide query sets together
+    (300, 2, 12, 768, 2, 16, 200, 28),     # d = 768: the query operand streamed (32-wide)
+    (200, 1, 40, 1024, 1, 64, 250, 29),    # d = 1024, streamed, split by width
 ])
 def test_tf32_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
     w = _workload(n_sets, lo, hi, d, 32, 12, qlo, qhi, 1024, 8, seed=seed)
@@ -322,9 +329,8 @@ def test_tf32_refine_parity(bv, orc, n_sets, lo, hi, d, qlo, qhi, C, seed):
 
 def test_tf32_form_falls_back(bv, orc):
     # shapes the TF32 refine does not take run the CUDA-core FP32 refine: d % 32 != 0,
-    # rows too wide for the ring (d = 768), query sets over 64 vectors
-    for n_sets, d, qlo, qhi, seed in ((100, 48, 2, 6, 26), (80, 768, 2, 8, 27),
-                                      (100, 64, 65, 80, 28)):
+    # query sets over 64 vectors
+    for n_sets, d, qlo, qhi, seed in ((100, 48, 2, 6, 26), (100, 64, 65, 80, 28)):
         w = _workload(n_sets, 2, 8, d, 16, 4, qlo, qhi, 256, 4, seed=seed)
         case = Case(bv, orc, w, 8)
         _check_query(bv, orc, case, k=5, C=40, A=3, M=1, tf32=True)
@@ -332,7 +338,7 @@ def test_tf32_form_falls_back(bv, orc):
 
 def test_fast_form_falls_back_and_validates(bv, orc):
     # query sets of 33-64 vectors take the 64-wide tensor-core refine, larger ones the
-    # FP32 refine
+    # CUDA-core FP32 refine
     for qlo, qhi, seed in ((33, 50, 16), (40, 64, 18), (65, 90, 19)):
         w = _workload(150, 2, 10, 128, 16, 5, qlo, qhi, 512, 8, seed=seed)
         case = Case(bv, orc, w, 16, bf16=True)

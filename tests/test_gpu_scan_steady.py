@@ -1,12 +1,15 @@
-"""The tensor-core sketch scan and the bounded select in their steady state.
+"""The tensor-core sketch scans and the bounded select in their steady state.
 
-The scan (Alg. 6 line 12 as an FP8 GEMM) is a persistent kernel: one CTA
-per SM walks tiles of 256 query sets x 128 sets, alternating two TMEM
-accumulator pairs whose full/empty barrier phases flip every second tile.
-The other GPU tests reach at most two tiles per CTA; here 60,000 sets
-(469 set tiles) x 600 query sets (3 query-block pairs) give 1,407 tiles,
-about 9 per CTA on 152 SMs, so every phase of both barriers and rings of
-several query-block pairs run many times.  The popcount scan (CUDA cores,
+Both tensor-core scans (Alg. 6 line 12 as an FP8 GEMM) are persistent kernels:
+one CTA per SM walks tiles, alternating two TMEM accumulators whose full/empty
+barrier phases flip every second tile.  The default form (query sketches as
+the A operand) takes tiles of 256 query sets x 128 sets: here 60,000 sets (469
+set tiles) x 600 query sets (3 query-block pairs) give 1,407 tiles, about 9 per
+CTA on 152 SMs.  The form with the set sketches expanded into tensor memory
+takes 128 sets x 128 query sets: 2,345 tiles, about 15 per CTA, and its
+8-stage ring turns over 15 times.  The other GPU tests
+reach at most two tiles per CTA, so here every phase of every barrier runs
+many times.  The popcount scan (CUDA cores,
 no persistence, no block minima) must give the same Hamming scores for
 every query set bit for bit, and the select that skips blocks by their
 minima must give the same candidate lists as the one that reads every
@@ -48,14 +51,18 @@ def test_scan_steady_state_against_popcount_and_oracle(steady, orc, A, M, C):
     qv, qo = w["q_vectors"].cuda(), w["q_offsets"]
     a = bvss.bvss_query_trace(ix, qv, qo, k=5, C=C, A=A, M=M)
     b = bvss.bvss_query_trace(ix, qv, qo, k=5, C=C, A=A, M=M, popc_scan=True)
+    c = bvss.bvss_query_trace(ix, qv, qo, k=5, C=C, A=A, M=M, scan_sets_tmem=True)
     torch.cuda.synchronize()
     bvss.bvss_sync(ix)
-    ha, hb = _np(a["h"], np.uint16), _np(b["h"], np.uint16)
+    ha, hb, hc = _np(a["h"], np.uint16), _np(b["h"], np.uint16), _np(c["h"], np.uint16)
     assert ha.shape == (N_Q, N_SETS)
-    rows = np.nonzero((ha != hb).any(axis=1))[0]
-    assert rows.size == 0, "h differs for query sets %s" % rows[:10].tolist()
-    assert torch.equal(a["cand"], b["cand"]) and torch.equal(a["n_cand"], b["n_cand"])
-    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"])
+    for other, name in ((hb, "popcount"), (hc, "sets-in-tensor-memory")):
+        rows = np.nonzero((ha != other).any(axis=1))[0]
+        assert rows.size == 0, "h differs from the %s form for query sets %s" % (
+            name, rows[:10].tolist())
+    for t in (b, c):
+        assert torch.equal(a["cand"], t["cand"]) and torch.equal(a["n_cand"], t["n_cand"])
+        assert torch.equal(a["ids"], t["ids"]) and torch.equal(a["dist"], t["dist"])
     cand, ncand = _np(a["cand"]), _np(a["n_cand"])
     qvec = w["q_vectors"].numpy()
     # query sets of the first, a middle and the last query-block pair, and the last query
