@@ -672,8 +672,11 @@ def measured_peaks():
 # kernel's source file at capture time; the summaries are in profiles/.
 TRAFFIC = {
     "k_refine_mma": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
-                         sha256="c5eb024e7d65a0b587fe3af5b71d52400b236dbc97a731d724bb6bcac9ff9f2d",
-                         bytes_per_unit=779.5, unit="candidate row"),
+                         sha256="725f5ddfcd51e66f64025cc18ea3d5d7cc6aed775d41108fef7c7b327551dfe1",
+                         bytes_per_unit=779.4, unit="candidate row"),
+    "k_refine_mma_tf32": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
+                              sha256="725f5ddfcd51e66f64025cc18ea3d5d7cc6aed775d41108fef7c7b327551dfe1",
+                              bytes_per_unit=1548.8, unit="candidate row"),
     "k_refine": dict(source="paper_2412_03301_gb300/csrc/refine.cu",
                      sha256="6c5ad74bce97e56f0ef9f81aa61baf4f5f2a700f738ffa6bc0c9eadcc846e9ca",
                      bytes_per_unit=1367.8, unit="candidate row"),
@@ -1103,7 +1106,10 @@ def run_ours(args, rank, world, local_rank):
                            / (stage_plain["refine"] / args.steps / 1e3) / 1e9,
                            "frac": cand_rows * c["d"] * 4
                            / (stage_plain["refine"] / args.steps / 1e3) / 1e9
-                           / measured_peaks()[0]},
+                           / measured_peaks()[0],
+                           "traffic": (traffic_per_unit("k_refine_mma_tf32") * cand_rows
+                                       if kw_plain["tf32"] and
+                                       traffic_per_unit("k_refine_mma_tf32") else None)},
                        "cuda_core_refine": {
                            "value": world * nq / (ms_simt / 1e3), "ms_per_step": ms_simt,
                            "stages_ms_per_step": {k: v / args.steps
