@@ -126,10 +126,13 @@ typedef struct bvss_params {
                                 values TF32 holds, such as those on the 2^-8 grid) widens the
                                 boundary band; the top k and their distances are exact as in
                                 bvss_query, and outside the band the trace's cand_dist is that
-                                GEMM-form value.  d % 32 == 0; query sets of up to 64 vectors
-                                (and at d > 768 the stages must fit: batches the kernel cannot
-                                take use the CUDA-core FP32 refine).  BVSS_SEARCH_FAST and
-                                BVSS_SEARCH_FP8 take precedence */
+                                GEMM-form value.  d % 32 == 0 and query sets of up to 64
+                                vectors (batches with a larger set use the CUDA-core FP32
+                                refine).  BVSS_SEARCH_FAST and BVSS_SEARCH_FP8 take
+                                precedence.  Every tensor-core form streams the query set's
+                                operand through its copy ring where it does not fit in shared
+                                memory beside it (TF32 above d = 512 for sets of up to 32
+                                vectors, above 384 for up to 64) */
 #define BVSS_SEARCH_SCAN_SETS_TMEM 64  /* the tensor-core sketch scan with the set sketches
                                           expanded into tensor memory as the A operand (128
                                           sets x 128 queries per tile) instead of the query

@@ -139,6 +139,28 @@ def test_width_split_and_batch_knobs_give_the_same_results(bv, orc, serving):
     plan.close()
 
 
+def test_plan_streams_the_query_operand(bv, orc):
+    """At d = 1024 the BF16 refine's 64-wide query operand does not fit in shared memory:
+    the graph holds the operand pre-pass and the streamed refine (split by width), and
+    the plan must still equal the oracle and bvss_query."""
+    w = datagen.workload(n_sets=400, size_lo=1, size_hi=24, d=1024, n_components=16,
+                         n_queries=10, q_lo=1, q_hi=64, m=1024, fanin=8, seed=SEED + 3)
+    ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=16, bf16=True)
+    orc_ix = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], 16)
+    qv, qo = w["q_vectors"], w["q_offsets"]
+    for kw in (dict(fast=True), dict(tf32=True)):
+        plan = bv.Plan(ix, 10, int(qo[-1]), 64, k=8, C=150, **kw)
+        plan.set_queries(qv.cuda(), qo)
+        ids, dist = plan.launch()
+        bv.bvss_sync(ix)
+        _check_oracle(orc, orc_ix, qv, qo, ids, dist, 8, 150, range(10))
+        ids_q, dist_q = bv.bvss_query(ix, qv.cuda(), qo, k=8, C=150, **kw)
+        assert torch.equal(ids, ids_q) and torch.equal(dist, dist_q), kw
+        assert plan.info()["launches"] >= 14   # the operand pre-pass is in the graph
+        plan.close()
+    ix.close()
+
+
 def test_plan_spans_several_batches(bv, orc, serving):
     # more query sets than one internal batch holds (1024 at this index size)
     w, ix, orc_ix = serving
