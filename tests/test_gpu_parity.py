@@ -395,6 +395,11 @@ def test_alg2_edges_and_long_codes(bv, orc):
     w = _workload(120, 2, 6, 64, 16, 5, 2, 9, 8192, 1, seed=32)
     case = Case(bv, orc, w, 200)
     _check_alg2(bv, orc, case, k=7, C=40)
+    # L = 64 (four carry-save groups, seven planes), sets of more than 32 rows (several
+    # row chunks per set) and query sets of up to 32 vectors
+    w = _workload(300, 20, 45, 64, 16, 6, 20, 32, 2048, 8, seed=35)
+    case = Case(bv, orc, w, 64)
+    _check_alg2(bv, orc, case, k=6, C=50)
 
 
 def test_alg2_with_fast_refine_and_limits(bv, orc):
