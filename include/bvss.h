@@ -302,29 +302,33 @@ int bvss_plan_launch(bvss_plan *p, void *stream);
  * after one warm-up per setting) while varying one choice at a time -- the
  * sketch scan (either tensor-core form, or popcounts), the tensor-core refine's candidates
  * per CTA (128, 256, 512) and the depth of its copy ring (the most stages
- * that fit, and two and four fewer), the split of a batch's query sets by width (on or
- * off) and the query sets per internal batch (1024 up to 4096) -- keeps the fastest
- * setting and re-captures the graph with it.
+ * that fit, and two and four fewer), whether the widest refine instance holds or streams
+ * its query operand (where both are possible), the split of a batch's query sets by width
+ * (on or off) and the query sets per internal batch (1024 up to 4096) -- keeps the
+ * fastest setting and re-captures the graph with it.
  * Every setting gives the same results.  Synchronises `stream` first and
  * runs on the plan's own stream; *best_ms (may be NULL) = the chosen pass's
  * time in milliseconds. */
 int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms);
-/* knobs (host, 6 entries, may be NULL): {scan (1 tensor-core with the query sketches as
+/* knobs (host, 7 entries, may be NULL): {scan (1 tensor-core with the query sketches as
  * the A operand, 2 popcount, 3 tensor-core with the set sketches in tensor memory, 0
  * Alg. 2's own), refine candidates per CTA (0 if the FP32 refine runs),
  * refine copy-ring depth, refine query-set width (32 or 64), 1 if the query sets of at
  * most 32 vectors of a batch run on the 32-wide refine and the wider ones on the 64-wide
- * one, query sets per internal batch}; *launches = kernels per pass. */
+ * one, query sets per internal batch, 1 if the widest refine instance streams its query
+ * operand through its copy ring}; *launches = kernels per pass. */
 int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches);
-/* Set the choices the autotuner varies and re-capture the graph: knobs (host, 5
+/* Set the choices the autotuner varies and re-capture the graph: knobs (host, 6
  * entries) = {scan (0 by the search flags, 1 tensor-core with the query sketches as the
  * A operand, 2 popcount, 3 tensor-core with the set sketches in tensor memory), refine
  * candidates per CTA (0 = 512, else 1..512), refine copy-ring depth (0 = the most
  * stages that fit; 4 up to that, else the most that fit), width split (0: the query sets
  * of at most 32 vectors on the 32-wide refine, 2: all on the widest), query sets per
  * internal batch (0: 1024 or fewer as the index's size allows; at most 4096, bounded by
- * the plan's workspace)}.  bvss_plan_info reports the values in effect.  Results do not
- * depend on them. */
+ * the plan's workspace), the refine's query operand (0: streamed through the copy ring
+ * where it does not fit in shared memory, or where holding it leaves a ring of five
+ * stages or fewer and streaming adds two; 1: held where it fits; 2: streamed)}.
+ * bvss_plan_info reports the values in effect.  Results do not depend on them. */
 int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs);
 void bvss_plan_free(bvss_plan *p);
 

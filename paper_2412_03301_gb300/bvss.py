@@ -288,19 +288,19 @@ class Plan:
         return ms.value
 
     def info(self):
-        kn = (_c_i32 * 6)()
+        kn = (_c_i32 * 7)()
         nl = _c_i64()
         _check(load().bvss_plan_info(self.handle, kn, ctypes.byref(nl)))
         return dict(scan={1: "tensor", 2: "popcount", 3: "tensor_sets_tmem", 0: "alg2"}[kn[0]],
-                    cand_cta=kn[1],
-                    stages=kn[2], mq=kn[3], width_split=kn[4], batch=kn[5],
-                    launches=nl.value)
+                    cand_cta=kn[1], stages=kn[2], mq=kn[3], width_split=kn[4], batch=kn[5],
+                    streams_query=kn[6], launches=nl.value)
 
-    def set_knobs(self, scan=0, cand_cta=0, stages=0, bucket=0, batch=0):
+    def set_knobs(self, scan=0, cand_cta=0, stages=0, bucket=0, batch=0, query_operand=0):
         """Pin the tuner's choices (0 = default); scan 1 = tensor-core (query sketches as the
         A operand), 2 = popcount, 3 = tensor-core (set sketches in tensor memory);
-        bucket 2 = no width split; batch = query sets per internal batch."""
-        kn = (_c_i32 * 5)(scan, cand_cta, stages, bucket, batch)
+        bucket 2 = no width split; batch = query sets per internal batch; query_operand
+        1 = held in shared memory where it fits, 2 = streamed through the copy ring."""
+        kn = (_c_i32 * 6)(scan, cand_cta, stages, bucket, batch, query_operand)
         _check(load().bvss_plan_set_knobs(self.handle, kn))
 
     def close(self):

@@ -232,14 +232,14 @@ int alloc_workspace(const bvss_index *ix, Workspace &w, int64_t nq, int64_t nvq,
     BVSS_CU(dalloc(&w.cand_dist, (size_t)nq * C));
     BVSS_CU(dalloc(&w.pair, (size_t)nq * C));
     BVSS_CU(dalloc(&w.wlist, (size_t)2 * nq + 2));
-    // the refine's streamed query operand, for the forms this index can run whose query
-    // operand does not fit in shared memory
+    // the refine's streamed query operand, for the forms this index can run that can
+    // stream it (by necessity, by default or when the tuner asks)
     size_t qop = 0;
     for (int wq = 32; wq <= 64; wq += 32) {
         const Elem forms[3] = {Elem::TF32, Elem::BF16, Elem::FP8};
         const bool have[3] = {true, ix->vec16 != nullptr, ix->vec8 != nullptr};
         for (int f = 0; f < 3; ++f)
-            if (have[f] && refine_mma_streams(d, wq, forms[f])) {
+            if (have[f] && refine_mma_streams(d, wq, forms[f], 2)) {
                 const size_t b = refine_mma_qop_bytes(d, forms[f]);
                 if (b > qop) qop = b;
             }
@@ -353,6 +353,8 @@ struct Knobs {
                         // 0 the sets of at most 32 on the 32-wide instance and the others on
                         // the 64-wide one, 2 all on the 64-wide one
     int batch = 0;      // query plans: query sets per internal batch (0: the default cap)
+    int qs = 0;         // tensor-core refine: 1 hold the query operand in shared memory where
+                        // it fits, 2 stream it through the ring, 0 by the default rule
 };
 
 // Codes (Def. 7) of n vectors x (device FP32) with the index's projection: the sparse
@@ -499,7 +501,9 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
                                    : (const void *)ix->vec16;
     const float *vnb = form == 2 ? ix->vnorm8 : (form == 3 ? ix->vnorm : ix->vnorm16);
     const bool split = mma && b.max_mq > 32 && kn.bucket != 2 && refine_mma_supported(d, 32, el);
-    if (mma && (refine_mma_streams(d, b.max_mq, el) || (split && refine_mma_streams(d, 32, el)))) {
+    const int qs_mode = w.qop ? kn.qs : 1;
+    if (mma && (refine_mma_streams(d, b.max_mq, el, qs_mode) ||
+                (split && refine_mma_streams(d, 32, el, qs_mode)))) {
         // a query operand too large for shared memory: stage it for the streamed refine
         if (!w.qop) return fail(BVSS_ECUDA, "no workspace for the streamed query operand");
         BVSS_CU(launch_query_op(qv, b.qoff, nb, d, el, w.qop, w.qop_n, w.qop_sc, st));
@@ -511,17 +515,17 @@ int enqueue_batch(bvss_index *ix, Workspace &w, const bvss_search *s, const Knob
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, 32, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages, w.wlist, w.wlist + 2 * nb, w.qop,
-                                  w.qop_n, w.qop_sc));
+                                  w.qop_n, w.qop_sc, kn.qs));
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages, w.wlist + nb, w.wlist + 2 * nb + 1,
-                                  w.qop, w.qop_n, w.qop_sc));
+                                  w.qop, w.qop_n, w.qop_sc, kn.qs));
         n += 2;
     } else if (mma)
         BVSS_CU(launch_refine_mma(qv, b.qoff, nb, b.max_mq, vecb, ix->vscale8, vnb, el,
                                   ix->set_off, d, w.cand, w.thr, C, w.pair, ix->err, st,
                                   kn.cand_cta, kn.stages, nullptr, nullptr, w.qop, w.qop_n,
-                                  w.qop_sc));
+                                  w.qop_sc, kn.qs));
     else if (refine_tma_supported(d, b.max_mq))
         BVSS_CU(launch_refine_tma(qv, b.qoff, nb, b.max_mq, ix->vec, ix->vnorm, ix->set_off, d,
                                   w.cand, w.thr, C, w.cand_dist, ix->err, st));
@@ -1213,7 +1217,7 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
     const bool alg2 = (p->s.flags & BVSS_SEARCH_ALG2) != 0;
     const int form = refine_form(p->ix, p->s.flags, p->max_qset);
     const bool mma = form > 0;
-    const int ns = mma ? refine_mma_stages(d, p->max_qset, static_cast<Elem>(form)) : 0;
+    const Elem el = static_cast<Elem>(mma ? form : 1);
     Knobs best = p->kn;
     float best_t = 0.0f;
     int rc = plan_time(p, best, reps, &best_t);
@@ -1242,7 +1246,14 @@ int bvss_plan_tune(bvss_plan *p, int32_t reps, void *stream, float *best_ms) {
         const int ctas[] = {128, 256, 512};
         rc = sweep(&Knobs::cand_cta, ctas, 3);
     }
+    if (!rc && mma && p->w.qop &&
+        refine_mma_streams(d, p->max_qset, el, 1) != refine_mma_streams(d, p->max_qset, el, 2)) {
+        // the widest instance's query operand: held in shared memory or streamed
+        const int modes[] = {1, 2};
+        rc = sweep(&Knobs::qs, modes, 2);
+    }
     if (!rc && mma) {
+        const int ns = refine_mma_stages(d, p->max_qset, el, p->w.qop ? best.qs : 1);
         int rings[4], nr = 0;
         for (int r = ns; r >= 4 && nr < 3; r -= 2) rings[nr++] = r;
         rc = sweep(&Knobs::stages, rings, nr);
@@ -1277,11 +1288,14 @@ int bvss_plan_info(const bvss_plan *p, int32_t *knobs, int64_t *launches) {
                    : (p->s.flags & BVSS_SEARCH_POPC_SCAN) ? 2
                    : (p->s.flags & BVSS_SEARCH_SCAN_SETS_TMEM) ? 3 : 1;
         knobs[1] = mma ? (p->kn.cand_cta ? p->kn.cand_cta : 512) : 0;
-        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, static_cast<Elem>(form)) : 0;
+        const Elem el = static_cast<Elem>(mma ? form : 1);
+        const int qs_mode = p->w.qop ? p->kn.qs : 1;
+        knobs[2] = mma ? refine_mma_ring(d, p->max_qset, p->kn.stages, el, qs_mode) : 0;
         knobs[3] = mma ? (p->max_qset <= 32 ? 32 : 64) : 0;
         knobs[4] = mma && p->max_qset > 32 && p->kn.bucket != 2 ? 1 : 0;
         int64_t qb = p->kn.batch > 0 ? p->kn.batch : batch_cap(p->ix);
         knobs[5] = (int32_t)(qb < p->w.cap_q ? qb : p->w.cap_q);
+        knobs[6] = mma && refine_mma_streams(d, p->max_qset, el, qs_mode) ? 1 : 0;
     }
     if (launches) *launches = p->launches;
     return BVSS_OK;
@@ -1298,12 +1312,15 @@ int bvss_plan_set_knobs(bvss_plan *p, const int32_t *knobs) {
     if (knobs[3] != 0 && knobs[3] != 2)
         return fail(BVSS_EINVAL, "bucket = %d: need 0 or 2", knobs[3]);
     if (knobs[4] < 0) return fail(BVSS_EINVAL, "batch = %d: need >= 0", knobs[4]);
+    if (knobs[5] < 0 || knobs[5] > 2)
+        return fail(BVSS_EINVAL, "query operand mode = %d: need 0, 1 or 2", knobs[5]);
     const Knobs old = p->kn;
     p->kn.scan = knobs[0];
     p->kn.cand_cta = knobs[1];
     p->kn.stages = knobs[2];
     p->kn.bucket = knobs[3];
     p->kn.batch = knobs[4];
+    p->kn.qs = knobs[5];
     const int rc = plan_capture(p);
     if (rc) p->kn = old;
     return rc;

@@ -238,12 +238,15 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta = 0, int stages = 0, const int32_t *qlist = nullptr,
                               const int32_t *qcount = nullptr, const unsigned char *qop = nullptr,
-                              const float *qop_n = nullptr, const float *qop_sc = nullptr);
-// true when the shape's query operand does not fit in shared memory beside the ring, so
-// the refine streams it: launch_query_op must first write the batch's operand (qop of
-// n_q x refine_mma_qop_bytes(d, el) bytes, qop_n / qop_sc of n_q x 64 floats), which
-// launch_refine_mma then reads
-bool refine_mma_streams(int d, int max_mq, Elem e);
+                              const float *qop_n = nullptr, const float *qop_sc = nullptr,
+                              int qs_mode = 0);
+// true when the refine streams the shape's query operand through its ring instead of
+// holding it in shared memory: always when it does not fit there; otherwise as qs_mode
+// asks (1 hold it, 2 stream it, 0 stream it when that deepens a ring of five stages or
+// fewer by two or more).  A streaming launch needs launch_query_op to have written the
+// batch's operand first (qop of n_q x refine_mma_qop_bytes(d, el) bytes, qop_n / qop_sc
+// of n_q x 64 floats); without those buffers a launch holds the operand where it fits.
+bool refine_mma_streams(int d, int max_mq, Elem e, int qs_mode = 0);
 size_t refine_mma_qop_bytes(int d, Elem e);
 cudaError_t launch_query_op(const float *qvec, const int64_t *qoff, int n_q, int d, Elem el,
                             unsigned char *qop, float *qop_n, float *qop_sc, cudaStream_t st);
@@ -254,9 +257,9 @@ cudaError_t launch_query_op(const float *qvec, const int64_t *qoff, int n_q, int
 cudaError_t launch_width_lists(const int64_t *qoff, int n_q, int32_t *lists, int32_t *counts,
                                cudaStream_t st);
 // stages of the refine's ring for this dimension and batch (0 if the kernel cannot run)
-int refine_mma_stages(int d, int max_mq, Elem e);
+int refine_mma_stages(int d, int max_mq, Elem e, int qs_mode = 0);
 // the ring depth a launch asking for `stages` runs with (0 if the kernel cannot run)
-int refine_mma_ring(int d, int max_mq, int stages, Elem e);
+int refine_mma_ring(int d, int max_mq, int stages, Elem e, int qs_mode = 0);
 // a kernel that waits on an mbarrier nothing completes, with a limit; sets *err on timeout
 cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t st);
 // ---- boundary.cu: the exact top-k over the candidates (Alg. 6 line 23, Def. 4) ------

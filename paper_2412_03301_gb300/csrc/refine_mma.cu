@@ -810,9 +810,17 @@ inline bool shape_ok(int d, int max_mq, Elem e) {
     return d % kv == 0 && d >= kv;
 }
 
-bool refine_mma_streams(int d, int max_mq, Elem e) {
-    return shape_ok(d, max_mq, e) && pick_stages(kblocks(d, e), mq_for(max_mq), false) == 0 &&
-           pick_stages(kblocks(d, e), mq_for(max_mq), true) > 0;
+bool refine_mma_streams(int d, int max_mq, Elem e, int mode) {
+    if (!shape_ok(d, max_mq, e)) return false;
+    const int res = pick_stages(kblocks(d, e), mq_for(max_mq), false);
+    const int str = pick_stages(kblocks(d, e), mq_for(max_mq), true);
+    if (str == 0) return false;   // cannot stream
+    if (res == 0) return true;    // cannot hold the operand
+    if (mode == 1) return false;
+    if (mode == 2) return true;
+    // by default a ring left shallow by the resident operand streams it when that buys
+    // two or more stages (more row bytes in flight)
+    return res <= 5 && str >= res + 2;
 }
 
 bool refine_mma_supported(int d, int max_mq, Elem e) {
@@ -841,14 +849,14 @@ cudaError_t launch_to_fp8(const float *x, int64_t n, int d, uint8_t *y, float *s
     return cudaGetLastError();
 }
 
-int refine_mma_stages(int d, int max_mq, Elem e) {
+int refine_mma_stages(int d, int max_mq, Elem e, int mode) {
     return refine_mma_supported(d, max_mq, e)
-               ? pick_stages(kblocks(d, e), mq_for(max_mq), refine_mma_streams(d, max_mq, e))
+               ? pick_stages(kblocks(d, e), mq_for(max_mq), refine_mma_streams(d, max_mq, e, mode))
                : 0;
 }
 
-int refine_mma_ring(int d, int max_mq, int stages, Elem e) {
-    const int ns = refine_mma_stages(d, max_mq, e);
+int refine_mma_ring(int d, int max_mq, int stages, Elem e, int mode) {
+    const int ns = refine_mma_stages(d, max_mq, e, mode);
     return stages >= kMinNS && stages < ns ? stages : ns;
 }
 
@@ -858,15 +866,17 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                               const int32_t *thr, int C, longlong2 *pair, int *err, cudaStream_t st,
                               int cand_cta, int stages, const int32_t *qlist,
                               const int32_t *qcount, const unsigned char *qop,
-                              const float *qop_n, const float *qop_sc) {
+                              const float *qop_n, const float *qop_sc, int qs_mode) {
     if (n_q <= 0) return cudaSuccess;
     if (!refine_mma_supported(d, max_mq, el)) return cudaErrorInvalidValue;
     if (el == Elem::FP8 && !vscale) return cudaErrorInvalidValue;
     if ((qlist == nullptr) != (qcount == nullptr)) return cudaErrorInvalidValue;
-    const bool qs = refine_mma_streams(d, max_mq, el);
+    // without an operand buffer only the shapes that cannot hold the operand stream
+    const int mode = qop && qop_n && qop_sc ? qs_mode : 1;
+    const bool qs = refine_mma_streams(d, max_mq, el, mode);
     if (qs && (!qop || !qop_n || !qop_sc)) return cudaErrorInvalidValue;
     const int MQ = mq_for(max_mq);
-    const int ns = refine_mma_ring(d, max_mq, stages, el);
+    const int ns = refine_mma_ring(d, max_mq, stages, el, mode);
     const Layout Lo = make_layout(kblocks(d, el), ns, MQ, qs);
     const int cpc = cand_cta >= 1 && cand_cta <= kCandCTA ? cand_cta : kCandCTA;
     const int gx = (C + cpc - 1) / cpc;

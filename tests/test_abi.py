@@ -97,7 +97,7 @@ def test_plan_and_fp8_arguments_fail_without_gpu(lib):
     assert b.bvss_plan_launch(None, None) == bvss.BVSS_EINVAL
     assert b.bvss_plan_tune(None, 1, None, None) == bvss.BVSS_EINVAL
     assert b.bvss_plan_info(None, None, None) == bvss.BVSS_EINVAL
-    kn = (ctypes.c_int32 * 5)(0, 0, 0, 0, 0)
+    kn = (ctypes.c_int32 * 6)(0, 0, 0, 0, 0, 0)
     assert b.bvss_plan_set_knobs(None, kn) == bvss.BVSS_EINVAL
     b.bvss_plan_free(None)                                   # a no-op
     p = bvss.bvss_params(d=64, m=128, fanin=2, wta_l=4, flags=bvss.BVSS_BUILD_FP8)

@@ -132,6 +132,15 @@ def test_width_split_and_batch_knobs_give_the_same_results(bv, orc, serving):
         assert torch.equal(ids0, ids1) and torch.equal(dist0, dist1), (bucket, batch)
         if batch == 0:
             assert kn["launches"] == n_split - 2
+    # the query operand held in shared memory or streamed through the copy ring
+    for mode, streams in ((2, 1), (1, 0)):
+        plan.set_knobs(query_operand=mode)
+        assert plan.info()["streams_query"] == streams
+        ids1, dist1 = plan.launch()
+        bv.bvss_sync(ix)
+        assert torch.equal(ids0, ids1) and torch.equal(dist0, dist1), mode
+    with pytest.raises(bv.BvssError):
+        plan.set_knobs(query_operand=3)
     with pytest.raises(bv.BvssError):
         plan.set_knobs(bucket=1)
     with pytest.raises(bv.BvssError):
