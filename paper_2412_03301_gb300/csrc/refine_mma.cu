@@ -80,7 +80,7 @@ struct Meta {
 };
 
 struct Layout {
-    int q, stages, meta, dist, rkey, carry, bars, grow0, vrow0, qn, qsc, misc, total;
+    int q, stages, meta, dist, rkey, carry, head, bars, grow0, vrow0, qn, qsc, misc, total;
 };
 
 constexpr float kE4M3Max = 448.0f;   // largest finite FP8 E4M3 value
@@ -112,6 +112,7 @@ __host__ __device__ inline Layout make_layout(int KB, int ns, int MQ, bool qs) {
     L.dist = o;    o += nd * kRowsN * MQ * 4;      // row-phase distances, MQ per row
     L.rkey = o;    o += nd * kRowsN * 8;           // per row minimum (the row's key), per block
     L.carry = o;   o += 2 * (MQ + 1) * 8;          // state of a candidate continuing into the next tile
+    L.head = o;    o += split ? 0 : 4 * (MQ + 1) * 8;   // 64-wide: the warps' head segments
     L.bars = o;    o += (2 * kMaxNS + 8 + kMaxMeta) * 8;
     L.grow0 = o;   o += kCandCTA * 8;
     L.vrow0 = o;   o += (kCandCTA + 4) * 4;
@@ -281,6 +282,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     Meta *meta = reinterpret_cast<Meta *>(smem + Lo.meta);
     unsigned char *dist = smem + Lo.dist;
     unsigned long long *carry = reinterpret_cast<unsigned long long *>(smem + Lo.carry);
+    unsigned long long *head = reinterpret_cast<unsigned long long *>(smem + Lo.head);
     unsigned long long *rkey = reinterpret_cast<unsigned long long *>(smem + Lo.rkey);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bars);
     uint64_t *full = bars, *empty = bars + kMaxNS, *tfull = bars + 2 * kMaxNS,
@@ -505,112 +507,236 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         const float INF = __int_as_float(0x7f800000);
         constexpr int H = MQ / 32;                   // query vectors per lane in the column phase
         const int coff = ((lane >> 2) << 4) + (lane & 3) * 4;   // column phase: my query vector's word
-        // column phase of tile t for group warp gw (lane = query vector): the candidates
-        // whose first row in the tile lies in rows 32gw..32gw+31, from the tile's distance
-        // block dblk and row keys kblk
-        auto column_phase = [&](int t, const Meta *mt, const unsigned char *dblk,
-                                const unsigned long long *kblk, int gw) {
-            const int t0 = t * kRowsN;
-            const int rows_t = min(kRowsN, R - t0);
-        // column phase: lane = query vector; candidates whose first row in this
-        // tile lies in rows lo..hi-1 belong to this warp
-        const int lo = gw * 32, hi = min(lo + 32, rows_t);
-        int c = mt[lo].slot;
-        int j = lo;
-        if (lo > 0 && vrow0[c] - t0 < lo) {   // begun in an earlier warp's rows
-            j = vrow0[c + 1] - t0;
-            ++c;
-        }
-        const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
-        unsigned long long *cout = carry + (t & 1) * (MQ + 1);
-        while (j < hi) {
-            const int cs = vrow0[c] - t0;                 // < 0: continues from the last tile
-            const int je = min(vrow0[c + 1] - t0, rows_t);
-            // per query vector lane + 32 h: minimum over the candidate's rows, with the row
-            float bmin[H];
-            int brow[H];
+        // A candidate's pair and value from its per-query-vector row minima (bmin, brow)
+        // and the largest row key kmax: the larger of the two directed values (Def. 4);
+        // the query side's pair is the lowest query vector attaining it.
+        auto finish = [&](int c, const float (&bmin)[H], const int (&brow)[H],
+                          unsigned long long kmax) {
+            uint32_t bits[H], lmx = 0;
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-                bmin[h] = INF;
-                brow[h] = 0;
+                bits[h] = 32 * h + lane < mq ? __float_as_uint(bmin[h]) : 0u;
+                lmx = bits[h] > lmx ? bits[h] : lmx;
             }
-            unsigned long long kmax = 0;
-            if (cs < 0) {
+            const uint32_t mx = __reduce_max_sync(0xffffffffu, lmx);
+            int pa = -1, pr = 0;
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const unsigned long long k0 = cin[32 * h + lane];
-                    bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
-                    brow[h] = (int)(uint32_t)k0;
-                }
-                kmax = cin[MQ];
-            }
-            for (int j0 = j; j0 < je; j0 += 4) {
-                float x[4][H];
-                unsigned long long kk[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
-#pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        x[i][h] = *reinterpret_cast<const float *>(
-                            dblk + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
-                    kk[i] = kblk[jr];
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        if (x[i][h] < bmin[h]) {
-                            bmin[h] = x[i][h];
-                            brow[h] = j0 + i - cs;   // row inside the candidate's set
-                        }
-                    kmax = kk[i] > kmax ? kk[i] : kmax;
+            for (int h = 0; h < H; ++h) {
+                const uint32_t who = __ballot_sync(0xffffffffu, 32 * h + lane < mq && bits[h] == mx);
+                const int src = __ffs(who) - 1;
+                const int rsrc = (int)__shfl_sync(0xffffffffu, (uint32_t)brow[h], src < 0 ? 0 : src);
+                if (pa < 0 && who != 0u) {
+                    pa = 32 * h + src;
+                    pr = rsrc;
                 }
             }
-            if (vrow0[c + 1] - t0 <= rows_t) {
-                // complete: max over query vectors of the row minima vs max over rows;
-                // the query side's pair is the lowest query vector attaining it
-                uint32_t bits[H], lmx = 0;
+            uint32_t hbits = mx;   // the candidate's squared value, as bits
+            if (mx < (uint32_t)(kmax >> 32)) {
+                pa = (int)(kmax & 0xff);
+                pr = (int)((kmax >> 8) & 0xffffff);
+                hbits = (uint32_t)(kmax >> 32);
+            }
+            // the pair as (query vector, global row of the database vector), with the
+            // squared Hausdorff value of the stored copies in the high word of .x
+            if (lane == 0)
+                pair[(int64_t)q * C + c0 + c] = make_longlong2(
+                    (long long)(((unsigned long long)hbits << 32) | (uint32_t)pa), grow0[c] + pr);
+        };
+        // Column phase of the 32-wide instances, which run it in warps of their own on
+        // double-buffered distance blocks: warp gw walks, whole, the candidates whose
+        // first row in the tile lies in rows 32gw..32gw+31 (lane = query vector), from the
+        // tile's distance block dblk and row keys kblk.
+        auto column_walk = [&](int t, const Meta *mt, const unsigned char *dblk,
+                               const unsigned long long *kblk, int gw) {
+            const int t0 = t * kRowsN;
+            const int rows_t = min(kRowsN, R - t0);
+            const int lo = gw * 32, hi = min(lo + 32, rows_t);
+            int c = mt[lo].slot;
+            int j = lo;
+            if (lo > 0 && vrow0[c] - t0 < lo) {   // begun in an earlier warp's rows
+                j = vrow0[c + 1] - t0;
+                ++c;
+            }
+            const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
+            unsigned long long *cout = carry + (t & 1) * (MQ + 1);
+            while (j < hi) {
+                const int cs = vrow0[c] - t0;   // < 0: continues from the last tile
+                const int je = min(vrow0[c + 1] - t0, rows_t);
+                float bmin[H];
+                int brow[H];
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
-                    bits[h] = 32 * h + lane < mq ? __float_as_uint(bmin[h]) : 0u;
-                    lmx = bits[h] > lmx ? bits[h] : lmx;
+                    bmin[h] = INF;
+                    brow[h] = 0;
                 }
-                const uint32_t mx = __reduce_max_sync(0xffffffffu, lmx);
-                int pa = -1, pr = 0;
+                unsigned long long kmax = 0;
+                if (cs < 0) {
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const uint32_t who =
-                        __ballot_sync(0xffffffffu, 32 * h + lane < mq && bits[h] == mx);
-                    const int src = __ffs(who) - 1;
-                    const int rsrc = (int)__shfl_sync(0xffffffffu, (uint32_t)brow[h],
-                                                      src < 0 ? 0 : src);
-                    if (pa < 0 && who != 0u) {
-                        pa = 32 * h + src;
-                        pr = rsrc;
+                    for (int h = 0; h < H; ++h) {
+                        const unsigned long long k0 = cin[32 * h + lane];
+                        bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
+                        brow[h] = (int)(uint32_t)k0;
+                    }
+                    kmax = cin[MQ];
+                }
+                for (int j0 = j; j0 < je; j0 += 4) {
+                    float x[4][H];
+                    unsigned long long kk[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jr = min(j0 + i, je - 1);   // rows past je repeat the last one
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            x[i][h] = *reinterpret_cast<const float *>(
+                                dblk + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
+                        kk[i] = kblk[jr];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            if (x[i][h] < bmin[h]) {
+                                bmin[h] = x[i][h];
+                                brow[h] = j0 + i - cs;   // row inside the candidate's set
+                            }
+                        kmax = kk[i] > kmax ? kk[i] : kmax;
                     }
                 }
-                uint32_t hbits = mx;   // the candidate's squared value, as bits
-                if (mx < (uint32_t)(kmax >> 32)) {
-                    pa = (int)(kmax & 0xff);
-                    pr = (int)((kmax >> 8) & 0xffffff);
-                    hbits = (uint32_t)(kmax >> 32);
-                }
-                // the pair as (query vector, global row of the database vector), with the
-                // squared Hausdorff value of the stored copies in the high word of .x
-                if (lane == 0)
-                    pair[(int64_t)q * C + c0 + c] = make_longlong2(
-                        (long long)(((unsigned long long)hbits << 32) | (uint32_t)pa),
-                        grow0[c] + pr);
-            } else {
-                // continues into the next tile
+                if (vrow0[c + 1] - t0 <= rows_t) {
+                    finish(c, bmin, brow, kmax);
+                } else {
+                    // continues into the next tile
 #pragma unroll
-                for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
-                if (lane == 0) cout[MQ] = kmax;
+                    for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
+                    if (lane == 0) cout[MQ] = kmax;
+                }
+                j = je;
+                ++c;
             }
-            j = je;
-            ++c;
-        }
+        };
+        // Column phase of the 64-wide instances (run by the row-phase warps after their
+        // row phase) for tile t and warp gw (lane = query vector), from the tile's
+        // distance block dblk and row keys kblk.  Each warp walks exactly its own rows
+        // 32gw..32gw+31, so a long candidate does not leave one warp with the tile's work:
+        // it finishes the candidates that start and end there, publishes in head[gw] the
+        // minima of the segment that continues a candidate begun before its rows, and keeps
+        // the candidate that runs past them.  After a barrier of the four warps the owner
+        // of such a candidate (the warp where it starts, or warp 0 for one carried from the
+        // last tile) merges the later warps' heads in row order and finishes it, or carries
+        // it into the next tile.  active false: the warp only meets the barrier.
+        auto column_phase = [&](int t, const Meta *mt, const unsigned char *dblk,
+                                const unsigned long long *kblk, int gw, bool active) {
+            const int t0 = t * kRowsN;
+            const int rows_t = min(kRowsN, R - t0);
+            const int lo = gw * 32, hi = min(lo + 32, rows_t);
+            const unsigned long long *cin = carry + ((t + 1) & 1) * (MQ + 1);
+            unsigned long long *cout = carry + (t & 1) * (MQ + 1);
+            int pc = -1;   // the candidate this warp owns that runs past its rows
+            float pmin[H];
+            int prow[H];
+            unsigned long long pkmax = 0;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                pmin[h] = INF;
+                prow[h] = 0;
+            }
+            if (active && lo < hi) {
+                int c = mt[lo].slot;
+                int j = lo;
+                while (j < hi) {
+                    const int cs = vrow0[c] - t0;   // < 0: continues from the last tile
+                    const int ce = vrow0[c + 1] - t0;
+                    const int je = min(ce, hi);
+                    const bool owned = cs >= lo || gw == 0;
+                    // per query vector lane + 32 h: minimum over the segment's rows, with
+                    // the row inside the candidate's set
+                    float bmin[H];
+                    int brow[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        bmin[h] = INF;
+                        brow[h] = 0;
+                    }
+                    unsigned long long kmax = 0;
+                    if (cs < 0 && gw == 0) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const unsigned long long k0 = cin[32 * h + lane];
+                            bmin[h] = __uint_as_float((uint32_t)(k0 >> 32));
+                            brow[h] = (int)(uint32_t)k0;
+                        }
+                        kmax = cin[MQ];
+                    }
+                    for (int j0 = j; j0 < je; j0 += 4) {
+                        float x[4][H];
+                        unsigned long long kk[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int jr = min(j0 + i, je - 1);   // rows past je repeat the last
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                x[i][h] = *reinterpret_cast<const float *>(
+                                    dblk + jr * kRowB + h * 128 + (coff ^ ((jr & 7) << 4)));
+                            kk[i] = kblk[jr];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                if (x[i][h] < bmin[h]) {
+                                    bmin[h] = x[i][h];
+                                    brow[h] = j0 + i - cs;
+                                }
+                            kmax = kk[i] > kmax ? kk[i] : kmax;
+                        }
+                    }
+                    if (!owned) {
+                        // the head: a candidate begun in an earlier warp's rows
+                        unsigned long long *hd = head + gw * (MQ + 1);
+#pragma unroll
+                        for (int h = 0; h < H; ++h) hd[32 * h + lane] = dkey(bmin[h], (uint32_t)brow[h]);
+                        if (lane == 0) hd[MQ] = kmax;
+                    } else if (ce <= hi) {
+                        finish(c, bmin, brow, kmax);
+                    } else {
+                        pc = c;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            pmin[h] = bmin[h];
+                            prow[h] = brow[h];
+                        }
+                        pkmax = kmax;
+                    }
+                    j = je;
+                    ++c;
+                }
+            }
+            named_barrier_sync(5, kEpi);   // every warp's head is visible
+            if (pc >= 0) {
+                const int ce = vrow0[pc + 1] - t0;
+                for (int w2 = gw + 1; w2 < 4 && 32 * w2 < min(ce, rows_t); ++w2) {
+                    const unsigned long long *hd = head + w2 * (MQ + 1);
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        const unsigned long long k0 = hd[32 * h + lane];
+                        const float v = __uint_as_float((uint32_t)(k0 >> 32));
+                        if (v < pmin[h]) {
+                            pmin[h] = v;
+                            prow[h] = (int)(uint32_t)k0;
+                        }
+                    }
+                    const unsigned long long km = hd[MQ];
+                    pkmax = km > pkmax ? km : pkmax;
+                }
+                if (ce <= rows_t) {
+                    finish(pc, pmin, prow, pkmax);
+                } else {
+                    // continues into the next tile
+#pragma unroll
+                    for (int h = 0; h < H; ++h) cout[32 * h + lane] = dkey(pmin[h], (uint32_t)prow[h]);
+                    if (lane == 0) cout[MQ] = pkmax;
+                }
+            }
         };
         if (!SPLIT || warp < 4) {
             // ---- row phase (and, unless split, the column phase): warps 0-3 ----------
@@ -693,7 +819,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                     continue;
                 }
                 named_barrier_sync(2, kEpi);   // the tile's distances and row keys are visible
-                if (ok && warp * 32 < rows_t) column_phase(t, mt, dblk, kblk, warp);
+                column_phase(t, mt, dblk, kblk, warp, ok);
             }
         } else if (warp >= 9) {
             // ---- column phase: warps 9-12 (split epilogue) ----------------------------
@@ -707,8 +833,8 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                 ok = __all_sync(0xffffffffu, wait_or_abort(&dfull[buf], (uint32_t)((t >> 1) & 1),
                                                            abort_flag, err));
                 if (ok && gw * 32 < min(kRowsN, R - t * kRowsN))
-                    column_phase(t, meta + (t % MR) * kRowsN, dist + buf * kDistBytes,
-                                 rkey + buf * kRowsN, gw);
+                    column_walk(t, meta + (t % MR) * kRowsN, dist + buf * kDistBytes,
+                                rkey + buf * kRowsN, gw);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&dempty[buf]);
             }
