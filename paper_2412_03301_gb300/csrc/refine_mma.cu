@@ -60,9 +60,10 @@ constexpr int kMaxMeta = 14;         // tiles of row metadata in flight, at most
 // warps 0-3 epilogue (row phase, and the column phase unless split), 4-7 producers, 8 MMA,
 // and with a split epilogue 9-12 the column phase
 __host__ __device__ constexpr int threads_for(bool split) { return (split ? 13 : 9) * 32; }
-// the column phase gets warps of its own (and double-buffered distance blocks) for the
-// 32-wide instances; the 64-wide one has no room for a second distance block
-__host__ __device__ constexpr bool split_for(int MQ) { return MQ == 32; }
+// the column phase gets warps of its own (and double-buffered distance blocks) in the
+// 32-wide instances and in the 64-wide ones that stream their query operand (holding it,
+// a 64-wide instance has no room for a second distance block)
+__host__ __device__ constexpr bool split_for(int MQ, bool qs) { return MQ == 32 || qs; }
 constexpr int kProd = 128;
 constexpr int kEpi = 128;
 constexpr int kMaxQ = 64;            // query vectors per query set, at most
@@ -102,7 +103,7 @@ __host__ __device__ inline int stage_bytes(int MQ, bool qs) {
 // 128 bytes per K-block, held whole (qs false) or streamed through the ring (qs true)
 __host__ __device__ inline Layout make_layout(int KB, int ns, int MQ, bool qs) {
     Layout L;
-    const bool split = split_for(MQ);
+    const bool split = split_for(MQ, qs);
     const int nd = split ? 2 : 1;                  // distance blocks
     const int MR = meta_ring(KB, ns, split);
     int o = 0;
@@ -129,7 +130,7 @@ constexpr int kMinNS = 4;   // smallest ring a caller may ask for
 inline int pick_stages(int KB, int MQ, bool qs) {
     for (int ns = kMaxNS; ns >= (qs ? 4 : 5); --ns)
         if (make_layout(KB, ns, MQ, qs).total <= kSmemMax &&
-            meta_ring(KB, ns, split_for(MQ)) <= kMaxMeta)
+            meta_ring(KB, ns, split_for(MQ, qs)) <= kMaxMeta)
             return ns;
     return 0;
 }
@@ -242,7 +243,7 @@ __device__ __forceinline__ unsigned long long dkey(float d2, uint32_t low) {
 // (vecb: 4d bytes per row, vnorm their FP32 squared norms), which the tensor core reads
 // as TF32, and the query vectors are rounded to TF32 (to nearest) in the CTA.
 template <int MQ, int EK, bool QS>
-__global__ void __launch_bounds__(threads_for(split_for(MQ)), 1)
+__global__ void __launch_bounds__(threads_for(split_for(MQ, QS)), 1)
 k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
              const unsigned char *__restrict__ vecb, const float *__restrict__ vscale,
              const float *__restrict__ vnorm,
@@ -269,7 +270,7 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
     constexpr bool F8 = EK == (int)Elem::FP8, TF = EK == (int)Elem::TF32;
     const int RB = F8 ? d : (TF ? 4 * d : 2 * d);   // bytes of one stored row
     const int KB = RB / 128;
-    constexpr bool SPLIT = split_for(MQ);
+    constexpr bool SPLIT = split_for(MQ, QS);
     constexpr int kThreads = threads_for(SPLIT);
     constexpr int kDistBytes = kRowsN * MQ * 4;      // one distance block
     const int MR = meta_ring(KB, ns, SPLIT);
@@ -740,9 +741,13 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
         };
         if (!SPLIT || warp < 4) {
             // ---- row phase (and, unless split, the column phase): warps 0-3 ----------
-            float qreg[MQ];
+            // the query norms (+inf past the set) in registers for 32 query vectors; the
+            // 64-wide instances read them from shared memory (broadcast) to stay within
+            // their registers
+            constexpr bool kQnReg = MQ == 32;
+            float qreg[kQnReg ? MQ : 1];
 #pragma unroll
-            for (int a = 0; a < MQ; ++a) qreg[a] = a < mq ? qn[a] : INF;
+            for (int a = 0; a < (kQnReg ? MQ : 1); ++a) qreg[a] = a < mq ? qn[a] : INF;
             // FP8: q.v = (query scale) (row scale) x accumulator; BF16: scales of 1.  The
             // 64-wide FP8 instance reads the scales from shared memory (broadcast) to stay
             // within its registers
@@ -796,8 +801,9 @@ k_refine_mma(const float *__restrict__ qvec, const int64_t *__restrict__ qoff,
                                 const float w2 =
                                     F8 ? (kQsReg ? qs2[kQsReg ? a : 0] : 2.0f * qsc[a]) * m.sc
                                        : 2.0f;
+                                const float qa = kQnReg ? qreg[kQnReg ? a : 0] : (a < mq ? qn[a] : INF);
                                 const float d2 =
-                                    fmaxf(qreg[a] + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
+                                    fmaxf(qa + m.vn - w2 * __uint_as_float(v[a]), 0.0f);
                                 x[i] = d2;
                                 if (d2 < best) {
                                     best = d2;
@@ -1020,7 +1026,7 @@ cudaError_t launch_refine_mma(const float *qvec, const int64_t *qoff, int n_q, i
                         : (qs ? k_refine_mma<64, kB, true> : k_refine_mma<64, kB, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(gx, n_q), threads_for(split_for(MQ)), Lo.total, st>>>(
+    kern<<<dim3(gx, n_q), threads_for(split_for(MQ, qs)), Lo.total, st>>>(
         qvec, qoff, static_cast<const unsigned char *>(vecb), vscale, vnorm, set_off, d, ns, cand,
         thr, C, cpc, pair, err, qlist, qcount, qop, qop_n, qop_sc);
     return cudaGetLastError();
