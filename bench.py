@@ -672,11 +672,11 @@ def measured_peaks():
 # kernel's source file at capture time; the summaries are in profiles/.
 TRAFFIC = {
     "k_refine_mma": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
-                         sha256="bfb9d189ad3777b3fcac34c604bbb9254d142e3234b77f94295c467a16a74a6f",
+                         sha256="08f24612e7c8e6fe02bcbe03b794d093c156c7e1e35c967f91493a26279fd9e3",
                          bytes_per_unit=779.5, unit="candidate row"),
     "k_refine_mma_tf32": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
-                              sha256="bfb9d189ad3777b3fcac34c604bbb9254d142e3234b77f94295c467a16a74a6f",
-                              bytes_per_unit=1548.8, unit="candidate row"),
+                              sha256="08f24612e7c8e6fe02bcbe03b794d093c156c7e1e35c967f91493a26279fd9e3",
+                              bytes_per_unit=1548.6, unit="candidate row"),
     "k_refine": dict(source="paper_2412_03301_gb300/csrc/refine.cu",
                      sha256="6c5ad74bce97e56f0ef9f81aa61baf4f5f2a700f738ffa6bc0c9eadcc846e9ca",
                      bytes_per_unit=1367.8, unit="candidate row"),
