@@ -111,6 +111,29 @@ def test_fp8_64_wide_with_the_exact_band(bv, orc, case):
         assert set(ids8[q].tolist()) <= set(r["cand"].tolist())
 
 
+def test_every_tensor_core_form_at_d_2048(bv, orc):
+    """At d = 2048 no form holds a 64-wide query operand in shared memory beside its ring,
+    and BF16 and TF32 not even a 32-wide one: every launch streams the operand (and the
+    64-wide ones run the split epilogue).  On these grid values BF16, TF32 and FP8 with
+    its rigorous band must return the oracle's ids and distances; query sets of 1-64
+    vectors exercise both widths."""
+    w = datagen.workload(n_sets=250, size_lo=1, size_hi=12, d=2048, n_components=16,
+                         n_queries=8, q_lo=1, q_hi=64, m=1024, fanin=8, seed=75)
+    ix = bv.bvss_build(w["vectors"].cuda(), w["offsets"], w["proj"], wta_l=16, bf16=True,
+                       fp8=True)
+    oix = orc.Index(w["vectors"].numpy(), w["offsets"], w["proj"], 16)
+    qv, qo = w["q_vectors"], w["q_offsets"]
+    want = [orc.query(oix, qv[qo[q]:qo[q + 1]].numpy(), k=6, C=120, A=3, M=1)
+            for q in range(8)]
+    for kw in (dict(fast=True), dict(tf32=True), dict(fp8=True, fp8_exact=True)):
+        ids, dist = bv.bvss_query(ix, qv.cuda(), qo, k=6, C=120, **kw)
+        bv.bvss_sync(ix)
+        for q, r in enumerate(want):
+            assert ids[q].tolist() == r["ids"].tolist(), (kw, q)
+            np.testing.assert_allclose(dist[q].cpu().numpy(), r["dist"], rtol=3e-6)
+    ix.close()
+
+
 def test_fp8_falls_back_for_wide_query_sets(bv, orc, case):
     # query sets of more than 64 vectors take the FP32 refine: exact again
     w, ix, oix, _ = case
