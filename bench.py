@@ -677,6 +677,9 @@ TRAFFIC = {
     "k_refine_mma_tf32": dict(source="paper_2412_03301_gb300/csrc/refine_mma.cu",
                               sha256="08f24612e7c8e6fe02bcbe03b794d093c156c7e1e35c967f91493a26279fd9e3",
                               bytes_per_unit=1548.6, unit="candidate row"),
+    "k_scan_mma": dict(source="paper_2412_03301_gb300/csrc/scan_mma.cu",
+                       sha256="829de8659085867ca25179631a803c06e3b812b050ed20c942c0d3eb881e94b8",
+                       bytes_per_unit=2.607505, unit="(query set, set) pair"),
     "k_refine": dict(source="paper_2412_03301_gb300/csrc/refine.cu",
                      sha256="6c5ad74bce97e56f0ef9f81aa61baf4f5f2a700f738ffa6bc0c9eadcc846e9ca",
                      bytes_per_unit=1367.8, unit="candidate row"),
@@ -697,7 +700,7 @@ def traffic_per_unit(kernel):
     return float(t["bytes_per_unit"]) if sha == t["sha256"] else None
 
 
-def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=False):
+def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=False, steps=1):
     """Roofline of the dominant kernel (scan or refine) of the timed region.
 
     Each kernel has a compute roof and an HBM roof; the one with the longer time
@@ -714,6 +717,11 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=F
     lanes (152 x 128 x 2 x 2070 MHz), bytes = rows x d x 4."""
     hbm, hbm_basis = measured_peaks()
     per = {k: v / max(1, nbatch) for k, v in stage_ms.items()}     # ms per launch
+    # work per launch: stage_ms and nbatch cover `steps` steps, the work counts one step,
+    # and each kernel launches once per internal batch
+    per_launch = steps / max(1, nbatch)
+    nq, gated_pairs, pair_elems, cand_rows = (x * per_launch for x in
+                                              (nq, gated_pairs, pair_elems, cand_rows))
     clock = SM_MAX_MHZ * 1e6
     try:
         mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -727,7 +735,7 @@ def roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast=F
         scan = dict(name="k_scan_mma", t=per["scan"],
                     alu=(2.0 * nq * c["n_sets"] * c["m"], 2 * bf16_peak, "TFLOP/s",
                          bf16_basis + " sustained bf16 x 2 (FP8 nominal ratio)", "tensor"),
-                    hbm_bytes=scan_bytes, units=None)
+                    hbm_bytes=scan_bytes, units=nq * c["n_sets"])
     else:
         scan = dict(name="k_scan", t=per["scan"],
                     alu=(gated_pairs * (c["m"] // 32), SM_COUNT * POPC_PER_CLK_PER_SM * clock,
@@ -1070,7 +1078,8 @@ def run_ours(args, rank, world, local_rank):
                                          if b95 else None)
 
     # roofline of the dominant kernel, from the per-stage CUDA events of the timed region
-    roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok)
+    roof = roofline(c, stage_ms, nbatch, nq, gated_pairs, pair_elems, cand_rows, fast_ok,
+                    steps=args.steps)
     ix.close()
     torch.cuda.empty_cache()
     offgrid = (offgrid_line(args, dev, stream)

@@ -50,13 +50,19 @@ def test_roofline_picks_the_slower_kernel_and_reports_both(bench):
     rows = 33_483_707
     per = {"encode": 0.5, "gate": 0.2, "scan": 4.0, "select": 1.0, "refine": 5.0,
            "rescore": 0.6, "topk": 0.1}
-    r = bench.roofline(c, {k: 2 * v for k, v in per.items()}, 2, 1000, 1, rows * 20, rows, True)
+    # stage times summed over two steps of one batch each; work counted per step
+    r = bench.roofline(c, {k: 2 * v for k, v in per.items()}, 2, 1000, 1, rows * 20, rows, True,
+                       steps=2)
     assert r["kernel"] == "k_refine_mma" and r["bound"] == "hbm"
     assert r["achieved"] == pytest.approx(rows * 384 * 2 / 5e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / hbm)
     other = r["other_kernels"][0]
     assert other["kernel"] == "k_scan_mma" and other["bound"] == "tensor"
     assert other["achieved"] == pytest.approx(2.0 * 1000 * c["n_sets"] * c["m"] / 4e-3 / 1e12)
+    # one step split into two internal batches: each launch does half the step's work
+    r = bench.roofline(c, per, 2, 1000, 1, rows * 20, rows, True, steps=1)
+    assert r["achieved"] == pytest.approx(rows / 2 * 384 * 2 / 2.5e-3 / 1e9)
+    assert r["algorithmic_bytes"] == pytest.approx(rows / 2 * 384 * 2)
     # the scan dominates when it is the slower one
     per["scan"], per["refine"] = 6.0, 5.0
     r = bench.roofline(c, per, 1, 1000, 1, rows * 20, rows, True)
